@@ -1,0 +1,178 @@
+/*
+ * rlbm.h -- C ABI of the GB300 relativistic lattice Boltzmann step.
+ *
+ * Method: Gabbana, Mendoza, Succi & Tripiccione, "Towards a unified lattice
+ * kinetic scheme for relativistic hydrodynamics" (arXiv:1703.04605).  One call
+ * of rlbm_step advances a periodic Nx x Ny lattice by the discrete
+ * relativistic Boltzmann equation with Anderson-Witting relaxation (Eq. 49,
+ * Sec. III C):
+ *
+ *   f_i(x + n_i, t + 1) = f_i(x, t) - (p_i.U / (p_i^0 tau)) (f_i - f_i^eq),
+ *
+ * where, per site, N^a = sum_i f_i p_i^a and T^ab = sum_i f_i p_i^a p_i^b
+ * (Eq. 4-5, 18), e and U solve the Landau-frame eigenproblem T^ab U_b = e U^a
+ * (Eq. 20), n = U_a N^a (Eq. 19), T solves e/n = 3T + m K1(m/T)/K2(m/T)
+ * (Eq. 28), and f_i^eq = n w_i sum_k b^(k)(U, T) J^(k)(p_i) is the
+ * second-order expansion (Eq. 16, App. A and B).
+ *
+ * Units: c = k_B = T_R = 1 (so mbar = m), lattice spacing 1, one time step 1.
+ * Metric diag(1,-1,-1,-1).  The velocity set is a second-order stencil of six
+ * groups of Table I (App. C) with common velocity parameter v0 (Eq. 48),
+ * folded onto the xy plane: the +-n_z members of a group merge into one
+ * population of doubled weight, which reproduces the 3D model on an
+ * Nx x Ny x 1 lattice exactly while U^z = 0.
+ *
+ * Conventions for every function:
+ *  - Status codes only; nothing throws across the ABI.  On failure the
+ *    context keeps its previous state and rlbm_last_error() describes why.
+ *  - Host arrays are owned by the caller, row-major [Ny][Nx] doubles.
+ *  - Device work is issued on the CUDA stream given at creation.  Device-side
+ *    errors (non-physical sites) are sticky: they are reported by the next
+ *    call that synchronises (rlbm_moments, rlbm_sync) as RLBM_ENONPHYS.
+ *  - The library never falls back to host computation: without a usable
+ *    CUDA device every call that needs one returns RLBM_ECUDA.
+ */
+#ifndef RLBM_H
+#define RLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rlbm_ctx rlbm_ctx;
+
+typedef enum {
+  RLBM_OK = 0,
+  RLBM_EINVAL = 1,   /* invalid argument, detected before any launch          */
+  RLBM_ENOQUAD = 2,  /* no positive-weight quadrature for these groups at m   */
+  RLBM_ENOMEM = 3,   /* device or host allocation failed                       */
+  RLBM_ECUDA = 4,    /* CUDA runtime error (including: no device)              */
+  RLBM_ENONPHYS = 5, /* a site left the physical domain (n<=0, |u|>=1, T<=0,
+                        non-finite); sticky until reported                     */
+  RLBM_ETIMEOUT = 6, /* a bounded device-side wait expired                     */
+  RLBM_ENOTSUP = 7   /* valid but unsupported (e.g. more populations than the
+                        compiled maximum)                                      */
+} rlbm_status;
+
+/* Population storage.  Arithmetic: F64 computes everything in FP64; F32 and
+ * BF16_DEV accumulate in FP32 and solve the Landau frame and the EOS with an
+ * FP64 correction step.  BF16_DEV stores d_i = f_i - f_i^eq in bfloat16 plus
+ * per-site FP32 macroscopic fields used to rebuild f_i^eq. */
+typedef enum { RLBM_F64 = 0, RLBM_F32 = 1, RLBM_BF16_DEV = 2 } rlbm_dtype;
+
+/* A second-order stencil (Sec. III C-D): exactly six distinct groups of
+ * Table I (ids 1..84) and v0.  v0 > 0 is used as given (it must make every
+ * weight positive and v0 ||n_k|| < 1); v0 == 0 selects the centre of the
+ * widest interval of v0 where all six weights are positive (Sec. III D). */
+typedef struct {
+  int ngroups;
+  const int* groups;
+  double v0;
+} rlbm_stencil;
+
+/* Read-only description of a context (rlbm_get_info). */
+typedef struct {
+  int Nx, Ny;
+  int Q;            /* folded populations                                   */
+  int halo;         /* largest |n_x| or |n_y| of the stencil                */
+  rlbm_dtype dtype;
+  double m, tau, v0;
+  double w_group[6];        /* weights of the six groups (Eq. 47/52)         */
+  long long t;              /* current time step                             */
+  size_t bytes_per_site;    /* populations read + written per site update:
+                               2 Q sizeof(storage)                           */
+  size_t extra_bytes_per_site; /* other per-site traffic of one step (macros) */
+  size_t device_bytes;      /* device memory owned by the context            */
+  int kernel;               /* step kernel: 0 generic (per-population constants
+                               from the parameter block), 1..3 compiled for the
+                               stencils {5,12,14,17,21,26}, {1..6},
+                               {1,14,49,51,60,70} (FP32 storage)              */
+} rlbm_info;
+
+/* Create a lattice context.
+ *  st     stencil (copied); m = particle mass in units of T_R (m > 0);
+ *  tau    relaxation time in lattice steps (tau > 1/2);
+ *  Nx,Ny  lattice size (>= 1 each);  dtype  population storage;
+ *  cuda_stream  a cudaStream_t (NULL = legacy default stream), borrowed.
+ * Builds the stencil tables on the host (weights of Eq. 52 in binary128),
+ * uploads them and allocates two population buffers.  *out is set only on
+ * success.  Errors: EINVAL, ENOQUAD, ENOTSUP, ENOMEM, ECUDA. */
+rlbm_status rlbm_create(const rlbm_stencil* st, double m, double tau, int Nx, int Ny,
+                        rlbm_dtype dtype, void* cuda_stream, rlbm_ctx** out);
+
+/* Set f_i = f_i^eq(n, U, T) everywhere (Eq. 16) and t = 0.  Host arrays of
+ * Nx*Ny doubles: density n > 0, three-velocity (ux, uy) with ux^2+uy^2 < 1,
+ * temperature T > 0 (validated on the host; EINVAL names the first bad site).
+ * Copies the fields to the device (blocking on the context stream). */
+rlbm_status rlbm_init(rlbm_ctx* ctx, const double* n, const double* ux, const double* uy,
+                      const double* T);
+
+/* Same as rlbm_init with the four fields already in device memory (each
+ * Nx*Ny doubles, row-major).  Asynchronous on the context stream; no
+ * validation beyond the device-side physicality flags. */
+rlbm_status rlbm_init_device(rlbm_ctx* ctx, const double* n, const double* ux, const double* uy,
+                             const double* T);
+
+/* Advance nsteps >= 0 time steps (Eq. 49 applied nsteps times).
+ * Asynchronous on the context stream: returns after enqueueing. */
+rlbm_status rlbm_step(rlbm_ctx* ctx, int nsteps);
+
+/* Macroscopic fields of the current pre-collision state f(., t).
+ * mask selects fields (bits below); out receives, in bit order, one
+ * Nx*Ny plane per scalar (RLBM_M_NVEC: 3 planes N^0,N^x,N^y; RLBM_M_TMN: 6
+ * planes T^00,T^0x,T^0y,T^xx,T^xy,T^yy).  Synchronises the stream, then
+ * reports any sticky device error. */
+#define RLBM_M_N    0x01u  /* n = U_a N^a (Eq. 19)             */
+#define RLBM_M_UX   0x02u  /* u_x = U^x / U^0                  */
+#define RLBM_M_UY   0x04u  /* u_y = U^y / U^0                  */
+#define RLBM_M_T    0x08u  /* temperature (Eq. 28)             */
+#define RLBM_M_E    0x10u  /* energy density e (Eq. 20)        */
+#define RLBM_M_NVEC 0x20u  /* N^a, 3 planes                    */
+#define RLBM_M_TMN  0x40u  /* T^ab, 6 planes                   */
+rlbm_status rlbm_moments(rlbm_ctx* ctx, double* out, unsigned mask);
+
+/* Number of doubles rlbm_moments writes for a mask (0 on a NULL ctx). */
+size_t rlbm_moments_size(const rlbm_ctx* ctx, unsigned mask);
+
+/* Block until the context stream is idle; report sticky device errors. */
+rlbm_status rlbm_sync(rlbm_ctx* ctx);
+
+/* Fill *info.  Never touches the device. */
+rlbm_status rlbm_get_info(const rlbm_ctx* ctx, rlbm_info* info);
+
+/* Human-readable description of the last failure on ctx (or of the last
+ * failed rlbm_create when ctx is NULL).  Valid until the next call. */
+const char* rlbm_last_error(const rlbm_ctx* ctx);
+
+/* Release the context and its device memory (synchronises its stream). */
+void rlbm_destroy(rlbm_ctx* ctx);
+
+/* ---- host-only helpers (no device needed) ---------------------------- */
+
+/* Weights of the six groups at (m, v0) from Eq. 52, solved in binary128 and
+ * rounded to FP64.  Returns ENOQUAD if the system is singular; the weights
+ * are returned whatever their sign. */
+rlbm_status rlbm_quadrature_weights(const int* groups, int ngroups, double m, double v0,
+                                    double* w_out);
+
+/* The widest v0 interval (lo, hi) in which all six weights are positive, and
+ * its count of disjoint positive intervals; ENOQUAD if there is none. */
+rlbm_status rlbm_quadrature_window(const int* groups, int ngroups, double m, double* lo,
+                                   double* hi, int* nwindows);
+
+/* R(zeta) = K1(zeta)/K2(zeta) from the library's piecewise-polynomial tables,
+ * evaluated on the host by the same formulas the kernels use (precision 64
+ * or 32).  For validation of the tables. */
+double rlbm_bessel_ratio(double zeta, int precision);
+
+/* Library version string. */
+const char* rlbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RLBM_H */

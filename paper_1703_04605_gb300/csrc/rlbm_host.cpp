@@ -1,0 +1,415 @@
+// C ABI of the library (include/rlbm.h): context lifetime, validation,
+// device buffers, launches and error reporting.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+
+#include "rlbm_fused_launch.h"
+#include "rlbm_stencil.h"
+
+using namespace rlbm;
+
+struct rlbm_ctx {
+  int Nx = 0, Ny = 0;
+  rlbm_dtype dtype = RLBM_F32;
+  cudaStream_t stream = nullptr;
+  double m = 0, tau = 0;
+  StencilBuild sb;
+  int Q = 0, qb = 0;
+  long long pitch = 0, plane = 0;
+  size_t elem = 0;
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;              // buffer holding S_t
+  long long t = 0;
+  unsigned* d_err = nullptr;
+  double* d_rt64 = nullptr;
+  float* d_rt32 = nullptr;
+  double* d_fields = nullptr;   // 4 planes for rlbm_init
+  double* d_out = nullptr;      // read-out planes
+  size_t out_cap = 0;
+  size_t device_bytes = 0;
+  bool initialised = false;
+  bool host_init = false;   // rlbm_init in progress (it sets the reference itself)
+  std::unique_ptr<StepParams<double>> p64;
+  std::unique_ptr<StepParams<float>> p32;
+  int fused = 0;                 // 1: G5.. (M1), 2: G1..G6, 3: E5; 0: generic kernel
+  std::unique_ptr<FusedParams> fp;
+  std::string last_error;
+};
+
+static thread_local std::string g_create_error;
+
+static rlbm_status fail(rlbm_ctx* c, rlbm_status s, const std::string& msg) {
+  if (c) c->last_error = msg;
+  else g_create_error = msg;
+  return s;
+}
+
+static rlbm_status cuda_fail(rlbm_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, RLBM_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+static void release(rlbm_ctx* c) {
+  if (!c) return;
+  if (c->buf[0]) cudaStreamSynchronize(c->stream);
+  for (void* p : {c->buf[0], c->buf[1], (void*)c->d_err, (void*)c->d_rt64, (void*)c->d_rt32,
+                  (void*)c->d_fields, (void*)c->d_out})
+    if (p) cudaFree(p);
+}
+
+template <typename CT>
+static void fill_params(rlbm_ctx* c, StepParams<CT>* p) {
+  std::memset(p, 0, sizeof(*p));
+  p->Nx = c->Nx;
+  p->Ny = c->Ny;
+  p->Q = c->Q;
+  p->halo = c->sb.halo;
+  p->pitch = c->pitch;
+  p->plane = c->plane;
+  p->inv_tau = 1.0 / c->tau;
+  p->v0 = c->sb.v0;
+  p->sc = c->sb.sc;
+  p->rt64 = c->d_rt64;
+  p->rt32 = c->d_rt32;
+  p->err = c->d_err;
+  fill_pop_table<CT>(c->sb, c->Nx, c->Ny, &p->pt);
+}
+
+static HL split(double x) {
+  HL h;
+  h.hi = (float)x;
+  h.lo = (float)(x - (double)h.hi);
+  return h;
+}
+
+// Which stencil-specialised kernel serves this context (0: none).
+static int fused_kind(const rlbm_ctx* c) {
+  if (c->dtype != RLBM_F32) return 0;
+  auto same = [&](const int* g) {
+    for (int k = 0; k < 6; ++k)
+      if (c->sb.groups[k] != g[k]) return false;
+    return true;
+  };
+  int kind = 0;
+  const Folded* F = nullptr;
+  if (same(StencilM1::groups)) kind = 1, F = &StencilM1::F;
+  else if (same(StencilG16::groups)) kind = 2, F = &StencilG16::F;
+  else if (same(StencilE5::groups)) kind = 3, F = &StencilE5::F;
+  if (!kind || F->Q != c->Q || F->halo != c->sb.halo) return 0;
+  // the compiled population order must be the host's (same storage planes)
+  for (int i = 0; i < F->Q; ++i) {
+    const FoldedPop& fp = c->sb.pops[i];
+    if (fp.nx != F->nx[i] || fp.ny != F->ny[i] || fp.group != F->grp[i] || fp.mult != F->mult[i]) return 0;
+  }
+  const int halo = F->halo;
+  // the kernels wrap a source coordinate at most once
+  if (c->Nx < halo || c->Ny < halo) return 0;
+  return kind;
+}
+
+static void fill_fused(rlbm_ctx* c, double nref) {
+  FusedParams& f = *c->fp;
+  std::memset(&f, 0, sizeof f);
+  const StencilBuild& sb = c->sb;
+  f.Nx = c->Nx;
+  f.Ny = c->Ny;
+  f.pitch = c->pitch;
+  f.plane = c->plane;
+  f.inv_tau = (float)(1.0 / c->tau);
+  f.v0 = (float)sb.v0;
+  f.mb = (float)sb.mbar;
+  f.k21 = (float)sb.sc.k21;
+  f.mk32 = (float)sb.sc.mk32;
+  f.cb00_1 = (float)sb.sc.cb00_1;
+  f.mY = (float)sb.sc.mY;
+  f.cv_r = (float)sb.cv_r;
+  f.Rr = split(sb.sc.Rr);
+  const double N0r = nref * sb.mref1[0];
+  const double er = nref * sb.mref1[3];
+  const double pr = nref * sb.mref1[6];
+  f.nr = split(N0r);
+  f.yr = split(er / N0r);
+  for (int k = 0; k < 9; ++k) f.mref[k] = (float)(nref * sb.mref1[k]);
+  f.Rr64 = sb.sc.Rr;
+  f.hr64 = er + pr;
+  f.mb64 = sb.mbar;
+  f.nr64 = N0r;
+  for (int g = 0; g < 6; ++g) {
+    for (int q = 0; q < 5; ++q) f.gm[g][q] = split(sb.gm[g][q]);
+    for (int q = 0; q < 10; ++q) f.gf[g][q] = split(sb.gf[g][q]);
+  }
+  f.rt64 = c->d_rt64;
+  f.rt32 = c->d_rt32;
+  f.err = c->d_err;
+}
+
+// Reference density of the FP32 deviation storage (see StepParams).
+static void set_reference(rlbm_ctx* c, double nref) {
+  if (c->dtype == RLBM_F64) return;
+  for (StepParams<double>* p : {c->p64.get()}) {
+    p->nref = nref;
+    p->b0ref = nref * c->sb.b0ref1;
+    for (int k = 0; k < 9; ++k) p->mref[k] = nref * c->sb.mref1[k];
+  }
+  StepParams<float>* q = c->p32.get();
+  q->nref = nref;
+  q->b0ref = nref * c->sb.b0ref1;
+  for (int k = 0; k < 9; ++k) q->mref[k] = nref * c->sb.mref1[k];
+  if (c->fused) fill_fused(c, nref);
+}
+
+static rlbm_status check_device_error(rlbm_ctx* c) {
+  unsigned h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, c->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "device synchronisation");
+  if (h) {
+    cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream);
+    cudaStreamSynchronize(c->stream);
+    std::string msg = "non-physical site(s):";
+    if (h & ERR_LANDAU) msg += " Landau frame failed or |u| >= 1;";
+    if (h & ERR_DENSITY) msg += " n <= 0;";
+    if (h & ERR_EOS) msg += " e/n <= m or T <= 0;";
+    if (h & ERR_ZETA) msg += " zeta = m/T invalid;";
+    return fail(c, RLBM_ENONPHYS, msg);
+  }
+  return RLBM_OK;
+}
+
+extern "C" {
+
+const char* rlbm_version(void) { return "rlbm-gb300 0.1 (sm_103a)"; }
+
+rlbm_status rlbm_create(const rlbm_stencil* st, double m, double tau, int Nx, int Ny,
+                        rlbm_dtype dtype, void* cuda_stream, rlbm_ctx** out) {
+  if (!out) return fail(nullptr, RLBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (Nx < 1 || Ny < 1) return fail(nullptr, RLBM_EINVAL, "Nx and Ny must be >= 1");
+  if (!(tau > 0.5) || !std::isfinite(tau)) return fail(nullptr, RLBM_EINVAL, "tau must exceed 1/2");
+  if (dtype != RLBM_F64 && dtype != RLBM_F32 && dtype != RLBM_BF16_DEV)
+    return fail(nullptr, RLBM_EINVAL, "unknown dtype");
+  if (dtype == RLBM_BF16_DEV) return fail(nullptr, RLBM_ENOTSUP, "BF16 deviation storage not built");
+  std::unique_ptr<rlbm_ctx> c(new (std::nothrow) rlbm_ctx);
+  if (!c) return fail(nullptr, RLBM_ENOMEM, "host allocation failed");
+  std::string err;
+  rlbm_status s = build_stencil(st, m, &c->sb, &err);
+  if (s != RLBM_OK) return fail(nullptr, s, err);
+  c->Nx = Nx;
+  c->Ny = Ny;
+  c->dtype = dtype;
+  c->m = m;
+  c->tau = tau;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->Q = (int)c->sb.pops.size();
+  c->qb = 0;
+  for (int q : QBUCKETS)
+    if (c->Q <= q) {
+      c->qb = q;
+      break;
+    }
+  if (!c->qb) return fail(nullptr, RLBM_ENOTSUP, "too many populations");
+  c->elem = (dtype == RLBM_F64) ? sizeof(double) : sizeof(float);
+  c->pitch = ((long long)Nx + 31) / 32 * 32;
+  c->plane = c->pitch * Ny;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) return fail(nullptr, RLBM_ECUDA, "no CUDA device available");
+  const size_t fbytes = (size_t)c->Q * (size_t)c->plane * c->elem;
+  for (int b = 0; b < 2; ++b) {
+    e = cudaMalloc(&c->buf[b], fbytes);
+    if (e != cudaSuccess) {
+      release(c.get());
+      return fail(nullptr, RLBM_ENOMEM, "population buffers: " + std::string(cudaGetErrorString(e)));
+    }
+  }
+  const auto& t64 = ratio_table64();
+  const auto& t32 = ratio_table32();
+  const size_t nsite = (size_t)Nx * Ny;
+  bool ok = cudaMalloc(&c->d_err, sizeof(unsigned)) == cudaSuccess &&
+            cudaMalloc(&c->d_rt64, t64.size() * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->d_rt32, t32.size() * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&c->d_fields, 4 * nsite * sizeof(double)) == cudaSuccess;
+  if (!ok) {
+    release(c.get());
+    return fail(nullptr, RLBM_ENOMEM, "device allocation failed");
+  }
+  c->device_bytes = 2 * fbytes + sizeof(unsigned) + t64.size() * 8 + t32.size() * 4 + 4 * nsite * 8;
+  e = cudaMemcpy(c->d_rt64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_rt32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(unsigned));
+  if (e != cudaSuccess) {
+    release(c.get());
+    return fail(nullptr, RLBM_ECUDA, std::string("upload: ") + cudaGetErrorString(e));
+  }
+  c->p64.reset(new StepParams<double>);
+  fill_params<double>(c.get(), c->p64.get());
+  if (dtype != RLBM_F64) {
+    c->p32.reset(new StepParams<float>);
+    fill_params<float>(c.get(), c->p32.get());
+  }
+  c->fused = fused_kind(c.get());
+  if (c->fused) {
+    c->fp.reset(new FusedParams);
+    fill_fused(c.get(), 1.0);
+  }
+  *out = c.release();
+  return RLBM_OK;
+}
+
+rlbm_status rlbm_init_device(rlbm_ctx* c, const double* n, const double* ux, const double* uy,
+                             const double* T) {
+  if (!c) return RLBM_EINVAL;
+  if (!n || !ux || !uy || !T) return fail(c, RLBM_EINVAL, "NULL field pointer");
+  FieldPtrs fp{n, ux, uy, T};
+  if (!c->host_init) set_reference(c, 1.0);
+  cudaError_t e = launch_init(c->dtype, *c->p64, fp, c->buf[0], c->buf[1], c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "init launch");
+  c->cur = 0;
+  c->t = 0;
+  c->initialised = true;
+  return RLBM_OK;
+}
+
+rlbm_status rlbm_init(rlbm_ctx* c, const double* n, const double* ux, const double* uy,
+                      const double* T) {
+  if (!c) return RLBM_EINVAL;
+  if (!n || !ux || !uy || !T) return fail(c, RLBM_EINVAL, "NULL field pointer");
+  const size_t N = (size_t)c->Nx * c->Ny;
+  for (size_t s = 0; s < N; ++s) {
+    const double v2 = ux[s] * ux[s] + uy[s] * uy[s];
+    if (!(n[s] > 0) || !(T[s] > 0) || !(v2 < 1) || !std::isfinite(n[s]) || !std::isfinite(T[s])) {
+      char b[160];
+      std::snprintf(b, sizeof b, "invalid field at site %zu (x=%zu, y=%zu): need n>0, T>0, |u|<1",
+                    s, s % (size_t)c->Nx, s / (size_t)c->Nx);
+      return fail(c, RLBM_EINVAL, b);
+    }
+  }
+  double nsum = 0;
+  for (size_t s = 0; s < N; ++s) nsum += n[s];
+  set_reference(c, nsum / (double)N);
+  const double* src[4] = {n, ux, uy, T};
+  for (int k = 0; k < 4; ++k) {
+    cudaError_t e = cudaMemcpyAsync(c->d_fields + k * N, src[k], N * sizeof(double),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "field upload");
+  }
+  c->host_init = true;
+  rlbm_status s = rlbm_init_device(c, c->d_fields, c->d_fields + N, c->d_fields + 2 * N,
+                                   c->d_fields + 3 * N);
+  c->host_init = false;
+  if (s != RLBM_OK) return s;
+  return check_device_error(c);
+}
+
+rlbm_status rlbm_step(rlbm_ctx* c, int nsteps) {
+  if (!c) return RLBM_EINVAL;
+  if (nsteps < 0) return fail(c, RLBM_EINVAL, "nsteps < 0");
+  if (!c->initialised) return fail(c, RLBM_EINVAL, "rlbm_init has not been called");
+  for (int k = 0; k < nsteps; ++k) {
+    const void* fin = c->buf[c->cur];
+    void* fout = c->buf[1 - c->cur];
+    cudaError_t e;
+    if (c->dtype == RLBM_F64) e = launch_step_f64(*c->p64, fin, fout, c->qb, c->stream);
+    else if (c->fused == 1) e = launch_fused<StencilM1>(*c->fp, fin, fout, c->stream);
+    else if (c->fused == 2) e = launch_fused<StencilG16>(*c->fp, fin, fout, c->stream);
+    else if (c->fused == 3) e = launch_fused<StencilE5>(*c->fp, fin, fout, c->stream);
+    else e = launch_step_f32(*c->p32, fin, fout, c->qb, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
+    c->cur = 1 - c->cur;
+    ++c->t;
+  }
+  return RLBM_OK;
+}
+
+size_t rlbm_moments_size(const rlbm_ctx* c, unsigned mask) {
+  if (!c) return 0;
+  size_t planes = 0;
+  for (unsigned b : {RLBM_M_N, RLBM_M_UX, RLBM_M_UY, RLBM_M_T, RLBM_M_E})
+    if (mask & b) ++planes;
+  if (mask & RLBM_M_NVEC) planes += 3;
+  if (mask & RLBM_M_TMN) planes += 6;
+  return planes * (size_t)c->Nx * c->Ny;
+}
+
+rlbm_status rlbm_moments(rlbm_ctx* c, double* out, unsigned mask) {
+  if (!c) return RLBM_EINVAL;
+  if (!out) return fail(c, RLBM_EINVAL, "out is NULL");
+  if (!c->initialised) return fail(c, RLBM_EINVAL, "rlbm_init has not been called");
+  if (mask & ~0x7Fu) return fail(c, RLBM_EINVAL, "unknown mask bits");
+  const size_t need = rlbm_moments_size(c, mask);
+  if (need == 0) return RLBM_OK;
+  if (need > c->out_cap) {
+    if (c->d_out) cudaFree(c->d_out);
+    c->d_out = nullptr;
+    c->out_cap = 0;
+    cudaError_t e = cudaMalloc(&c->d_out, need * sizeof(double));
+    if (e != cudaSuccess) return fail(c, RLBM_ENOMEM, "read-out buffer");
+    c->out_cap = need;
+  }
+  MomentOut mo{c->d_out, mask};
+  cudaError_t e = launch_moments(c->dtype, *c->p64, c->buf[1 - c->cur], mo, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "moments launch");
+  e = cudaMemcpyAsync(out, c->d_out, need * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "read-out copy");
+  return check_device_error(c);
+}
+
+rlbm_status rlbm_sync(rlbm_ctx* c) {
+  if (!c) return RLBM_EINVAL;
+  return check_device_error(c);
+}
+
+rlbm_status rlbm_get_info(const rlbm_ctx* c, rlbm_info* info) {
+  if (!c || !info) return RLBM_EINVAL;
+  std::memset(info, 0, sizeof(*info));
+  info->Nx = c->Nx;
+  info->Ny = c->Ny;
+  info->Q = c->Q;
+  info->halo = c->sb.halo;
+  info->dtype = c->dtype;
+  info->m = c->m;
+  info->tau = c->tau;
+  info->v0 = c->sb.v0;
+  for (int k = 0; k < 6; ++k) info->w_group[k] = c->sb.w_group[k];
+  info->t = c->t;
+  info->bytes_per_site = 2 * (size_t)c->Q * c->elem;
+  info->extra_bytes_per_site = 0;
+  info->device_bytes = c->device_bytes + c->out_cap * sizeof(double);
+  info->kernel = c->fused;
+  return RLBM_OK;
+}
+
+const char* rlbm_last_error(const rlbm_ctx* c) {
+  return c ? c->last_error.c_str() : g_create_error.c_str();
+}
+
+void rlbm_destroy(rlbm_ctx* c) {
+  if (!c) return;
+  release(c);
+  delete c;
+}
+
+rlbm_status rlbm_quadrature_weights(const int* groups, int ngroups, double m, double v0,
+                                    double* w_out) {
+  if (!groups || ngroups != 6 || !w_out || !(m > 0) || !(v0 > 0)) return RLBM_EINVAL;
+  for (int k = 0; k < 6; ++k)
+    if (groups[k] < 1 || groups[k] > 84) return RLBM_EINVAL;
+  return quadrature_weights(groups, m, v0, w_out) ? RLBM_OK : RLBM_ENOQUAD;
+}
+
+rlbm_status rlbm_quadrature_window(const int* groups, int ngroups, double m, double* lo, double* hi,
+                                   int* nwindows) {
+  if (!groups || ngroups != 6 || !lo || !hi || !(m > 0)) return RLBM_EINVAL;
+  for (int k = 0; k < 6; ++k)
+    if (groups[k] < 1 || groups[k] > 84) return RLBM_EINVAL;
+  const int n = quadrature_window(groups, m, lo, hi);
+  if (nwindows) *nwindows = n;
+  return n > 0 ? RLBM_OK : RLBM_ENOQUAD;
+}
+
+double rlbm_bessel_ratio(double zeta, int precision) { return ratio_eval_host(zeta, precision); }
+
+}  // extern "C"

@@ -1,0 +1,151 @@
+// Internal layout shared by the host library (rlbm_host.cpp) and the CUDA
+// kernels (rlbm_kernels.cuh).  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/rlbm.h"
+
+namespace rlbm {
+
+// Largest folded stencil the kernels are compiled for.
+constexpr int QMAX = 96;
+// Population-count buckets with compiled kernels (register arrays of QB).
+constexpr int QBUCKETS[] = {40, 64, 80, 96};
+
+// Second-order polynomials that survive in 2D (U^z = 0), in this order:
+//   0: J^(0)  1: J_0  2: J_x  3: J_y  4: J_00  5: J_0x  6: J_0y
+//   7: J_xx = (p_y^2 - p_z^2)/(2E)   8: J_yy = (-2p_x^2 + p_y^2 + p_z^2)/(2 sqrt3 E)
+//   9: J_xy
+constexpr int NJ = 10;
+
+// Piecewise-polynomial tables of R(zeta) = K1(zeta)/K2(zeta).  zeta in
+// [2^RT_EMIN, 2^RT_EMAX) is split into octaves and each octave into
+// RT_SEG equal mantissa slices; each slice holds a polynomial in the local
+// variable x in [-1, 1] (monomial coefficients, lowest degree first).
+constexpr int RT_EMIN = -16;
+constexpr int RT_EMAX = 16;
+constexpr int RT_SEG = 8;                                  // slices per octave (2^3)
+constexpr int RT_NSEG = (RT_EMAX - RT_EMIN) * RT_SEG;
+constexpr int RT_NC64 = 11;                                // degree 10
+constexpr int RT_NC32 = 6;                                 // degree 5
+
+// Constants of App. A and B at mbar (rounded once from binary128).
+// Derived forms used by the kernels (all exact rearrangements of App. B):
+//   b0  = R/mbar
+//   b_0 = (U0 - k21 R)/A                = (dU - k21 (R - Rr)) iA
+//   b_a = U_a / B
+//   b00 = (mbar r32 U0^2 + cb00_1 U0 + R Y - T)/(sqrt3 C)
+//       = (F + dU (2 mbar r32 + cb00_1) + dU^2 mbar r32) i3C,
+//         F = (mbar + Y)(R - Rr) + 3 (T - 1)
+//   b0a = (mbar r32 U0 - mbar k32) U_a / D = (G + mbar r32 dU) U_a iD,
+//         G = mbar (R - Rr) + 4 (T - 1)
+//   bxx = mbar r32 U_y^2 i2E,  byy = mbar r32 (U_y^2 - 2 U_x^2) i23E,
+//   bxy = mbar r32 U_x U_y iE
+// with dU = U0 - 1, r32 = K3/K2(zeta) = R + 4 T/mbar, Rr = R(mbar) = 1/k21
+// (T_R = 1), F and G vanishing at T = T_R because b_00 = b_0 = 0 for the
+// rest-frame weight itself.  The differences R - Rr and T - 1 are formed in
+// FP64 so that the FP32 path keeps b_00, b_0 and b_0a accurate near T_R.
+struct SiteConsts {
+  double mbar, inv_m;
+  double k21;     // K2/K1 (mbar)
+  double k32;     // K3/K2 (mbar)
+  double Rr;      // K1/K2 (mbar) = 1/k21
+  double A, B, C, D, E;
+  double iA, iB, i3C, iD, i2E, i23E, iE;
+  double cb00_1;  // U_0 coefficient of b_00: 3 (1/X - 1)
+  double Y;       // mbar fraction of b_00
+  double mY;      // mbar + Y
+  double mk32;    // mbar k32
+};
+
+// Per-population constants of one folded stencil.  Entries i >= Q are zero.
+template <typename CT>
+struct PopTable {
+  int dxm[QMAX], dym[QMAX];   // displacement reduced mod Nx, Ny (in [0, N))
+  CT mom[9][QMAX];            // p0, px, py, p0p0, p0px, p0py, pxpx, pxpy, pypy
+  CT cj[NJ][QMAX];            // w_i J_k(p_i)
+  CT vx[QMAX], vy[QMAX];      // p^x/p^0, p^y/p^0
+};
+
+// FP32 storage holds d_i = f_i - r_i, r_i = nref w_i K1/K2(mbar)/mbar: the
+// rest-frame equilibrium at density nref and T = T_R (all b^(k>0) vanish
+// there).  r_i is uniform in space, so streaming and the Anderson-Witting
+// relaxation act on d_i exactly as on f_i (with f^eq_i - r_i in place of
+// f^eq_i); the moments of r_i are added back in FP64.  FP64 storage holds f_i
+// (nref = 0).
+template <typename CT>
+struct StepParams {
+  int Nx, Ny, Q, halo;
+  long long pitch, plane;     // elements
+  double inv_tau, v0;
+  double nref;                // reference density (0: plain f_i storage)
+  double b0ref;               // nref K1/K2(mbar)/mbar: n b^(0) of r_i
+  double mref[9];             // moments of r_i (same order as PopTable::mom)
+  SiteConsts sc;
+  const double* rt64;         // RT_NSEG * RT_NC64
+  const float* rt32;          // RT_NSEG * RT_NC32
+  unsigned* err;              // sticky device error bits
+  PopTable<CT> pt;
+};
+
+// Parameters of the stencil-specialised FP32 kernels (rlbm_fused.cuh).
+// A constant as the sum of two FP32 numbers (about 48 significant bits).
+struct HL {
+  float hi, lo;
+};
+
+struct FusedParams {
+  int Nx, Ny;
+  long long pitch, plane;
+  float inv_tau, v0;
+  // FP32 constants of the projection formulas (deviation-level terms only)
+  float mb, k21, mk32, cb00_1, mY;
+  float cv_r;          // specific heat per particle at T_R (Newton start)
+  HL Rr;               // R(mbar) = K1/K2(mbar)
+  HL nr;               // reference density
+  HL yr;               // reference energy per particle e_r/n_r
+  float mref[9];       // reference moments (FP32 copy, Newton start only)
+  double Rr64, hr64, mb64, nr64;
+  HL gm[6][5];         // per group: P0, P0^2, Pv, P0 Pv, Pv^2 (P0 = m gamma, Pv = m gamma v0)
+  HL gf[6][10];        // per group: a0 a1 a4 a7 a8 bx2 bx5 q78 qy7 q9 (see host)
+  const double* rt64;
+  const float* rt32;
+  unsigned* err;
+};
+
+// Device error bits (OR-ed into *err).
+enum : unsigned {
+  ERR_LANDAU = 1u,   // Landau frame: non-finite or |u| >= 1
+  ERR_DENSITY = 2u,  // n <= 0 or non-finite
+  ERR_EOS = 4u,      // e/n <= m or T <= 0 or non-finite
+  ERR_ZETA = 8u,     // zeta outside the tabulated range
+};
+
+// Fields read by the init kernel and written by the moments kernel.
+struct FieldPtrs {
+  const double* n;
+  const double* ux;
+  const double* uy;
+  const double* T;
+};
+
+struct MomentOut {
+  double* out;           // device buffer, planes of Nx*Ny doubles
+  unsigned mask;
+};
+
+// Kernel launchers (rlbm_kernels_*.cu).
+cudaError_t launch_step_f64(const StepParams<double>& p, const void* fin, void* fout, int qb,
+                            cudaStream_t s);
+cudaError_t launch_step_f32(const StepParams<float>& p, const void* fin, void* fout, int qb,
+                            cudaStream_t s);
+cudaError_t launch_init(rlbm_dtype dt, const StepParams<double>& p, FieldPtrs f, void* cur,
+                        void* prev, cudaStream_t s);
+cudaError_t launch_moments(rlbm_dtype dt, const StepParams<double>& p, const void* prev,
+                           MomentOut mo, cudaStream_t s);
+
+}  // namespace rlbm

@@ -1,0 +1,65 @@
+// Host-side construction of a second-order stencil (Sec. III C-D, App. A-C)
+// and of the R(zeta) tables.  Internal to the library.
+#pragma once
+
+#include <array>
+#include <string>
+#include <vector>
+
+#include "rlbm_internal.h"
+
+namespace rlbm {
+
+// One population of the stencil folded onto the xy plane.
+struct FoldedPop {
+  int group;        // index 0..5 into the stencil's group list
+  int nx, ny;       // displacement per step (lattice cells)
+  int nz2;          // n_z^2 of the merged +-n_z pair
+  int mult;         // 1 (n_z = 0) or 2 (merged pair)
+};
+
+struct StencilBuild {
+  int groups[6];
+  double mbar, v0;
+  double w_group[6];          // Eq. 52 weights (FP64)
+  std::vector<FoldedPop> pops;
+  // per population, rounded once from binary128: mom[9] (p0, px, py, p0p0,
+  // p0px, p0py, pxpx, pxpy, pypy), cj[10] = w_i J_k(p_i), vx, vy
+  std::vector<std::array<double, 21>> popc;
+  // the reference r_i = w_i K1/K2(mbar)/mbar (unit density, rest, T = T_R):
+  // its J^(0) coefficient and its nine moments, rounded once from binary128
+  double b0ref1;
+  double mref1[9];
+  // per group constants of the stencil-specialised kernels (see rlbm_fused.cuh):
+  // gm = P0, P0^2, Pv, P0 Pv, Pv^2 with P0 = m gamma_k, Pv = m gamma_k v0;
+  // gf = a0 a1 a4 a7 a8 bx2 bx5 q78 qy7 q9 (App. A/B normalisations folded in)
+  double gm[6][5];
+  double gf[6][10];
+  double cv_r;          // 3 - mbar^2 R'(mbar): specific heat per particle at T_R
+  int halo;
+  SiteConsts sc;
+};
+
+// Vectors of group gid of Table I (full-symmetric orbit of its generator).
+std::vector<std::array<int, 3>> group_orbit(int gid);
+
+// Weights of Eq. 52 at (m, v0) in extended precision; false if singular.
+bool quadrature_weights(const int* groups, double m, double v0, double* w);
+
+// Widest positive-weight interval; returns number of disjoint windows (0: none).
+int quadrature_window(const int* groups, double m, double* lo, double* hi);
+
+// Full build: validates, solves weights, folds, App. A constants.
+// Returns RLBM_OK or an error with a message.
+rlbm_status build_stencil(const rlbm_stencil* st, double m, StencilBuild* out, std::string* err);
+
+// Per-population constant table for the kernels (CT = float or double).
+template <typename CT>
+void fill_pop_table(const StencilBuild& sb, int Nx, int Ny, PopTable<CT>* pt);
+
+// R(zeta) tables (built once per process).
+const std::vector<double>& ratio_table64();
+const std::vector<float>& ratio_table32();
+double ratio_eval_host(double z, int precision);
+
+}  // namespace rlbm

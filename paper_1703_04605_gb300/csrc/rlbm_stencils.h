@@ -1,0 +1,129 @@
+// Table I (App. C) and the folded second-order stencils known at compile
+// time.  Usable from host and device code (constexpr).
+#pragma once
+
+#include <utility>
+
+namespace rlbm {
+
+// Generating vector (a >= b >= c >= 0) of the 84 full-symmetric groups of
+// Table I, in table order (row k-1 is group k).
+struct TableI {
+  int v[84][3];
+};
+constexpr TableI kTableI = {{
+    {0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {1, 1, 1}, {2, 0, 0}, {2, 1, 0}, {2, 2, 0}, {2, 1, 1},
+    {2, 2, 1}, {2, 2, 2}, {3, 0, 0}, {3, 1, 0}, {3, 2, 0}, {3, 3, 0}, {3, 1, 1}, {3, 2, 1},
+    {3, 2, 2}, {3, 3, 1}, {3, 3, 2}, {3, 3, 3}, {4, 0, 0}, {4, 1, 0}, {4, 2, 0}, {4, 3, 0},
+    {4, 4, 0}, {4, 1, 1}, {4, 2, 1}, {4, 3, 1}, {4, 4, 1}, {4, 2, 2}, {4, 3, 2}, {4, 4, 2},
+    {4, 3, 3}, {4, 4, 3}, {4, 4, 4}, {5, 0, 0}, {5, 1, 0}, {5, 2, 0}, {5, 3, 0}, {5, 4, 0},
+    {5, 5, 0}, {5, 1, 1}, {5, 2, 1}, {5, 3, 1}, {5, 4, 1}, {5, 5, 1}, {5, 2, 2}, {5, 3, 2},
+    {5, 4, 2}, {5, 5, 2}, {5, 3, 3}, {5, 4, 3}, {5, 5, 3}, {5, 4, 4}, {5, 5, 4}, {5, 5, 5},
+    {6, 0, 0}, {6, 1, 0}, {6, 2, 0}, {6, 3, 0}, {6, 4, 0}, {6, 5, 0}, {6, 6, 0}, {6, 1, 1},
+    {6, 2, 1}, {6, 3, 1}, {6, 4, 1}, {6, 5, 1}, {6, 6, 1}, {6, 2, 2}, {6, 3, 2}, {6, 4, 2},
+    {6, 5, 2}, {6, 6, 2}, {6, 3, 3}, {6, 4, 3}, {6, 5, 3}, {6, 6, 3}, {6, 4, 4}, {6, 5, 4},
+    {6, 6, 4}, {6, 5, 5}, {6, 6, 5}, {6, 6, 6}}};
+
+constexpr int kMaxFolded = 160;
+
+// Folded populations of a six-group stencil: the full-symmetric orbit of each
+// group with (nx, ny, +nz) and (nx, ny, -nz) merged.  Order: group by group,
+// inside a group by (nx, ny, |nz|) lexicographically -- the host builder uses
+// the same order.
+struct Folded {
+  int Q;
+  int halo;
+  int grp[kMaxFolded];
+  int nx[kMaxFolded], ny[kMaxFolded], nz2[kMaxFolded], mult[kMaxFolded];
+};
+
+constexpr Folded fold_stencil(int g0, int g1, int g2, int g3, int g4, int g5) {
+  Folded F{};
+  const int gs[6] = {g0, g1, g2, g3, g4, g5};
+  int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  F.Q = 0;
+  F.halo = 0;
+  for (int g = 0; g < 6; ++g) {
+    const int* b = kTableI.v[gs[g] - 1];
+    // collect distinct (nx, ny, |nz|) with multiplicity = number of distinct
+    // 3D vectors mapping to it
+    int key[48][3] = {};
+    int vec[48][3] = {};
+    int nvec = 0;
+    for (int p = 0; p < 6; ++p)
+      for (int s = 0; s < 8; ++s) {
+        int v[3] = {0, 0, 0};
+        for (int a = 0; a < 3; ++a) v[a] = ((s >> a) & 1 ? -1 : 1) * b[perms[p][a]];
+        bool seen = false;
+        for (int q = 0; q < nvec; ++q)
+          if (vec[q][0] == v[0] && vec[q][1] == v[1] && vec[q][2] == v[2]) seen = true;
+        if (!seen) {
+          vec[nvec][0] = v[0];
+          vec[nvec][1] = v[1];
+          vec[nvec][2] = v[2];
+          ++nvec;
+        }
+      }
+    int nkey = 0;
+    int mult[48] = {};
+    for (int q = 0; q < nvec; ++q) {
+      const int az = vec[q][2] < 0 ? -vec[q][2] : vec[q][2];
+      int found = -1;
+      for (int k = 0; k < nkey; ++k)
+        if (key[k][0] == vec[q][0] && key[k][1] == vec[q][1] && key[k][2] == az) found = k;
+      if (found < 0) {
+        key[nkey][0] = vec[q][0];
+        key[nkey][1] = vec[q][1];
+        key[nkey][2] = az;
+        mult[nkey] = 1;
+        ++nkey;
+      } else {
+        mult[found] += 1;
+      }
+    }
+    // lexicographic order of the keys
+    for (int i = 0; i < nkey; ++i)
+      for (int j = i + 1; j < nkey; ++j) {
+        bool less = key[j][0] < key[i][0] || (key[j][0] == key[i][0] && key[j][1] < key[i][1]) ||
+                    (key[j][0] == key[i][0] && key[j][1] == key[i][1] && key[j][2] < key[i][2]);
+        if (less) {
+          for (int a = 0; a < 3; ++a) {
+            const int t = key[i][a];
+            key[i][a] = key[j][a];
+            key[j][a] = t;
+          }
+          const int t = mult[i];
+          mult[i] = mult[j];
+          mult[j] = t;
+        }
+      }
+    for (int k = 0; k < nkey; ++k) {
+      F.grp[F.Q] = g;
+      F.nx[F.Q] = key[k][0];
+      F.ny[F.Q] = key[k][1];
+      F.nz2[F.Q] = key[k][2] * key[k][2];
+      F.mult[F.Q] = mult[k];
+      const int ax = key[k][0] < 0 ? -key[k][0] : key[k][0];
+      const int ay = key[k][1] < 0 ? -key[k][1] : key[k][1];
+      if (ax > F.halo) F.halo = ax;
+      if (ay > F.halo) F.halo = ay;
+      ++F.Q;
+    }
+  }
+  return F;
+}
+
+// Stencils with compiled fused kernels (group ids ascending).
+template <int G0, int G1, int G2, int G3, int G4, int G5>
+struct StencilDef {
+  static constexpr int groups[6] = {G0, G1, G2, G3, G4, G5};
+  static constexpr Folded F = fold_stencil(G0, G1, G2, G3, G4, G5);
+  static constexpr int Q = F.Q;
+  static constexpr int halo = F.halo;
+};
+
+using StencilM1 = StencilDef<5, 12, 14, 17, 21, 26>;    // m/T_R ~ 1
+using StencilG16 = StencilDef<1, 2, 3, 4, 5, 6>;        // m/T_R >~ 5 (Sec. III D example)
+using StencilE5 = StencilDef<1, 14, 49, 51, 60, 70>;    // m/T_R ~ 0.36 (Sec. IV, Fig. 5)
+
+}  // namespace rlbm

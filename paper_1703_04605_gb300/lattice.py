@@ -1,0 +1,99 @@
+"""Python handle on one lattice context of librlbm (marshalling only)."""
+import ctypes as C
+
+import numpy as np
+
+from . import _abi as A
+
+
+def _default_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+class Lattice:
+    """A periodic Nx x Ny lattice advanced by the library's CUDA kernels.
+
+    groups  six group ids of Table I; m = m/T_R; tau in lattice steps;
+    dtype   'f64' | 'f32' | 'bf16dev';  v0 = 0 picks the centre of the widest
+    positive-weight window.  stream: a cudaStream_t as int (default: torch's
+    current stream when torch sees a GPU, else the legacy default stream)."""
+
+    def __init__(self, groups, m, tau, Nx, Ny, dtype="f32", v0=0.0, stream=None):
+        L = A.load()
+        self._lib = L
+        self._ctx = C.c_void_p()
+        self._groups = A.int_array(groups)
+        st = A.Stencil(len(groups), self._groups, float(v0))
+        if stream is None:
+            stream = _default_stream()
+        A.check(L.rlbm_create(C.byref(st), float(m), float(tau), int(Nx), int(Ny), A.DTYPES[dtype],
+                              C.c_void_p(stream) if stream else None, C.byref(self._ctx)))
+        self.Nx, self.Ny = int(Nx), int(Ny)
+        self.dtype = dtype
+
+    # -- lifetime -----------------------------------------------------------
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            self._lib.rlbm_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls --------------------------------------------------------------
+    def _chk(self, status):
+        A.check(status, self._ctx)
+
+    def init(self, n, ux, uy, T):
+        """Host FP64 fields (anything convertible to [Ny, Nx] float64)."""
+        arrs = [np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), (self.Ny, self.Nx)))
+                for a in (n, ux, uy, T)]
+        ptrs = [a.ctypes.data_as(C.POINTER(C.c_double)) for a in arrs]
+        self._chk(self._lib.rlbm_init(self._ctx, *ptrs))
+
+    def init_device(self, n, ux, uy, T):
+        """Device fields: four contiguous CUDA float64 tensors of Nx*Ny elements."""
+        for t in (n, ux, uy, T):
+            if not (t.is_cuda and t.is_contiguous() and t.numel() == self.Nx * self.Ny):
+                raise ValueError("device fields must be contiguous CUDA tensors of Nx*Ny float64")
+        self._chk(self._lib.rlbm_init_device(self._ctx, *[C.c_void_p(t.data_ptr()) for t in (n, ux, uy, T)]))
+
+    def step(self, k=1):
+        self._chk(self._lib.rlbm_step(self._ctx, int(k)))
+
+    def sync(self):
+        self._chk(self._lib.rlbm_sync(self._ctx))
+
+    def moments(self, mask=A.M_N | A.M_UX | A.M_UY | A.M_T | A.M_E):
+        size = self._lib.rlbm_moments_size(self._ctx, mask)
+        out = np.empty(size, dtype=np.float64)
+        self._chk(self._lib.rlbm_moments(self._ctx, out.ctypes.data_as(C.POINTER(C.c_double)), mask))
+        res = {}
+        plane = 0
+        N = self.Nx * self.Ny
+        for bit, names in A.MASK_PLANES:
+            if mask & bit:
+                for nm in names:
+                    res[nm] = out[plane * N:(plane + 1) * N].reshape(self.Ny, self.Nx)
+                    plane += 1
+        return res
+
+    def info(self):
+        inf = A.Info()
+        self._chk(self._lib.rlbm_get_info(self._ctx, C.byref(inf)))
+        return {k: (list(getattr(inf, k)) if k == "w_group" else getattr(inf, k)) for k, _ in A.Info._fields_}
