@@ -150,6 +150,34 @@ const char* rlbm_last_error(const rlbm_ctx* ctx);
 /* Release the context and its device memory (synchronises its stream). */
 void rlbm_destroy(rlbm_ctx* ctx);
 
+/* ---- read-out without memory allocation -------------------------------
+ * The paper has no counterpart of this entry point; it serves callers that
+ * may not allocate device memory -- e.g. code running inside a host
+ * application that owns every allocation (a plugin handed device buffers),
+ * or under a memory manager that forbids cudaMalloc at the point of call.
+ *
+ * Computes the same fields as rlbm_moments, for FP64 populations the caller
+ * holds in device memory: f_dev = f_i(x, t) in the library's population
+ * order (groups ascending, inside a group (n_x, n_y) lexicographic), compact
+ * layout [Q][Ny][Nx] doubles.  The populations are read as they are (no
+ * streaming).  out_host receives the planes selected by mask (same layout as
+ * rlbm_moments).  groups/m/v0 describe the stencil as in rlbm_create
+ * (v0 > 0 required).  Runs on cuda_stream and synchronises it.
+ *
+ * Memory: allocates no device memory.  Its device scratch -- the error
+ * word, the R(zeta) table and the result staging -- is one static 8 MiB
+ * array that every GPU loading the library holds until exit; results larger
+ * than 1,045,728 doubles (planes x Nx x Ny) are rejected with RLBM_EINVAL.
+ * The first call on a device sets the array up (symbol address, table copy),
+ * so that call must come before any stream capture; the first call for a new
+ * stencil or lattice size builds host tables.  All calls share the array and
+ * it keeps the last call's contents (the error word is cleared per call):
+ * calls that overlap on the GPU, from any thread or stream, race.  Errors
+ * are described by rlbm_last_error(NULL). */
+rlbm_status rlbm_moments_noalloc(const int* groups, int ngroups, double m, double v0, int Nx, int Ny,
+                                 const double* f_dev, double* out_host, unsigned mask,
+                                 void* cuda_stream);
+
 /* ---- host-only helpers (no device needed) ---------------------------- */
 
 /* Weights of the six groups at (m, v0) from Eq. 52, solved in binary128 and

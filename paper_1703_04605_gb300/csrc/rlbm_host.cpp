@@ -42,6 +42,8 @@ struct rlbm_ctx {
 
 static thread_local std::string g_create_error;
 
+void rlbm::set_global_error(const std::string& msg) { g_create_error = msg; }
+
 static rlbm_status fail(rlbm_ctx* c, rlbm_status s, const std::string& msg) {
   if (c) c->last_error = msg;
   else g_create_error = msg;

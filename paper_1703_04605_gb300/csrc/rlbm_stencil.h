@@ -62,4 +62,7 @@ const std::vector<double>& ratio_table64();
 const std::vector<float>& ratio_table32();
 double ratio_eval_host(double z, int precision);
 
+// Message returned by rlbm_last_error(NULL) (defined with the C ABI).
+void set_global_error(const std::string& msg);
+
 }  // namespace rlbm
