@@ -16,10 +16,12 @@
 //    n = nref + n_d, e/n = y_r + y_d, T = 1 + T_d, R = R(mbar) + dR.  The
 //    FP32 deviations are small, so FP32 arithmetic on them loses nothing that
 //    the FP32 storage keeps;
-//  * FP64 is used in the Landau frame (one Newton correction with an FP64
-//    residual) and in the EOS (one FP64 Newton step with the FP64 R(zeta)
-//    table); the same R enters the EOS and the projections, which keeps the
-//    energy of f^eq equal to the Landau energy (Eq. 20, 28).
+//  * the Landau frame is solved in FP32 on the full moments (the velocity is
+//    well conditioned; the cancelling energy and density are formed from the
+//    deviation moments), and FP64 enters only the EOS: one FP64 Newton step
+//    with the FP64 R(zeta) table after the FP32 iterations.  The same R enters
+//    the EOS and the projections, which keeps the energy of f^eq equal to the
+//    Landau energy (Eq. 20, 28).
 #pragma once
 
 #include <utility>
@@ -104,8 +106,10 @@ __device__ __forceinline__ void fused_collide_all(std::integer_sequence<int, Is.
   (fused_collide<Def, Is>(d, c, a0, ax, ay, out, plane), ...);
 }
 
+// Five resident blocks of 128 threads (96 registers) for Q <= 64, four
+// (128 registers) for larger stencils, whose populations would spill.
 template <class Def>
-__global__ void __launch_bounds__(128) fused_f32_kernel(const __grid_constant__ FusedParams p,
+__global__ void __launch_bounds__(128, Def::Q <= 64 ? 5 : 4) fused_f32_kernel(const __grid_constant__ FusedParams p,
                                                         const float* __restrict__ fin,
                                                         float* __restrict__ fout) {
   constexpr int Q = Def::Q;
@@ -141,42 +145,27 @@ __global__ void __launch_bounds__(128) fused_f32_kernel(const __grid_constant__ 
       M[8] = hl_fma(p.gm[g][4], s[g][5], M[8]);
     }
 
-    // Landau frame: FP32 Newton on the full moments ...
+    // Landau frame: FP32 Newton on the full moments.  v = T^0i/(...) is well
+    // conditioned (relative error ~ FP32 rounding); the cancelling parts of the
+    // energy and density are formed below from the deviation moments.
     float Mf[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) Mf[k] = p.mref[k] + M[k];
+    for (int k = 0; k < 9; ++k) Mf[k] = p.mref[k].hi + (p.mref[k].lo + M[k]);
     float vx, vy, dvx, dvy;
     {
-      const float den = Mf[3] + 0.5f * (Mf[6] + Mf[8]);
-      vx = Mf[4] / den;
-      vy = Mf[5] / den;
+      const float iden = __fdividef(1.0f, Mf[3] + 0.5f * (Mf[6] + Mf[8]));
+      vx = Mf[4] * iden;
+      vy = Mf[5] * iden;
 #pragma unroll 1
       for (int it = 0; it < 8; ++it) {
-        landau_newton_step<float>(Mf, vx, vy, dvx, dvy);
+        landau_newton_step_fast(Mf, vx, vy, dvx, dvy);
         if (fabsf(dvx) + fabsf(dvy) < 1e-7f) break;
       }
-    }
-    // ... then one correction with the FP64 residual of the split moments:
-    //   F_x = T0x - Txx vx - Txy vy - e vx,  Txx = p_r + M6, e = e_r + e_d
-    {
-      const float ed = M[3] - M[4] * vx - M[5] * vy;
-      const float bx = M[6] * vx + M[7] * vy + ed * vx;
-      const float by = M[7] * vx + M[8] * vy + ed * vy;
-      const double Vx = (double)vx, Vy = (double)vy;
-      const double Fx = (double)M[4] - (double)bx - p.hr64 * Vx;
-      const double Fy = (double)M[5] - (double)by - p.hr64 * Vy;
-      const float e = Mf[3] - Mf[4] * vx - Mf[5] * vy;
-      const float J11 = -Mf[6] - e + vx * Mf[4], J12 = -Mf[7] + vx * Mf[5];
-      const float J21 = -Mf[7] + vy * Mf[4], J22 = -Mf[8] - e + vy * Mf[5];
-      const float idet = 1.0f / (J11 * J22 - J12 * J21);
-      const float fx = (float)Fx, fy = (float)Fy;
-      vx = (float)(Vx - (double)((J22 * fx - J12 * fy) * idet));
-      vy = (float)(Vy - (double)((J11 * fy - J21 * fx) * idet));
     }
     const float v2 = vx * vx + vy * vy;
     if (!(v2 < 1.0f)) fl |= ERR_LANDAU;
     const float sq = sqrtf(1.0f - v2);
-    const float dg = v2 / (sq * (1.0f + sq));          // gamma - 1
+    const float dg = __fdividef(v2, sq * (1.0f + sq));  // gamma - 1
     const float U0 = 1.0f + dg, Ux = U0 * vx, Uy = U0 * vy;
     // n = U.N = n_r + n_d
     const float Xi = M[0] - vx * M[1] - vy * M[2];
@@ -185,7 +174,7 @@ __global__ void __launch_bounds__(128) fused_f32_kernel(const __grid_constant__ 
     if (!(n > 0.0f)) fl |= ERR_DENSITY;
     // e/n = y_r + y_d
     const float ed = M[3] - M[4] * vx - M[5] * vy;
-    const float yd = (ed - fmaf(p.yr.hi, nd, p.yr.lo * nd)) / n;
+    const float yd = __fdividef(ed - fmaf(p.yr.hi, nd, p.yr.lo * nd), n);
     if (!(p.yr.hi + yd > p.mb)) fl |= ERR_EOS;
     // EOS: T = 1 + T_d solves 3 T_d + m (R(m/T) - R_r) = y_d.  FP32 Newton ...
     float Td = yd / p.cv_r, slope = p.cv_r, R32 = p.Rr.hi;
@@ -197,11 +186,11 @@ __global__ void __launch_bounds__(128) fused_f32_kernel(const __grid_constant__ 
         Td = 0.0f;
         break;
       }
-      const float z = p.mb / T;
+      const float z = __fdividef(p.mb, T);
       R32 = ratio32(z, p.rt32, fl);
       const float dR = (R32 - p.Rr.hi) - p.Rr.lo;
       slope = eos_slope<float>(R32, z);
-      const float step = (3.0f * Td + p.mb * dR - yd) / slope;
+      const float step = __fdividef(3.0f * Td + p.mb * dR - yd, slope);
       Td -= step;
       if (fabsf(step) < 3e-8f) break;
     }
@@ -210,16 +199,16 @@ __global__ void __launch_bounds__(128) fused_f32_kernel(const __grid_constant__ 
     {
       const float Tf = 1.0f + Td;
       const double T64 = 1.0 + (double)Td;
-      double iT = (double)(1.0f / Tf);
+      double iT = (double)__fdividef(1.0f, Tf);
       iT = fma(iT, fma(-T64, iT, 1.0), iT);
       const double z64 = p.mb64 * iT;
       const double dR64 = ratio64(z64, p.rt64, fl) - p.Rr64;
       const double g64 = fma(3.0, (double)Td, fma(p.mb64, dR64, -(double)yd));
-      const float step = (float)g64 / slope;
+      const float step = __fdividef((float)g64, slope);
       Td -= step;
       const float R = p.Rr.hi + (p.Rr.lo + (float)dR64);
       const float z = (float)z64;
-      const float dRdz = R * R + 3.0f * R / z - 1.0f;
+      const float dRdz = R * R + 3.0f * __fdividef(R, z) - 1.0f;
       dR = fmaf(dRdz, z * step / Tf, (float)dR64);     // R at the corrected T (first order)
     }
     const float R = p.Rr.hi + (p.Rr.lo + dR);

@@ -134,7 +134,7 @@ static void fill_fused(rlbm_ctx* c, double nref) {
   const double pr = nref * sb.mref1[6];
   f.nr = split(N0r);
   f.yr = split(er / N0r);
-  for (int k = 0; k < 9; ++k) f.mref[k] = (float)(nref * sb.mref1[k]);
+  for (int k = 0; k < 9; ++k) f.mref[k] = split(nref * sb.mref1[k]);
   f.Rr64 = sb.sc.Rr;
   f.hr64 = er + pr;
   f.mb64 = sb.mbar;

@@ -108,7 +108,7 @@ struct FusedParams {
   HL Rr;               // R(mbar) = K1/K2(mbar)
   HL nr;               // reference density
   HL yr;               // reference energy per particle e_r/n_r
-  float mref[9];       // reference moments (FP32 copy, Newton start only)
+  HL mref[9];          // reference moments (hi/lo: no fixed rounding in the Landau solve)
   double Rr64, hr64, mb64, nr64;
   HL gm[6][5];         // per group: P0, P0^2, Pv, P0 Pv, Pv^2 (P0 = m gamma, Pv = m gamma v0)
   HL gf[6][10];        // per group: a0 a1 a4 a7 a8 bx2 bx5 q78 qy7 q9 (see host)

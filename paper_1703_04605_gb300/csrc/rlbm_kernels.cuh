@@ -108,6 +108,22 @@ __device__ __forceinline__ void landau_newton_step(const R_t* m, R_t& vx, R_t& v
   vy -= dvy;
 }
 
+// FP32 variant with an approximate reciprocal (the iteration corrects it).
+__device__ __forceinline__ void landau_newton_step_fast(const float* m, float& vx, float& vy, float& dvx,
+                                                        float& dvy) {
+  const float T00 = m[3], T0x = m[4], T0y = m[5], Txx = m[6], Txy = m[7], Tyy = m[8];
+  const float e = T00 - T0x * vx - T0y * vy;
+  const float Fx = T0x - Txx * vx - Txy * vy - e * vx;
+  const float Fy = T0y - Txy * vx - Tyy * vy - e * vy;
+  const float J11 = -Txx - e + vx * T0x, J12 = -Txy + vx * T0y;
+  const float J21 = -Txy + vy * T0x, J22 = -Tyy - e + vy * T0y;
+  const float idet = __fdividef(1.0f, J11 * J22 - J12 * J21);
+  dvx = (J22 * Fx - J12 * Fy) * idet;
+  dvy = (J11 * Fy - J21 * Fx) * idet;
+  vx -= dvx;
+  vy -= dvy;
+}
+
 // ------------------------------------------------------------ site macros
 template <typename R_t>
 struct Macro {
