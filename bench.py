@@ -122,6 +122,15 @@ def cpu_baseline(seconds=12.0, side=96):
                 side, side, d["steps"], d["seconds"])}
 
 
+def kernel_name(dtype, variant):
+    stencil = {1: "5,12,14,17,21,26", 2: "1,2,3,4,5,6", 3: "1,14,49,51,60,70"}.get(variant)
+    if dtype == "f64":
+        return "step_f64_kernel<64>"
+    if stencil is None:
+        return "step_f32_kernel<64>"
+    return "fused_f32_kernel<StencilDef<%s>, %s>" % (stencil, "true" if dtype == "bf16dev" else "false")
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -159,6 +168,7 @@ def main():
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the accuracy check and the other dtypes")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -185,48 +195,74 @@ def main():
     st = W.STENCIL_M1
     f = W.random_flow(N_SIDE)
     stream = torch.cuda.Stream()
-    lat = Lattice(st["groups"], st["m"], TAU, N_SIDE, N_SIDE, dtype=args.dtype, v0=st["v0"],
-                  stream=stream.cuda_stream)
-    info = lat.info()
-    lat.init(f["n"], f["ux"], f["uy"], f["T"])
-    lat.step(args.warmup)
-    lat.sync()
+    sites = float(N_SIDE) * N_SIDE
+    peak, peak_kind = _peaks()
 
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+    def measure(dtype, steps, warmup, sample_clocks=False):
+        lat = Lattice(st["groups"], st["m"], TAU, N_SIDE, N_SIDE, dtype=dtype, v0=st["v0"],
+                      stream=stream.cuda_stream)
+        info = lat.info()
+        lat.init(f["n"], f["ux"], f["uy"], f["T"])
+        lat.step(warmup)
+        lat.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        clk = ClockSampler(local) if sample_clocks else None
+        if clk:
+            clk.__enter__()
         barrier()
         e0.record(stream)
-        lat.step(args.steps)
+        lat.step(steps)
         e1.record(stream)
         stream.synchronize()
         barrier()
-    lat.sync()
-    ms = e0.elapsed_time(e1)
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-    sites = float(N_SIDE) * N_SIDE
-    ms_step = ms / args.steps
-    value = ws * sites * args.steps / (ms / 1e3) / 1e6
-    peak, peak_kind = _peaks()
+        if clk:
+            clk.__exit__(None, None, None)
+        lat.sync()
+        ms = e0.elapsed_time(e1)
+        if pg:
+            t = torch.tensor([ms], device="cuda")
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            ms = float(t.item())
+        return lat, info, ms / steps, clk
+
+    lat, info, ms_step, clk = measure(args.dtype, args.steps, args.warmup, sample_clocks=True)
+    value = ws * sites / (ms_step / 1e3) / 1e6
     bytes_launch = info["bytes_per_site"] * sites
     achieved = bytes_launch / (ms_step / 1e3) / 1e9
 
-    # accuracy of this run against the FP64 path on the same input (untimed)
+    def errs(got, rm):
+        umax = max(np.abs(rm["ux"]).max(), np.abs(rm["uy"]).max())
+        return {"n": float(np.max(np.abs(got["n"] / rm["n"] - 1))),
+                "T": float(np.max(np.abs(got["T"] / rm["T"] - 1))),
+                "u": float(max(np.abs(got["ux"] - rm["ux"]).max(), np.abs(got["uy"] - rm["uy"]).max()) / umax)}
+
+    # accuracy against the FP64 path on the same input and step count (untimed),
+    # and the other storage types on the same workload
     err = None
-    if args.dtype != "f64" and rank == 0:
+    by_dtype = {}
+    if rank == 0 and not args.no_extra:
         got = lat.moments()
+        nsteps = args.warmup + args.steps
         with Lattice(st["groups"], st["m"], TAU, N_SIDE, N_SIDE, dtype="f64", v0=st["v0"]) as ref:
             ref.init(f["n"], f["ux"], f["uy"], f["T"])
-            ref.step(args.warmup + args.steps)
+            ref.step(nsteps)
             rm = ref.moments()
-        umax = max(np.abs(rm["ux"]).max(), np.abs(rm["uy"]).max())
-        err = {"n": float(np.max(np.abs(got["n"] / rm["n"] - 1))),
-               "T": float(np.max(np.abs(got["T"] / rm["T"] - 1))),
-               "u": float(max(np.abs(got["ux"] - rm["ux"]).max(), np.abs(got["uy"] - rm["uy"]).max()) / umax),
-               "steps": args.warmup + args.steps, "against": "FP64 path of this library (parity-tested vs oracle)"}
+        if args.dtype != "f64":
+            err = dict(errs(got, rm), steps=nsteps, against="FP64 path of this library (parity-tested vs oracle)")
+        for dt, k in (("bf16dev", args.steps), ("f64", 10), ("f32", args.steps)):
+            if dt == args.dtype:
+                continue
+            l2, i2, m2, _ = measure(dt, k, args.warmup if dt != "f64" else 3)
+            rec = {"MLUPS": sites / (m2 / 1e3) / 1e6, "ms_per_step": m2, "bytes_per_site": i2["bytes_per_site"],
+                   "frac_hbm": i2["bytes_per_site"] * sites / (m2 / 1e3) / 1e9 / peak,
+                   "frac_hbm_incl_extra": (i2["bytes_per_site"] + i2["extra_bytes_per_site"]) * sites
+                   / (m2 / 1e3) / 1e9 / peak, "steps": k}
+            if dt != "f64":
+                l2.step(nsteps - (args.warmup + k))
+                rec["error_vs_f64"] = dict(errs(l2.moments(), rm), steps=nsteps)
+            by_dtype[dt] = rec
+            l2.close()
 
     # end to end through the C ABI: pinned host fields in, K steps with the
     # status word read back every step, macroscopic fields out
@@ -262,11 +298,12 @@ def main():
                    "l2": "inputs larger than L2 (%.1f GB of populations per step)" % (2 * bytes_launch / 2 / 1e9)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "step_%s_kernel" % args.dtype, "peak_kind": peak_kind,
+                     "kernel": kernel_name(args.dtype, info["kernel"]), "peak_kind": peak_kind,
                      "bytes_per_site": info["bytes_per_site"]},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
         "error_vs_f64": err,
+        "by_dtype": by_dtype,
         "e2e": e2e,
     }
     if not args.no_cpu_baseline:

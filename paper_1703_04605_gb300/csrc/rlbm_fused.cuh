@@ -22,8 +22,18 @@
 //    with the FP64 R(zeta) table after the FP32 iterations.  The same R enters
 //    the EOS and the projections, which keeps the energy of f^eq equal to the
 //    Landau energy (Eq. 20, 28).
+//
+// BF16 deviation storage (template flag BF): the stored value is
+// d_i = (f_i - r_i) - ref_i(x), rounded to bfloat16, where ref_i(x) =
+// mult_i (a + b_x n_x + b_y n_y + q (n_x^2 + n_y^2)) uses the equilibrium
+// coefficients of the writing site x for the population's group, rounded to
+// bfloat16 and stored beside the populations (four per group and site).  The
+// reader rebuilds f_i - r_i = d_i + ref_i(source site) from the same stored
+// numbers, so encoding and decoding agree exactly; the rest of the step is the
+// FP32 path above.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <utility>
 
 #include "rlbm_kernels.cuh"
@@ -45,13 +55,40 @@ __device__ __forceinline__ int wrap_c(int x, int N) {
   return r;
 }
 
-template <class Def, int I>
-__device__ __forceinline__ void fused_load(float (&d)[Def::Q], const float* __restrict__ fin,
-                                           long long plane, long long pitch, int x, int y, int Nx, int Ny) {
+__device__ __forceinline__ float bf_lo(unsigned u) { return __uint_as_float(u << 16); }
+__device__ __forceinline__ float bf_hi(unsigned u) { return __uint_as_float(u & 0xffff0000u); }
+__device__ __forceinline__ unsigned bf_pack(float lo, float hi) {
+  return (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
+         ((unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+}
+
+// reference of a population from its group's packed coefficients
+template <int nx, int ny, int mult>
+__device__ __forceinline__ float bf_ref(uint2 c) {
+  float r = bf_lo(c.x);
+  if constexpr (nx != 0) r = fmaf((float)nx, bf_hi(c.x), r);
+  if constexpr (ny != 0) r = fmaf((float)ny, bf_lo(c.y), r);
+  if constexpr (nx * nx + ny * ny != 0) r = fmaf((float)(nx * nx + ny * ny), bf_hi(c.y), r);
+  if constexpr (mult != 1) r *= (float)mult;
+  return r;
+}
+
+template <class Def, bool BF, int I>
+__device__ __forceinline__ void fused_load(float (&d)[Def::Q], const void* __restrict__ fin,
+                                           const uint2* __restrict__ cin, long long plane, long long pitch,
+                                           int x, int y, int Nx, int Ny) {
   constexpr int DX = Def::F.nx[I], DY = Def::F.ny[I];
   const int xs = wrap_c<DX>(x, Nx);
   const int ys = wrap_c<DY>(y, Ny);
-  d[I] = __ldg(fin + (long long)I * plane + (long long)ys * pitch + xs);
+  const long long idx = (long long)ys * pitch + xs;
+  if constexpr (BF) {
+    constexpr int g = Def::F.grp[I], mult = Def::F.mult[I];
+    const unsigned short h = __ldg(static_cast<const unsigned short*>(fin) + (long long)I * plane + idx);
+    const uint2 c = __ldg(cin + (long long)g * plane + idx);
+    d[I] = __uint_as_float((unsigned)h << 16) + bf_ref<DX, DY, mult>(c);
+  } else {
+    d[I] = __ldg(static_cast<const float*>(fin) + (long long)I * plane + idx);
+  }
 }
 
 template <class Def, int I>
@@ -66,9 +103,10 @@ __device__ __forceinline__ void fused_acc(const float (&d)[Def::Q], float (&s)[6
   if constexpr (ny != 0) s[g][5] = fmaf((float)(ny * ny), v, s[g][5]);
 }
 
-template <class Def, int I>
-__device__ __forceinline__ void fused_collide(const float (&d)[Def::Q], const float (&c)[6][6], float a0,
-                                              float ax, float ay, float* __restrict__ out, long long plane) {
+template <class Def, bool BF, int I>
+__device__ __forceinline__ void fused_collide(const float (&d)[Def::Q], const float (&c)[6][6],
+                                              const uint2 (&cq)[6], float a0, float ax, float ay,
+                                              void* __restrict__ out, long long plane) {
   constexpr int g = Def::F.grp[I], nx = Def::F.nx[I], ny = Def::F.ny[I], mult = Def::F.mult[I];
   // group polynomial alpha + bx nx + by ny + qxx nx^2 + qyy ny^2 + qxy nx ny
   float e = c[g][0];
@@ -83,14 +121,21 @@ __device__ __forceinline__ void fused_collide(const float (&d)[Def::Q], const fl
   if constexpr (nx != 0) om = fmaf(-(float)nx, ax, om);
   if constexpr (ny != 0) om = fmaf(-(float)ny, ay, om);
   const float v = d[I];
-  __stcs(out + (long long)I * plane, fmaf(om, e - v, v));
+  const float vn = fmaf(om, e - v, v);
+  if constexpr (BF) {
+    const float dv = vn - bf_ref<nx, ny, mult>(cq[g]);
+    __stcs(static_cast<unsigned short*>(out) + (long long)I * plane,
+           __bfloat16_as_ushort(__float2bfloat16_rn(dv)));
+  } else {
+    __stcs(static_cast<float*>(out) + (long long)I * plane, vn);
+  }
 }
 
-template <class Def, int... Is>
+template <class Def, bool BF, int... Is>
 __device__ __forceinline__ void fused_load_all(std::integer_sequence<int, Is...>, float (&d)[Def::Q],
-                                               const float* __restrict__ fin, long long plane, long long pitch,
-                                               int x, int y, int Nx, int Ny) {
-  (fused_load<Def, Is>(d, fin, plane, pitch, x, y, Nx, Ny), ...);
+                                               const void* __restrict__ fin, const uint2* __restrict__ cin,
+                                               long long plane, long long pitch, int x, int y, int Nx, int Ny) {
+  (fused_load<Def, BF, Is>(d, fin, cin, plane, pitch, x, y, Nx, Ny), ...);
 }
 
 template <class Def, int... Is>
@@ -99,19 +144,19 @@ __device__ __forceinline__ void fused_acc_all(std::integer_sequence<int, Is...>,
   (fused_acc<Def, Is>(d, s), ...);
 }
 
-template <class Def, int... Is>
+template <class Def, bool BF, int... Is>
 __device__ __forceinline__ void fused_collide_all(std::integer_sequence<int, Is...>, const float (&d)[Def::Q],
-                                                  const float (&c)[6][6], float a0, float ax, float ay,
-                                                  float* __restrict__ out, long long plane) {
-  (fused_collide<Def, Is>(d, c, a0, ax, ay, out, plane), ...);
+                                                  const float (&c)[6][6], const uint2 (&cq)[6], float a0,
+                                                  float ax, float ay, void* __restrict__ out, long long plane) {
+  (fused_collide<Def, BF, Is>(d, c, cq, a0, ax, ay, out, plane), ...);
 }
 
-// Five resident blocks of 128 threads (96 registers) for Q <= 64, four
-// (128 registers) for larger stencils, whose populations would spill.
-template <class Def>
-__global__ void __launch_bounds__(128, Def::Q <= 64 ? 5 : 4) fused_f32_kernel(const __grid_constant__ FusedParams p,
-                                                        const float* __restrict__ fin,
-                                                        float* __restrict__ fout) {
+// Five resident blocks of 128 threads (96 registers) for Q <= 64 in FP32, four
+// (128 registers) for larger stencils and for BF16 storage, which would spill.
+template <class Def, bool BF>
+__global__ void __launch_bounds__(128, (Def::Q <= 64 && !BF) ? 5 : 4) fused_f32_kernel(const __grid_constant__ FusedParams p,
+                                                        const void* __restrict__ fin,
+                                                        void* __restrict__ fout) {
   constexpr int Q = Def::Q;
   using Seq = std::make_integer_sequence<int, Q>;
   const int site = blockIdx.x * blockDim.x + threadIdx.x;
@@ -120,7 +165,8 @@ __global__ void __launch_bounds__(128, Def::Q <= 64 ? 5 : 4) fused_f32_kernel(co
     int x, y;
     site_of(site, p.Nx, x, y);
     float d[Q];
-    fused_load_all<Def>(Seq{}, d, fin, p.plane, p.pitch, x, y, p.Nx, p.Ny);
+    fused_load_all<Def, BF>(Seq{}, d, fin, static_cast<const uint2*>(p.cin), p.plane, p.pitch, x, y, p.Nx,
+                            p.Ny);
     float s[6][6];
 #pragma unroll
     for (int g = 0; g < 6; ++g)
@@ -242,9 +288,183 @@ __global__ void __launch_bounds__(128, Def::Q <= 64 ? 5 : 4) fused_f32_kernel(co
       c[g][5] = hl(a[9], r9);
     }
     const float a0 = U0 * p.inv_tau, ax = p.v0 * Ux * p.inv_tau, ay = p.v0 * Uy * p.inv_tau;
-    fused_collide_all<Def>(Seq{}, d, c, a0, ax, ay, fout + (long long)y * p.pitch + x, p.plane);
+    const long long here = (long long)y * p.pitch + x;
+    uint2 cq[6];
+    if constexpr (BF) {
+      // this site's reference coefficients, rounded once and stored for the readers
+#pragma unroll
+      for (int g = 0; g < 6; ++g) {
+        cq[g].x = bf_pack(c[g][0], c[g][1]);
+        cq[g].y = bf_pack(c[g][2], 0.5f * (c[g][3] + c[g][4]));
+        __stcs(static_cast<uint2*>(p.cout) + (long long)g * p.plane + here, cq[g]);
+      }
+    }
+    void* out = BF ? static_cast<void*>(static_cast<unsigned short*>(fout) + here)
+                   : static_cast<void*>(static_cast<float*>(fout) + here);
+    fused_collide_all<Def, BF>(Seq{}, d, c, cq, a0, ax, ay, out, p.plane);
   }
   report(fl, p.err);
+}
+
+}  // namespace rlbm
+
+namespace rlbm {
+
+// ---------------------------------------------------- BF16 init and read-out
+// Group coefficients of f^eq - r at one site from its fields, in FP64 (same
+// definitions as the step kernel: r0..r9 and the folded constants p.gf).
+__device__ __forceinline__ void fp64_group_coeffs(const FusedParams& p, const SiteConsts& sc, double n,
+                                                  double ux, double uy, double T, double (&c)[6][6],
+                                                  unsigned& fl) {
+  const double v2 = ux * ux + uy * uy;
+  const double g = 1.0 / sqrt(1.0 - v2);
+  const double dU = g * g * v2 / (g + 1.0);
+  const double Ux = g * ux, Uy = g * uy;
+  const double R = ratio64(sc.mbar / T, p.rt64, fl);
+  const double dR = R - sc.Rr;
+  const double mr32 = sc.mbar * R + 4.0 * T;
+  const double F = sc.mY * dR + 3.0 * (T - 1.0);
+  const double G = sc.mbar * dR + 4.0 * (T - 1.0);
+  const double r0 = n * R - p.nr64 * sc.Rr;
+  const double r1 = n * (dU - sc.k21 * dR);
+  const double r2 = n * Ux, r3 = n * Uy;
+  const double r4 = n * (F + dU * (2.0 * mr32 + sc.cb00_1) + dU * dU * mr32);
+  const double h = G + mr32 * dU;
+  const double r5 = n * h * Ux, r6 = n * h * Uy;
+  const double r7 = n * mr32 * Uy * Uy, r8 = n * mr32 * (Uy * Uy - 2.0 * Ux * Ux), r9 = n * mr32 * Ux * Uy;
+  for (int k = 0; k < 6; ++k) {
+    double a[10];
+    for (int q = 0; q < 10; ++q) a[q] = (double)p.gf[k][q].hi + (double)p.gf[k][q].lo;
+    c[k][0] = a[0] * r0 + a[1] * r1 + a[2] * r4 + a[3] * r7 + a[4] * r8;
+    c[k][1] = a[5] * r2 + a[6] * r5;
+    c[k][2] = a[5] * r3 + a[6] * r6;
+    c[k][3] = a[7] * (r7 - r8);
+    c[k][4] = a[8] * r7;
+    c[k][5] = a[9] * r9;
+  }
+}
+
+__device__ __forceinline__ uint2 bf_coeffs(const double (&c)[6][6], int g) {
+  uint2 q;
+  q.x = bf_pack((float)c[g][0], (float)c[g][1]);
+  q.y = bf_pack((float)c[g][2], (float)(0.5 * (c[g][3] + c[g][4])));
+  return q;
+}
+
+__device__ __forceinline__ double bf_ref_rt(uint2 c, int nx, int ny, int mult) {
+  return mult * ((double)bf_lo(c.x) + nx * (double)bf_hi(c.x) + ny * (double)bf_lo(c.y) +
+                 (nx * nx + ny * ny) * (double)bf_hi(c.y));
+}
+
+// Init, phase 1: reference coefficients of every site into both buffers.
+template <class Def>
+__global__ void __launch_bounds__(128) bf16_init_coeffs(const __grid_constant__ FusedParams p, SiteConsts sc,
+                                                        FieldPtrs fd, uint2* __restrict__ c0,
+                                                        uint2* __restrict__ c1) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned fl = 0;
+  if (s < p.Nx * p.Ny) {
+    int x, y;
+    site_of(s, p.Nx, x, y);
+    double c[6][6];
+    fp64_group_coeffs(p, sc, fd.n[s], fd.ux[s], fd.uy[s], fd.T[s], c, fl);
+    const long long here = (long long)y * p.pitch + x;
+    for (int g = 0; g < 6; ++g) {
+      const uint2 q = bf_coeffs(c, g);
+      c0[(long long)g * p.plane + here] = q;
+      c1[(long long)g * p.plane + here] = q;
+    }
+  }
+  report(fl, p.err);
+}
+
+// Init, phase 2: S_0 at the site and S_{-1} at x - n_i (see init_kernel).
+template <class Def>
+__global__ void __launch_bounds__(128) bf16_init_pops(const __grid_constant__ FusedParams p, SiteConsts sc,
+                                                      FieldPtrs fd, const uint2* __restrict__ coef,
+                                                      unsigned short* __restrict__ cur,
+                                                      unsigned short* __restrict__ prev) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned fl = 0;
+  if (s < p.Nx * p.Ny) {
+    int x, y;
+    site_of(s, p.Nx, x, y);
+    double c[6][6];
+    fp64_group_coeffs(p, sc, fd.n[s], fd.ux[s], fd.uy[s], fd.T[s], c, fl);
+    const long long here = (long long)y * p.pitch + x;
+    constexpr Folded F = Def::F;   // local copy: indexed at run time below
+    for (int i = 0; i < Def::Q; ++i) {
+      const int g = F.grp[i], nx = F.nx[i], ny = F.ny[i], mult = F.mult[i];
+      const double fr = mult * (c[g][0] + nx * c[g][1] + ny * c[g][2] + nx * nx * c[g][3] + ny * ny * c[g][4] +
+                                nx * ny * c[g][5]);
+      const uint2 own = coef[(long long)g * p.plane + here];
+      cur[(long long)i * p.plane + here] = __bfloat16_as_ushort(__double2bfloat16(fr - bf_ref_rt(own, nx, ny, mult)));
+      int xs = x - nx, ys = y - ny;
+      xs = ((xs % p.Nx) + p.Nx) % p.Nx;
+      ys = ((ys % p.Ny) + p.Ny) % p.Ny;
+      const long long there = (long long)ys * p.pitch + xs;
+      const uint2 rem = coef[(long long)g * p.plane + there];
+      prev[(long long)i * p.plane + there] =
+          __bfloat16_as_ushort(__double2bfloat16(fr - bf_ref_rt(rem, nx, ny, mult)));
+    }
+  }
+  report(fl, p.err);
+}
+
+// Read-out: decode the pull of S_{t-1} with its coefficients, FP64 solve.
+template <class Def>
+__global__ void __launch_bounds__(128) bf16_moments(const __grid_constant__ StepParams<double> p,
+                                                    const unsigned short* __restrict__ prev,
+                                                    const uint2* __restrict__ cprev, MomentOut mo) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned fl = 0;
+  const long long N = (long long)p.Nx * p.Ny;
+  if (s < N) {
+    int x, y;
+    site_of(s, p.Nx, x, y);
+    double m[9];
+    for (int k = 0; k < 9; ++k) m[k] = 0.0;
+    constexpr Folded F = Def::F;   // local copy: indexed at run time below
+    for (int i = 0; i < Def::Q; ++i) {
+      const int g = F.grp[i], nx = F.nx[i], ny = F.ny[i], mult = F.mult[i];
+      const int xs = wrap_sub(x, p.pt.dxm[i], p.Nx);
+      const int ys = wrap_sub(y, p.pt.dym[i], p.Ny);
+      const long long there = (long long)ys * p.pitch + xs;
+      const double f = (double)__uint_as_float((unsigned)prev[(long long)i * p.plane + there] << 16) +
+                       bf_ref_rt(cprev[(long long)g * p.plane + there], nx, ny, mult);
+      for (int k = 0; k < 9; ++k) m[k] = fma(f, p.pt.mom[k][i], m[k]);
+    }
+    for (int k = 0; k < 9; ++k) m[k] += p.mref[k];
+    const Macro<double> md = solve_site_f64(m, p.sc, p.rt64, fl);
+    double* out = mo.out;
+    int plane = 0;
+    if (mo.mask & RLBM_M_N) out[(plane++) * N + s] = md.n;
+    if (mo.mask & RLBM_M_UX) out[(plane++) * N + s] = md.Ux / md.U0;
+    if (mo.mask & RLBM_M_UY) out[(plane++) * N + s] = md.Uy / md.U0;
+    if (mo.mask & RLBM_M_T) out[(plane++) * N + s] = md.T;
+    if (mo.mask & RLBM_M_E) out[(plane++) * N + s] = m[3] - m[4] * (md.Ux / md.U0) - m[5] * (md.Uy / md.U0);
+    if (mo.mask & RLBM_M_NVEC)
+      for (int k = 0; k < 3; ++k) out[(plane++) * N + s] = m[k];
+    if (mo.mask & RLBM_M_TMN)
+      for (int k = 3; k < 9; ++k) out[(plane++) * N + s] = m[k];
+  }
+  report(fl, p.err);
+}
+
+template <class Def>
+cudaError_t launch_bf16_io_impl(int what, const FusedParams& fp, const StepParams<double>& p, FieldPtrs fd,
+                                void* cur, void* prev, void* ccur, void* cprev, MomentOut mo, cudaStream_t s) {
+  const long long nsite = (long long)p.Nx * p.Ny;
+  const unsigned grid = (unsigned)((nsite + 127) / 128);
+  if (what == 0) {
+    bf16_init_coeffs<Def><<<grid, 128, 0, s>>>(fp, p.sc, fd, static_cast<uint2*>(ccur), static_cast<uint2*>(cprev));
+    bf16_init_pops<Def><<<grid, 128, 0, s>>>(fp, p.sc, fd, static_cast<const uint2*>(ccur),
+                                             static_cast<unsigned short*>(cur), static_cast<unsigned short*>(prev));
+  } else {
+    bf16_moments<Def><<<grid, 128, 0, s>>>(p, static_cast<const unsigned short*>(prev),
+                                           static_cast<const uint2*>(cprev), mo);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace rlbm

@@ -4,10 +4,16 @@
 
 namespace rlbm {
 template <>
-cudaError_t launch_fused<StencilG16>(const FusedParams& p, const void* fin, void* fout, cudaStream_t s) {
+cudaError_t launch_fused<StencilG16>(const FusedParams& p, const void* fin, void* fout, bool bf16, cudaStream_t s) {
   const long long nsite = (long long)p.Nx * p.Ny;
-  fused_f32_kernel<StencilG16><<<(unsigned)((nsite + 127) / 128), 128, 0, s>>>(
-      p, static_cast<const float*>(fin), static_cast<float*>(fout));
+  const unsigned grid = (unsigned)((nsite + 127) / 128);
+  if (bf16) fused_f32_kernel<StencilG16, true><<<grid, 128, 0, s>>>(p, fin, fout);
+  else fused_f32_kernel<StencilG16, false><<<grid, 128, 0, s>>>(p, fin, fout);
   return cudaGetLastError();
+}
+template <>
+cudaError_t launch_bf16_io<StencilG16>(int what, const FusedParams& fp, const StepParams<double>& p, FieldPtrs fd,
+                               void* cur, void* prev, void* ccur, void* cprev, MomentOut mo, cudaStream_t s) {
+  return launch_bf16_io_impl<StencilG16>(what, fp, p, fd, cur, prev, ccur, cprev, mo, s);
 }
 }  // namespace rlbm

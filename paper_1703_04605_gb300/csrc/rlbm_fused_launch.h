@@ -3,16 +3,29 @@
 
 #include <cuda_runtime.h>
 
+#include "rlbm_internal.h"
 #include "rlbm_stencils.h"
 
 namespace rlbm {
-struct FusedParams;
 template <class Def>
-cudaError_t launch_fused(const FusedParams& p, const void* fin, void* fout, cudaStream_t s);
+cudaError_t launch_fused(const FusedParams& p, const void* fin, void* fout, bool bf16, cudaStream_t s);
 template <>
-cudaError_t launch_fused<StencilM1>(const FusedParams&, const void*, void*, cudaStream_t);
+cudaError_t launch_fused<StencilM1>(const FusedParams&, const void*, void*, bool, cudaStream_t);
 template <>
-cudaError_t launch_fused<StencilG16>(const FusedParams&, const void*, void*, cudaStream_t);
+cudaError_t launch_fused<StencilG16>(const FusedParams&, const void*, void*, bool, cudaStream_t);
 template <>
-cudaError_t launch_fused<StencilE5>(const FusedParams&, const void*, void*, cudaStream_t);
+cudaError_t launch_fused<StencilE5>(const FusedParams&, const void*, void*, bool, cudaStream_t);
+// BF16 deviation storage: what = 0 init (fields -> coefficients, S_0, S_{-1}),
+// what = 1 read-out of the pull of prev.
+template <class Def>
+cudaError_t launch_bf16_io(int what, const FusedParams& fp, const StepParams<double>& p, FieldPtrs fd,
+                           void* cur, void* prev, void* ccur, void* cprev, MomentOut mo, cudaStream_t s);
+#define RLBM_DECL_BF16_IO(S)                                                                              \
+  template <>                                                                                            \
+  cudaError_t launch_bf16_io<S>(int, const FusedParams&, const StepParams<double>&, FieldPtrs, void*, void*, \
+                                void*, void*, MomentOut, cudaStream_t);
+RLBM_DECL_BF16_IO(StencilM1)
+RLBM_DECL_BF16_IO(StencilG16)
+RLBM_DECL_BF16_IO(StencilE5)
+#undef RLBM_DECL_BF16_IO
 }  // namespace rlbm

@@ -22,6 +22,7 @@ struct rlbm_ctx {
   long long pitch = 0, plane = 0;
   size_t elem = 0;
   void* buf[2] = {nullptr, nullptr};
+  void* coef[2] = {nullptr, nullptr};   // BF16 storage: per-site reference coefficients
   int cur = 0;              // buffer holding S_t
   long long t = 0;
   unsigned* d_err = nullptr;
@@ -57,7 +58,7 @@ static rlbm_status cuda_fail(rlbm_ctx* c, cudaError_t e, const char* where) {
 static void release(rlbm_ctx* c) {
   if (!c) return;
   if (c->buf[0]) cudaStreamSynchronize(c->stream);
-  for (void* p : {c->buf[0], c->buf[1], (void*)c->d_err, (void*)c->d_rt64, (void*)c->d_rt32,
+  for (void* p : {c->buf[0], c->buf[1], c->coef[0], c->coef[1], (void*)c->d_err, (void*)c->d_rt64, (void*)c->d_rt32,
                   (void*)c->d_fields, (void*)c->d_out})
     if (p) cudaFree(p);
 }
@@ -89,7 +90,7 @@ static HL split(double x) {
 
 // Which stencil-specialised kernel serves this context (0: none).
 static int fused_kind(const rlbm_ctx* c) {
-  if (c->dtype != RLBM_F32) return 0;
+  if (c->dtype == RLBM_F64) return 0;
   auto same = [&](const int* g) {
     for (int k = 0; k < 6; ++k)
       if (c->sb.groups[k] != g[k]) return false;
@@ -193,7 +194,6 @@ rlbm_status rlbm_create(const rlbm_stencil* st, double m, double tau, int Nx, in
   if (!(tau > 0.5) || !std::isfinite(tau)) return fail(nullptr, RLBM_EINVAL, "tau must exceed 1/2");
   if (dtype != RLBM_F64 && dtype != RLBM_F32 && dtype != RLBM_BF16_DEV)
     return fail(nullptr, RLBM_EINVAL, "unknown dtype");
-  if (dtype == RLBM_BF16_DEV) return fail(nullptr, RLBM_ENOTSUP, "BF16 deviation storage not built");
   std::unique_ptr<rlbm_ctx> c(new (std::nothrow) rlbm_ctx);
   if (!c) return fail(nullptr, RLBM_ENOMEM, "host allocation failed");
   std::string err;
@@ -213,7 +213,7 @@ rlbm_status rlbm_create(const rlbm_stencil* st, double m, double tau, int Nx, in
       break;
     }
   if (!c->qb) return fail(nullptr, RLBM_ENOTSUP, "too many populations");
-  c->elem = (dtype == RLBM_F64) ? sizeof(double) : sizeof(float);
+  c->elem = (dtype == RLBM_F64) ? sizeof(double) : (dtype == RLBM_F32) ? sizeof(float) : 2;
   c->pitch = ((long long)Nx + 31) / 32 * 32;
   c->plane = c->pitch * Ny;
   int ndev = 0;
@@ -257,6 +257,23 @@ rlbm_status rlbm_create(const rlbm_stencil* st, double m, double tau, int Nx, in
     c->fp.reset(new FusedParams);
     fill_fused(c.get(), 1.0);
   }
+  if (dtype == RLBM_BF16_DEV) {
+    if (!c->fused) {
+      release(c.get());
+      return fail(nullptr, RLBM_ENOTSUP,
+                  "BF16 deviation storage needs a compiled stencil ({5,12,14,17,21,26}, {1..6} or "
+                  "{1,14,49,51,60,70}) and Nx, Ny >= its halo");
+    }
+    const size_t cbytes = (size_t)6 * (size_t)c->plane * 8;
+    for (int b = 0; b < 2; ++b) {
+      e = cudaMalloc(&c->coef[b], cbytes);
+      if (e != cudaSuccess) {
+        release(c.get());
+        return fail(nullptr, RLBM_ENOMEM, "coefficient buffers: " + std::string(cudaGetErrorString(e)));
+      }
+    }
+    c->device_bytes += 2 * cbytes;
+  }
   *out = c.release();
   return RLBM_OK;
 }
@@ -267,7 +284,15 @@ rlbm_status rlbm_init_device(rlbm_ctx* c, const double* n, const double* ux, con
   if (!n || !ux || !uy || !T) return fail(c, RLBM_EINVAL, "NULL field pointer");
   FieldPtrs fp{n, ux, uy, T};
   if (!c->host_init) set_reference(c, 1.0);
-  cudaError_t e = launch_init(c->dtype, *c->p64, fp, c->buf[0], c->buf[1], c->stream);
+  cudaError_t e;
+  if (c->dtype == RLBM_BF16_DEV) {
+    MomentOut none{nullptr, 0};
+    if (c->fused == 1) e = launch_bf16_io<StencilM1>(0, *c->fp, *c->p64, fp, c->buf[0], c->buf[1], c->coef[0], c->coef[1], none, c->stream);
+    else if (c->fused == 2) e = launch_bf16_io<StencilG16>(0, *c->fp, *c->p64, fp, c->buf[0], c->buf[1], c->coef[0], c->coef[1], none, c->stream);
+    else e = launch_bf16_io<StencilE5>(0, *c->fp, *c->p64, fp, c->buf[0], c->buf[1], c->coef[0], c->coef[1], none, c->stream);
+  } else {
+    e = launch_init(c->dtype, *c->p64, fp, c->buf[0], c->buf[1], c->stream);
+  }
   if (e != cudaSuccess) return cuda_fail(c, e, "init launch");
   c->cur = 0;
   c->t = 0;
@@ -315,9 +340,14 @@ rlbm_status rlbm_step(rlbm_ctx* c, int nsteps) {
     void* fout = c->buf[1 - c->cur];
     cudaError_t e;
     if (c->dtype == RLBM_F64) e = launch_step_f64(*c->p64, fin, fout, c->qb, c->stream);
-    else if (c->fused == 1) e = launch_fused<StencilM1>(*c->fp, fin, fout, c->stream);
-    else if (c->fused == 2) e = launch_fused<StencilG16>(*c->fp, fin, fout, c->stream);
-    else if (c->fused == 3) e = launch_fused<StencilE5>(*c->fp, fin, fout, c->stream);
+    else if (c->fused) {
+      const bool bf = c->dtype == RLBM_BF16_DEV;
+      c->fp->cin = c->coef[c->cur];
+      c->fp->cout = c->coef[1 - c->cur];
+      if (c->fused == 1) e = launch_fused<StencilM1>(*c->fp, fin, fout, bf, c->stream);
+      else if (c->fused == 2) e = launch_fused<StencilG16>(*c->fp, fin, fout, bf, c->stream);
+      else e = launch_fused<StencilE5>(*c->fp, fin, fout, bf, c->stream);
+    }
     else e = launch_step_f32(*c->p32, fin, fout, c->qb, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
     c->cur = 1 - c->cur;
@@ -352,7 +382,17 @@ rlbm_status rlbm_moments(rlbm_ctx* c, double* out, unsigned mask) {
     c->out_cap = need;
   }
   MomentOut mo{c->d_out, mask};
-  cudaError_t e = launch_moments(c->dtype, *c->p64, c->buf[1 - c->cur], mo, c->stream);
+  cudaError_t e;
+  if (c->dtype == RLBM_BF16_DEV) {
+    FieldPtrs none{nullptr, nullptr, nullptr, nullptr};
+    void* pv = c->buf[1 - c->cur];
+    void* cp = c->coef[1 - c->cur];
+    if (c->fused == 1) e = launch_bf16_io<StencilM1>(1, *c->fp, *c->p64, none, nullptr, pv, nullptr, cp, mo, c->stream);
+    else if (c->fused == 2) e = launch_bf16_io<StencilG16>(1, *c->fp, *c->p64, none, nullptr, pv, nullptr, cp, mo, c->stream);
+    else e = launch_bf16_io<StencilE5>(1, *c->fp, *c->p64, none, nullptr, pv, nullptr, cp, mo, c->stream);
+  } else {
+    e = launch_moments(c->dtype, *c->p64, c->buf[1 - c->cur], mo, c->stream);
+  }
   if (e != cudaSuccess) return cuda_fail(c, e, "moments launch");
   e = cudaMemcpyAsync(out, c->d_out, need * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "read-out copy");
@@ -378,7 +418,7 @@ rlbm_status rlbm_get_info(const rlbm_ctx* c, rlbm_info* info) {
   for (int k = 0; k < 6; ++k) info->w_group[k] = c->sb.w_group[k];
   info->t = c->t;
   info->bytes_per_site = 2 * (size_t)c->Q * c->elem;
-  info->extra_bytes_per_site = 0;
+  info->extra_bytes_per_site = (c->dtype == RLBM_BF16_DEV) ? 2 * 6 * 8 : 0;   // coefficients read + written
   info->device_bytes = c->device_bytes + c->out_cap * sizeof(double);
   info->kernel = c->fused;
   return RLBM_OK;

@@ -115,6 +115,10 @@ struct FusedParams {
   const double* rt64;
   const float* rt32;
   unsigned* err;
+  // BF16 deviation storage only: per-site equilibrium reference coefficients,
+  // six planes (one per group) of uint2 = 4 bf16 (alpha, beta_x, beta_y, q)
+  const void* cin;
+  void* cout;
 };
 
 // Device error bits (OR-ed into *err).

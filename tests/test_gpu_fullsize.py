@@ -75,3 +75,11 @@ def test_f32_vs_f64_after_1000_steps(fields):
     g64, _ = _run(fields, "f64", 1000)
     e = errors(g32, g64)
     assert max(e.values()) < 1e-5, e
+
+
+def test_bf16dev_vs_f64_after_1000_steps(fields):
+    gb, info = _run(fields, "bf16dev", 1000)
+    assert info["kernel"] == 1
+    g64, _ = _run(fields, "f64", 1000)
+    e = errors(gb, g64)
+    assert max(e.values()) < 2e-3, e

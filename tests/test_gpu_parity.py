@@ -10,7 +10,7 @@ from paper_1703_04605_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 STENCILS = {"M1": W.STENCIL_M1, "G16": W.STENCIL_G16, "E5": W.STENCIL_E5}
-TOL = {"f64": 1e-12, "f32": 1e-5}
+TOL = {"f64": 1e-12, "f32": 1e-5, "bf16dev": 2e-3}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -129,3 +129,42 @@ def test_f32_generic_kernel_tiny_lattice():
     ref = run_oracle(st, 0.8, f, 20)
     e = errors(got, ref)
     assert e["n"] < 1e-5 and e["T"] < 1e-5, e
+
+
+@pytest.mark.parametrize("name", ["M1", "G16", "E5"])
+def test_bf16dev_small_ragged(name):
+    st = STENCILS[name]
+    f = smooth_fields(45, 31, seed=19)
+    got, info = run_gpu(st, 0.8, f, "bf16dev", 50)
+    assert info["kernel"] == {"M1": 1, "G16": 2, "E5": 3}[name]
+    assert info["bytes_per_site"] == 2 * info["Q"] * 2
+    ref = run_oracle(st, 0.8, f, 50)
+    e = errors(got, ref)
+    assert max(e.values()) < TOL["bf16dev"], e
+
+
+def test_bf16dev_moments_at_t0():
+    # the stored deviations decode back to the equilibrium of the fields
+    st = W.STENCIL_M1
+    f = smooth_fields(24, 20, seed=6, du=0.3, dT=0.5)
+    got, _ = run_gpu(st, 0.8, f, "bf16dev", 0)
+    assert np.max(np.abs(got["n"] / f["n"] - 1)) < 1e-3
+    assert np.max(np.abs(got["T"] / f["T"] - 1)) < 1e-3
+    assert np.max(np.abs(got["ux"] - f["ux"])) < 1e-3
+
+
+def test_bf16dev_blast_crop():
+    # the near-massless blast (disc at T = 2 in T = 1) on the E5 stencil,
+    # 64 x 64 with a radius-8 disc, 60 steps, against the FP64 oracle
+    st = W.STENCIL_E5
+    f = W.blast(64, 8)
+    got, _ = run_gpu(st, 0.7, f, "bf16dev", 60)
+    ref = run_oracle(st, 0.7, f, 60)
+    e = errors(got, ref)
+    assert e["n"] < TOL["bf16dev"] and e["T"] < TOL["bf16dev"] and e["u"] < 1e-2, e
+
+
+def test_bf16dev_unsupported_stencil_is_an_error():
+    from paper_1703_04605_gb300 import Lattice, RLBMError
+    with pytest.raises(RLBMError):
+        Lattice([1, 2, 25, 29, 32, 57], 1.0, 0.8, 32, 32, dtype="bf16dev", v0=0.164844)
