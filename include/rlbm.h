@@ -150,6 +150,32 @@ const char* rlbm_last_error(const rlbm_ctx* ctx);
 /* Release the context and its device memory (synchronises its stream). */
 void rlbm_destroy(rlbm_ctx* ctx);
 
+/* Advance count contexts by nsteps each, as one batch (the independent
+ * lattices of a parameter sweep or an ensemble).  Equivalent to calling
+ * rlbm_step(ctxs[i], nsteps) for every i, but the lattices of one stencil
+ * advance together in the same launches (up to 30 lattices per launch, their
+ * parameters in the launch's constant bank), and the launches of two steps
+ * are captured once into a CUDA graph that is replayed.  An autotuner picks
+ * the occupancy variant and the number of lattices per launch by timing the
+ * first steps of the first call for a given batch (those steps count towards
+ * nsteps), and caches the choice.
+ * Requirements: every context initialised, FP32 storage, a compiled stencil
+ * (rlbm_info.kernel != 0), all on the same CUDA stream, no context listed
+ * twice.  Asynchronous on that stream (a NULL stream is bridged to an
+ * internal stream with events).  Errors: EINVAL (violated requirement),
+ * ENOTSUP, ECUDA. */
+rlbm_status rlbm_batch_step(rlbm_ctx* const* ctxs, int count, int nsteps);
+
+/* The autotuner's choice for a batch that rlbm_batch_step has already
+ * advanced (same contexts, same order): *minb = minimum resident blocks per
+ * SM of the kernel variant (4 or 5), *per_launch = lattices per launch,
+ * *launches = kernel launches of one step (one per stencil kind and chunk of
+ * per_launch lattices).  Any output pointer may be NULL.  Never touches the
+ * device.  Errors: EINVAL (bad arguments, or no choice cached for this
+ * batch).  The paper has no counterpart; it reports how the batch runs. */
+rlbm_status rlbm_batch_tuning(rlbm_ctx* const* ctxs, int count, int* minb, int* per_launch,
+                              int* launches);
+
 /* ---- read-out without memory allocation -------------------------------
  * The paper has no counterpart of this entry point; it serves callers that
  * may not allocate device memory -- e.g. code running inside a host

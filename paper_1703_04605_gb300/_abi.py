@@ -20,7 +20,7 @@ MASK_PLANES = [(M_N, ["n"]), (M_UX, ["ux"]), (M_UY, ["uy"]), (M_T, ["T"]), (M_E,
 EXPORTS = ["rlbm_create", "rlbm_init", "rlbm_init_device", "rlbm_step", "rlbm_moments",
            "rlbm_moments_size", "rlbm_sync", "rlbm_get_info", "rlbm_last_error", "rlbm_destroy",
            "rlbm_quadrature_weights", "rlbm_quadrature_window", "rlbm_bessel_ratio", "rlbm_version",
-           "rlbm_moments_noalloc"]
+           "rlbm_moments_noalloc", "rlbm_batch_step", "rlbm_batch_tuning"]
 
 
 class Stencil(C.Structure):
@@ -76,6 +76,9 @@ def load():
         "rlbm_quadrature_window": (C.c_int, [ip, C.c_int, C.c_double, dp, dp, ip]),
         "rlbm_bessel_ratio": (C.c_double, [C.c_double, C.c_int]),
         "rlbm_version": (C.c_char_p, []),
+        "rlbm_batch_step": (C.c_int, [C.POINTER(P), C.c_int, C.c_int]),
+        "rlbm_batch_tuning": (C.c_int, [C.POINTER(P), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                        C.POINTER(C.c_int)]),
         "rlbm_moments_noalloc": (C.c_int, [ip, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, P, dp,
                                            C.c_uint, P]),
     }

@@ -151,17 +151,13 @@ __device__ __forceinline__ void fused_collide_all(std::integer_sequence<int, Is.
   (fused_collide<Def, BF, Is>(d, c, cq, a0, ax, ay, out, plane), ...);
 }
 
-// Five resident blocks of 128 threads (96 registers) for Q <= 64 in FP32, four
-// (128 registers) for larger stencils and for BF16 storage, which would spill.
+// One site update (see the header comment); p describes the lattice.
 template <class Def, bool BF>
-__global__ void __launch_bounds__(128, (Def::Q <= 64 && !BF) ? 5 : 4) fused_f32_kernel(const __grid_constant__ FusedParams p,
-                                                        const void* __restrict__ fin,
-                                                        void* __restrict__ fout) {
+__device__ __forceinline__ void fused_site(const FusedParams& p, const void* __restrict__ fin,
+                                           void* __restrict__ fout, int site, unsigned& fl) {
   constexpr int Q = Def::Q;
   using Seq = std::make_integer_sequence<int, Q>;
-  const int site = blockIdx.x * blockDim.x + threadIdx.x;
-  unsigned fl = 0;
-  if (site < p.Nx * p.Ny) {
+  {
     int x, y;
     site_of(site, p.Nx, x, y);
     float d[Q];
@@ -303,8 +299,42 @@ __global__ void __launch_bounds__(128, (Def::Q <= 64 && !BF) ? 5 : 4) fused_f32_
                    : static_cast<void*>(static_cast<float*>(fout) + here);
     fused_collide_all<Def, BF>(Seq{}, d, c, cq, a0, ax, ay, out, p.plane);
   }
+}
+
+// Five resident blocks of 128 threads (96 registers) for Q <= 64 in FP32, four
+// (128 registers) for larger stencils and for BF16 storage, which would spill.
+template <class Def, bool BF>
+__global__ void __launch_bounds__(128, (Def::Q <= 64 && !BF) ? 5 : 4) fused_f32_kernel(const __grid_constant__ FusedParams p,
+                                                        const void* __restrict__ fin,
+                                                        void* __restrict__ fout) {
+  const int site = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned fl = 0;
+  if (site < p.Nx * p.Ny) fused_site<Def, BF>(p, fin, fout, site, fl);
   report(fl, p.err);
 }
+
+template <class Def, bool BF, int MINB>
+__global__ void __launch_bounds__(128, MINB) fused_batch_kernel(const __grid_constant__ BatchParams bp) {
+  const int b = blockIdx.x;
+  int l = 0;
+#pragma unroll 1
+  while (l + 1 < bp.n && bp.start[l + 1] <= b) ++l;
+  const BatchLattice& L = bp.lat[l];
+  const int site = (b - bp.start[l]) * 128 + threadIdx.x;
+  unsigned fl = 0;
+  if (site < L.p.Nx * L.p.Ny) fused_site<Def, BF>(L.p, L.fin, L.fout, site, fl);
+  report(fl, L.p.err);
+}
+
+template <class Def>
+cudaError_t launch_batch_impl(const BatchParams& bp, int minb, cudaStream_t s) {
+  const unsigned grid = (unsigned)bp.start[bp.n];
+  if (grid == 0) return cudaSuccess;
+  if (minb == 5) fused_batch_kernel<Def, false, 5><<<grid, 128, 0, s>>>(bp);
+  else fused_batch_kernel<Def, false, 4><<<grid, 128, 0, s>>>(bp);
+  return cudaGetLastError();
+}
+
 
 }  // namespace rlbm
 

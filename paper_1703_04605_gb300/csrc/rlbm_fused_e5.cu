@@ -16,4 +16,8 @@ cudaError_t launch_bf16_io<StencilE5>(int what, const FusedParams& fp, const Ste
                                void* cur, void* prev, void* ccur, void* cprev, MomentOut mo, cudaStream_t s) {
   return launch_bf16_io_impl<StencilE5>(what, fp, p, fd, cur, prev, ccur, cprev, mo, s);
 }
+template <>
+cudaError_t launch_batch<StencilE5>(const BatchParams& bp, int minb, cudaStream_t s) {
+  return launch_batch_impl<StencilE5>(bp, minb, s);
+}
 }  // namespace rlbm

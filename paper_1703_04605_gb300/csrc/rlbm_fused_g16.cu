@@ -16,4 +16,8 @@ cudaError_t launch_bf16_io<StencilG16>(int what, const FusedParams& fp, const St
                                void* cur, void* prev, void* ccur, void* cprev, MomentOut mo, cudaStream_t s) {
   return launch_bf16_io_impl<StencilG16>(what, fp, p, fd, cur, prev, ccur, cprev, mo, s);
 }
+template <>
+cudaError_t launch_batch<StencilG16>(const BatchParams& bp, int minb, cudaStream_t s) {
+  return launch_batch_impl<StencilG16>(bp, minb, s);
+}
 }  // namespace rlbm

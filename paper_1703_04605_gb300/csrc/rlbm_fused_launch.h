@@ -15,6 +15,22 @@ template <>
 cudaError_t launch_fused<StencilG16>(const FusedParams&, const void*, void*, bool, cudaStream_t);
 template <>
 cudaError_t launch_fused<StencilE5>(const FusedParams&, const void*, void*, bool, cudaStream_t);
+template <>
+cudaError_t launch_fused<StencilS2>(const FusedParams&, const void*, void*, bool, cudaStream_t);
+
+// Batched FP32 step over up to kBatchMax lattices of one stencil (minb: 4 or 5
+// resident blocks per SM, i.e. 128 or 96 registers).
+struct BatchParams;
+template <class Def>
+cudaError_t launch_batch(const BatchParams& bp, int minb, cudaStream_t s);
+template <>
+cudaError_t launch_batch<StencilM1>(const BatchParams&, int, cudaStream_t);
+template <>
+cudaError_t launch_batch<StencilG16>(const BatchParams&, int, cudaStream_t);
+template <>
+cudaError_t launch_batch<StencilE5>(const BatchParams&, int, cudaStream_t);
+template <>
+cudaError_t launch_batch<StencilS2>(const BatchParams&, int, cudaStream_t);
 // BF16 deviation storage: what = 0 init (fields -> coefficients, S_0, S_{-1}),
 // what = 1 read-out of the pull of prev.
 template <class Def>
@@ -27,5 +43,6 @@ cudaError_t launch_bf16_io(int what, const FusedParams& fp, const StepParams<dou
 RLBM_DECL_BF16_IO(StencilM1)
 RLBM_DECL_BF16_IO(StencilG16)
 RLBM_DECL_BF16_IO(StencilE5)
+RLBM_DECL_BF16_IO(StencilS2)
 #undef RLBM_DECL_BF16_IO
 }  // namespace rlbm

@@ -1,0 +1,23 @@
+// Fused FP32 kernel for the stencil G3,G9,G10,G14,G17,G21.
+#include "rlbm_fused.cuh"
+#include "rlbm_fused_launch.h"
+
+namespace rlbm {
+template <>
+cudaError_t launch_fused<StencilS2>(const FusedParams& p, const void* fin, void* fout, bool bf16, cudaStream_t s) {
+  const long long nsite = (long long)p.Nx * p.Ny;
+  const unsigned grid = (unsigned)((nsite + 127) / 128);
+  if (bf16) fused_f32_kernel<StencilS2, true><<<grid, 128, 0, s>>>(p, fin, fout);
+  else fused_f32_kernel<StencilS2, false><<<grid, 128, 0, s>>>(p, fin, fout);
+  return cudaGetLastError();
+}
+template <>
+cudaError_t launch_bf16_io<StencilS2>(int what, const FusedParams& fp, const StepParams<double>& p, FieldPtrs fd,
+                               void* cur, void* prev, void* ccur, void* cprev, MomentOut mo, cudaStream_t s) {
+  return launch_bf16_io_impl<StencilS2>(what, fp, p, fd, cur, prev, ccur, cprev, mo, s);
+}
+template <>
+cudaError_t launch_batch<StencilS2>(const BatchParams& bp, int minb, cudaStream_t s) {
+  return launch_batch_impl<StencilS2>(bp, minb, s);
+}
+}  // namespace rlbm

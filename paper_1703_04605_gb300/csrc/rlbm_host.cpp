@@ -1,11 +1,15 @@
 // C ABI of the library (include/rlbm.h): context lifetime, validation,
 // device buffers, launches and error reporting.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "rlbm_fused_launch.h"
 #include "rlbm_stencil.h"
@@ -36,12 +40,13 @@ struct rlbm_ctx {
   bool host_init = false;   // rlbm_init in progress (it sets the reference itself)
   std::unique_ptr<StepParams<double>> p64;
   std::unique_ptr<StepParams<float>> p32;
-  int fused = 0;                 // 1: G5.. (M1), 2: G1..G6, 3: E5; 0: generic kernel
+  int fused = 0;                 // 1: M1, 2: G1..G6, 3: E5, 4: S2; 0: generic kernel
   std::unique_ptr<FusedParams> fp;
   std::string last_error;
 };
 
 static thread_local std::string g_create_error;
+static void batch_forget(const rlbm_ctx* c);   // drop cached batch graphs that use c
 
 void rlbm::set_global_error(const std::string& msg) { g_create_error = msg; }
 
@@ -101,6 +106,7 @@ static int fused_kind(const rlbm_ctx* c) {
   if (same(StencilM1::groups)) kind = 1, F = &StencilM1::F;
   else if (same(StencilG16::groups)) kind = 2, F = &StencilG16::F;
   else if (same(StencilE5::groups)) kind = 3, F = &StencilE5::F;
+  else if (same(StencilS2::groups)) kind = 4, F = &StencilS2::F;
   if (!kind || F->Q != c->Q || F->halo != c->sb.halo) return 0;
   // the compiled population order must be the host's (same storage planes)
   for (int i = 0; i < F->Q; ++i) {
@@ -283,13 +289,15 @@ rlbm_status rlbm_init_device(rlbm_ctx* c, const double* n, const double* ux, con
   if (!c) return RLBM_EINVAL;
   if (!n || !ux || !uy || !T) return fail(c, RLBM_EINVAL, "NULL field pointer");
   FieldPtrs fp{n, ux, uy, T};
+  batch_forget(c);   // its parameters change below
   if (!c->host_init) set_reference(c, 1.0);
   cudaError_t e;
   if (c->dtype == RLBM_BF16_DEV) {
     MomentOut none{nullptr, 0};
     if (c->fused == 1) e = launch_bf16_io<StencilM1>(0, *c->fp, *c->p64, fp, c->buf[0], c->buf[1], c->coef[0], c->coef[1], none, c->stream);
     else if (c->fused == 2) e = launch_bf16_io<StencilG16>(0, *c->fp, *c->p64, fp, c->buf[0], c->buf[1], c->coef[0], c->coef[1], none, c->stream);
-    else e = launch_bf16_io<StencilE5>(0, *c->fp, *c->p64, fp, c->buf[0], c->buf[1], c->coef[0], c->coef[1], none, c->stream);
+    else if (c->fused == 3) e = launch_bf16_io<StencilE5>(0, *c->fp, *c->p64, fp, c->buf[0], c->buf[1], c->coef[0], c->coef[1], none, c->stream);
+    else e = launch_bf16_io<StencilS2>(0, *c->fp, *c->p64, fp, c->buf[0], c->buf[1], c->coef[0], c->coef[1], none, c->stream);
   } else {
     e = launch_init(c->dtype, *c->p64, fp, c->buf[0], c->buf[1], c->stream);
   }
@@ -346,7 +354,8 @@ rlbm_status rlbm_step(rlbm_ctx* c, int nsteps) {
       c->fp->cout = c->coef[1 - c->cur];
       if (c->fused == 1) e = launch_fused<StencilM1>(*c->fp, fin, fout, bf, c->stream);
       else if (c->fused == 2) e = launch_fused<StencilG16>(*c->fp, fin, fout, bf, c->stream);
-      else e = launch_fused<StencilE5>(*c->fp, fin, fout, bf, c->stream);
+      else if (c->fused == 3) e = launch_fused<StencilE5>(*c->fp, fin, fout, bf, c->stream);
+      else e = launch_fused<StencilS2>(*c->fp, fin, fout, bf, c->stream);
     }
     else e = launch_step_f32(*c->p32, fin, fout, c->qb, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
@@ -389,7 +398,8 @@ rlbm_status rlbm_moments(rlbm_ctx* c, double* out, unsigned mask) {
     void* cp = c->coef[1 - c->cur];
     if (c->fused == 1) e = launch_bf16_io<StencilM1>(1, *c->fp, *c->p64, none, nullptr, pv, nullptr, cp, mo, c->stream);
     else if (c->fused == 2) e = launch_bf16_io<StencilG16>(1, *c->fp, *c->p64, none, nullptr, pv, nullptr, cp, mo, c->stream);
-    else e = launch_bf16_io<StencilE5>(1, *c->fp, *c->p64, none, nullptr, pv, nullptr, cp, mo, c->stream);
+    else if (c->fused == 3) e = launch_bf16_io<StencilE5>(1, *c->fp, *c->p64, none, nullptr, pv, nullptr, cp, mo, c->stream);
+    else e = launch_bf16_io<StencilS2>(1, *c->fp, *c->p64, none, nullptr, pv, nullptr, cp, mo, c->stream);
   } else {
     e = launch_moments(c->dtype, *c->p64, c->buf[1 - c->cur], mo, c->stream);
   }
@@ -430,6 +440,7 @@ const char* rlbm_last_error(const rlbm_ctx* c) {
 
 void rlbm_destroy(rlbm_ctx* c) {
   if (!c) return;
+  batch_forget(c);
   release(c);
   delete c;
 }
@@ -455,3 +466,250 @@ rlbm_status rlbm_quadrature_window(const int* groups, int ngroups, double m, dou
 double rlbm_bessel_ratio(double zeta, int precision) { return ratio_eval_host(zeta, precision); }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ batches
+namespace {
+
+struct BatchLaunch {
+  int kind;
+  BatchParams bp;
+};
+
+struct BatchPlan {
+  std::vector<rlbm_ctx*> ctxs;
+  std::vector<int> parity;                 // cur of each context when built
+  int minb = 5, lmax = kBatchMax;
+  cudaGraphExec_t two = nullptr;           // two consecutive steps
+  std::vector<BatchLaunch> step[2];
+};
+
+std::mutex g_batch_mutex;
+std::map<std::string, int> g_tuned;        // batch signature -> (minb << 8) | lmax
+std::map<std::string, std::unique_ptr<BatchPlan>> g_plans;
+
+std::string signature(rlbm_ctx* const* ctxs, int n, bool with_parity) {
+  std::string s;
+  for (int i = 0; i < n; ++i) {
+    char b[64];
+    std::snprintf(b, sizeof b, "%p:%d:%d;", (void*)ctxs[i], ctxs[i]->fused, with_parity ? ctxs[i]->cur : 0);
+    s += b;
+  }
+  return s;
+}
+
+cudaError_t launch_kind(int kind, const BatchParams& bp, int minb, cudaStream_t s) {
+  switch (kind) {
+    case 1: return launch_batch<StencilM1>(bp, minb, s);
+    case 2: return launch_batch<StencilG16>(bp, minb, s);
+    case 3: return launch_batch<StencilE5>(bp, minb, s);
+    default: return launch_batch<StencilS2>(bp, minb, s);
+  }
+}
+
+// Launches of one step: lattices grouped by stencil, largest first, at most
+// lmax per launch.  k = 0 or 1 selects the buffer parity relative to now.
+std::vector<BatchLaunch> build_step(const std::vector<rlbm_ctx*>& v, int k, int lmax) {
+  std::vector<rlbm_ctx*> order(v);
+  std::stable_sort(order.begin(), order.end(), [](rlbm_ctx* a, rlbm_ctx* b) {
+    if (a->fused != b->fused) return a->fused < b->fused;
+    return (long long)a->Nx * a->Ny > (long long)b->Nx * b->Ny;
+  });
+  std::vector<BatchLaunch> out;
+  for (size_t i = 0; i < order.size();) {
+    BatchLaunch L;
+    std::memset(&L.bp, 0, sizeof L.bp);
+    L.kind = order[i]->fused;
+    int n = 0, blocks = 0;
+    while (i < order.size() && n < lmax && order[i]->fused == L.kind) {
+      rlbm_ctx* c = order[i];
+      const int cur = c->cur ^ k;
+      BatchLattice& bl = L.bp.lat[n];
+      bl.p = *c->fp;
+      bl.fin = c->buf[cur];
+      bl.fout = c->buf[1 - cur];
+      L.bp.start[n] = blocks;
+      blocks += (int)(((long long)c->Nx * c->Ny + 127) / 128);
+      ++n;
+      ++i;
+    }
+    L.bp.n = n;
+    L.bp.start[n] = blocks;
+    out.push_back(L);
+  }
+  return out;
+}
+
+cudaError_t run_launches(const std::vector<BatchLaunch>& ls, int minb, cudaStream_t s) {
+  for (const BatchLaunch& L : ls) {
+    cudaError_t e = launch_kind(L.kind, L.bp, minb, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+static void batch_forget(const rlbm_ctx* c) {
+  std::lock_guard<std::mutex> lock(g_batch_mutex);
+  char b[32];
+  std::snprintf(b, sizeof b, "%p:", (const void*)c);
+  for (auto it = g_plans.begin(); it != g_plans.end();) {
+    if (it->first.find(b) != std::string::npos) {
+      if (it->second->two) cudaGraphExecDestroy(it->second->two);
+      it = g_plans.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  for (auto it = g_tuned.begin(); it != g_tuned.end();) {
+    if (it->first.find(b) != std::string::npos) it = g_tuned.erase(it);
+    else ++it;
+  }
+}
+
+extern "C" rlbm_status rlbm_batch_step(rlbm_ctx* const* ctxs, int count, int nsteps) {
+  if (!ctxs || count < 1 || nsteps < 0) return fail(nullptr, RLBM_EINVAL, "batch: bad arguments");
+  std::lock_guard<std::mutex> lock(g_batch_mutex);
+  for (int i = 0; i < count; ++i) {
+    rlbm_ctx* c = ctxs[i];
+    if (!c || !c->initialised) return fail(nullptr, RLBM_EINVAL, "batch: a context is missing or not initialised");
+    if (c->dtype != RLBM_F32 || !c->fused)
+      return fail(nullptr, RLBM_ENOTSUP, "batch: every context needs FP32 storage and a compiled stencil");
+    if (c->stream != ctxs[0]->stream) return fail(nullptr, RLBM_EINVAL, "batch: contexts on different streams");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == c) return fail(nullptr, RLBM_EINVAL, "batch: a context is listed twice");
+  }
+  if (nsteps == 0) return RLBM_OK;
+  std::vector<rlbm_ctx*> v(ctxs, ctxs + count);
+  cudaStream_t user = ctxs[0]->stream;
+  // stream capture needs a non-legacy stream: bridge a NULL stream with events
+  static cudaStream_t bridge = nullptr;
+  cudaStream_t s = user;
+  struct Events {
+    cudaEvent_t in = nullptr, out = nullptr;
+    ~Events() {
+      if (in) cudaEventDestroy(in);
+      if (out) cudaEventDestroy(out);
+    }
+  } ev;
+  cudaError_t e = cudaSuccess;
+  if (!user) {
+    if (!bridge) e = cudaStreamCreateWithFlags(&bridge, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev.in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev.out, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev.in, user);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(bridge, ev.in, 0);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch stream bridge");
+    s = bridge;
+  }
+  auto advance = [&](int k) {
+    for (rlbm_ctx* c : v) {
+      c->cur ^= (k & 1);
+      c->t += k;
+    }
+  };
+  const std::string sig = signature(ctxs, count, false);
+  int done = 0;
+  // autotune on the first steps of the first call for this batch
+  auto tuned = g_tuned.find(sig);
+  int minb = 5, lmax = kBatchMax;
+  if (tuned != g_tuned.end()) {
+    minb = tuned->second >> 8;
+    lmax = tuned->second & 0xff;
+  } else {
+    const int cand_minb[2] = {5, 4};
+    const int cand_lmax[3] = {8, 16, kBatchMax};
+    const int per = 2;
+    if (nsteps >= per * 6 + 1) {
+      float best = 1e30f;
+      cudaEvent_t a, b;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      for (int im = 0; im < 2 && e == cudaSuccess; ++im)
+        for (int il = 0; il < 3; ++il) {
+          cudaEventRecord(a, s);
+          for (int k = 0; k < per; ++k) {
+            e = run_launches(build_step(v, 0, cand_lmax[il]), cand_minb[im], s);
+            if (e != cudaSuccess) break;
+            advance(1);
+          }
+          cudaEventRecord(b, s);
+          cudaEventSynchronize(b);
+          float ms = 0;
+          cudaEventElapsedTime(&ms, a, b);
+          done += per;
+          if (e != cudaSuccess) break;
+          if (ms < best) {
+            best = ms;
+            minb = cand_minb[im];
+            lmax = cand_lmax[il];
+          }
+        }
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch autotune");
+    }
+    g_tuned[sig] = (minb << 8) | lmax;
+  }
+  // graph of two consecutive steps for the current buffer parities
+  const std::string psig = signature(ctxs, count, true) + std::to_string(minb) + "/" + std::to_string(lmax);
+  auto it = g_plans.find(psig);
+  if (it == g_plans.end() && nsteps - done >= 2) {
+    std::unique_ptr<BatchPlan> plan(new BatchPlan);
+    plan->ctxs = v;
+    plan->minb = minb;
+    plan->lmax = lmax;
+    plan->step[0] = build_step(v, 0, lmax);
+    plan->step[1] = build_step(v, 1, lmax);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e1 = run_launches(plan->step[0], minb, s);
+      cudaError_t e2 = run_launches(plan->step[1], minb, s);
+      e = cudaStreamEndCapture(s, &g);
+      if (e == cudaSuccess && e1 != cudaSuccess) e = e1;
+      if (e == cudaSuccess && e2 != cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&plan->two, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch graph capture");
+    it = g_plans.emplace(psig, std::move(plan)).first;
+  }
+  while (nsteps - done >= 2) {
+    e = cudaGraphLaunch(it->second->two, s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch graph launch");
+    advance(2);   // parity unchanged, so the same graph serves the next pair
+    done += 2;
+  }
+  if (nsteps - done == 1) {
+    e = run_launches(build_step(v, 0, lmax), minb, s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch step");
+    advance(1);
+    done += 1;
+  }
+  if (!user) {
+    e = cudaEventRecord(ev.out, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(user, ev.out, 0);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch stream bridge");
+  }
+  return RLBM_OK;
+}
+
+extern "C" rlbm_status rlbm_batch_tuning(rlbm_ctx* const* ctxs, int count, int* minb, int* per_launch,
+                                         int* launches) {
+  if (!ctxs || count < 1) return fail(nullptr, RLBM_EINVAL, "batch tuning: bad arguments");
+  for (int i = 0; i < count; ++i)
+    if (!ctxs[i]) return fail(nullptr, RLBM_EINVAL, "batch tuning: a context is missing");
+  std::lock_guard<std::mutex> lock(g_batch_mutex);
+  auto tuned = g_tuned.find(signature(ctxs, count, false));
+  if (tuned == g_tuned.end()) return fail(nullptr, RLBM_EINVAL, "batch tuning: this batch has not run");
+  const int lmax = tuned->second & 0xff;
+  std::map<int, int> per_kind;
+  for (int i = 0; i < count; ++i) per_kind[ctxs[i]->fused] += 1;
+  int n = 0;
+  for (const auto& kv : per_kind) n += (kv.second + lmax - 1) / lmax;
+  if (minb) *minb = tuned->second >> 8;
+  if (per_launch) *per_launch = lmax;
+  if (launches) *launches = n;
+  return RLBM_OK;
+}

@@ -116,7 +116,31 @@ static qf bessel_ratio_q(qf x, double digits = 36.0) {
 // In rapidity chi: d^3p/p0 = m^2 sinh^2 chi dchi dOmega and N_R = 4 pi m K1(m):
 //   <p0^a |p|^b * ang> = ang int e^{-m cosh} (m cosh)^a (m sinh)^(b+2) dchi / (m K1(m)),
 // with angular means 1, 1, 1/3, 1/3, 1/5, 1/15.
+static void rest_moments_q_uncached(qf m, qf out[6]);
+
+// The moments depend on m only; the last few are kept (window searches and
+// stencil builds ask for the same m many times).
 static void rest_moments_q(qf m, qf out[6]) {
+  struct Entry {
+    qf m;
+    qf v[6];
+  };
+  static thread_local Entry cache[8];
+  static thread_local int used = 0, next = 0;
+  for (int i = 0; i < used; ++i)
+    if (cache[i].m == m) {
+      for (int k = 0; k < 6; ++k) out[k] = cache[i].v[k];
+      return;
+    }
+  rest_moments_q_uncached(m, out);
+  Entry& e = cache[next];
+  e.m = m;
+  for (int k = 0; k < 6; ++k) e.v[k] = out[k];
+  next = (next + 1) % 8;
+  if (used < 8) ++used;
+}
+
+static void rest_moments_q_uncached(qf m, qf out[6]) {
   const qf h = trap_step<qf>((double)m, 36.0);
   qf s[6] = {0, 0, 0, 0, 0, 0};
   const qf tiny = (qf)1e-38;
@@ -257,7 +281,7 @@ int quadrature_window(const int* groups, double m, double* lo, double* hi) {
     if (!build_system<double>(gs, m, v, A)) return false;
     return solve6<double>(A, bb, w);
   };
-  const int N = 200000;
+  const int N = 20000;
   const double v_a = vmax * 1e-4, v_b = vmax * (1 - 1e-9);
   std::vector<double> cross;
   double wprev[6];

@@ -124,6 +124,7 @@ struct StencilDef {
 
 using StencilM1 = StencilDef<5, 12, 14, 17, 21, 26>;    // m/T_R ~ 1
 using StencilG16 = StencilDef<1, 2, 3, 4, 5, 6>;        // m/T_R >~ 5 (Sec. III D example)
-using StencilE5 = StencilDef<1, 14, 49, 51, 60, 70>;    // m/T_R ~ 0.36 (Sec. IV, Fig. 5)
+using StencilE5 = StencilDef<1, 14, 49, 51, 60, 70>;    // m/T_R in [0.36, 0.58] (Sec. IV, Fig. 5)
+using StencilS2 = StencilDef<3, 9, 10, 14, 17, 21>;     // m/T_R in [1.1, 8.4]
 
 }  // namespace rlbm

@@ -97,3 +97,20 @@ class Lattice:
         inf = A.Info()
         self._chk(self._lib.rlbm_get_info(self._ctx, C.byref(inf)))
         return {k: (list(getattr(inf, k)) if k == "w_group" else getattr(inf, k)) for k, _ in A.Info._fields_}
+
+
+def batch_step(lattices, k=1):
+    """Advance every lattice by k steps as one batch (rlbm_batch_step)."""
+    L = A.load()
+    arr = (C.c_void_p * len(lattices))(*[lat._ctx.value for lat in lattices])
+    A.check(L.rlbm_batch_step(arr, len(lattices), int(k)))
+
+
+def batch_tuning(lattices):
+    """The autotuner's choice for a batch already advanced by batch_step:
+    dict(minb, per_launch, launches) -- launches = kernel launches per step."""
+    L = A.load()
+    arr = (C.c_void_p * len(lattices))(*[lat._ctx.value for lat in lattices])
+    out = [C.c_int(0) for _ in range(3)]
+    A.check(L.rlbm_batch_tuning(arr, len(lattices), *[C.byref(o) for o in out]))
+    return dict(minb=out[0].value, per_launch=out[1].value, launches=out[2].value)

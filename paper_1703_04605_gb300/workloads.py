@@ -35,23 +35,39 @@ def _smooth_unit(rng, N, sigma):
     return s / s.std()
 
 
-def sod(Nx=800, Ny=1, n=(1.0, 0.5), T=(1.0, 0.8), x0=None):
-    """Quasi-1D relativistic shock tube: left state for x < x0."""
+def sod(Nx=800, Ny=1, n=(1.0, 0.5), T=(1.0, 0.8), x0=None, width=0.0):
+    """Quasi-1D relativistic shock tube: left state for x < x0 (cell x has
+    centre x + 1/2; the domain is periodic, so the tube has a second jump at
+    x = 0).  width > 0 replaces both jumps by tanh profiles of that width in
+    cells (the indicator of [0, x0) summed over its periodic images)."""
     x0 = Nx // 2 if x0 is None else x0
-    x = np.arange(Nx)[None, :].repeat(Ny, 0)
-    left = x < x0
-    return dict(n=np.where(left, n[0], n[1]).astype(np.float64),
-                ux=np.zeros((Ny, Nx)), uy=np.zeros((Ny, Nx)),
-                T=np.where(left, T[0], T[1]).astype(np.float64))
+    if width > 0.0:
+        xc = np.arange(Nx) + 0.5
+        a = sum(0.5 * (np.tanh((x0 + k * Nx - xc) / width) - np.tanh((k * Nx - xc) / width))
+                for k in (-1, 0, 1))
+    else:
+        a = (np.arange(Nx) < x0).astype(np.float64)
+    a = np.broadcast_to(a[None, :], (Ny, Nx))
+    return dict(n=n[1] + (n[0] - n[1]) * a, ux=np.zeros((Ny, Nx)), uy=np.zeros((Ny, Nx)),
+                T=T[1] + (T[0] - T[1]) * a)
 
 
-def sod_tau(eta_over_s=0.1, v0=STENCIL_M1["v0"], n=1.0, T=1.0, d_g=16.0):
-    """tau for a target eta/s, reading eta = (2/3) P (tau - 1/2)/v0 in units
-    dx = c = T_R = 1 (Sec. IV: tau = tau_f v0/dx, eta = (2/3) P (tau_f - dt/2)),
-    with s = 4n - n ln(n/n_eq), n_eq = d_g T^3/pi^2 (Sec. IV), left state."""
+# Physical scale of the paper's Riemann problem (Sec. IV): T_R = 400 MeV and a
+# periodic tube of 6400 cells of 0.002 fm (the 6.4 fm domain plus its mirror).
+HBARC_GEV_FM = 0.1973269804
+T_R_GEV = 0.4
+DX_T_PAPER = 0.002 * T_R_GEV / HBARC_GEV_FM            # dx in units of 1/T_R
+DX_T_SOD800 = (6400 / 800) * DX_T_PAPER                # the same tube on 800 cells
+
+
+def sod_tau(eta_over_s=0.1, v0=STENCIL_M1["v0"], n=1.0, T=1.0, d_g=16.0, dxT=DX_T_SOD800):
+    """Lattice tau for a target eta/s (Sec. IV): eta = (2/3) P (tau_f - dt/2)
+    with tau = tau_f / dt and dt = dx / v0, so tau = 1/2 + (3/2)(eta/s)(s/P)
+    v0 / dx, with dx in units of 1/T_R (dxT) and s = 4n - n ln(n/n_eq),
+    n_eq = d_g T^3/pi^2, P = n T, taken at the left state."""
     s = 4 * n - n * math.log(n / (d_g * T ** 3 / math.pi ** 2))
     P = n * T
-    return 0.5 + 1.5 * eta_over_s * s * v0 / P
+    return 0.5 + 1.5 * eta_over_s * (s / P) * v0 / dxT
 
 
 def taylor_green(N=512, u0=0.05, n0=1.0, T0=1.0):
@@ -86,7 +102,13 @@ def batch_specs(count=256, Lmin=64, Lmax=1024, mT=(0.1, 10.0), tau=(0.6, 1.5), m
                 config_index=3):
     """Independent lattices: side log-uniform, m/T log-uniform (clamped below
     at m_min, the smallest m with a positive quadrature here), tau uniform;
-    even index Sod tube, odd index Taylor-Green vortex."""
+    even index Sod tube, odd index Taylor-Green vortex.  A Sod tube's two
+    temperatures, drawn in [0.5, 1.5], are expressed in units of their mean
+    (the lattice's reference temperature T_R), so that m/T_R is the drawn
+    m/T of the mean state, and pulled towards that mean where their ratio
+    exceeds 2 (the ratio of the paper's Riemann problems, Sec. IV): at the
+    drawn tau in [0.6, 1.5] stronger jumps are beyond the stability of the
+    second-order scheme for some m/T_R (in FP64 as well)."""
     rng = np.random.default_rng(seed(config_index))
     out = []
     for i in range(count):
@@ -95,7 +117,8 @@ def batch_specs(count=256, Lmin=64, Lmax=1024, mT=(0.1, 10.0), tau=(0.6, 1.5), m
         spec = dict(L=L, m_drawn=m, m=max(m, m_min), tau=rng.uniform(*tau))
         if i % 2 == 0:
             nl, nr, tl, tr = rng.uniform(0.5, 1.5, 4)
-            spec.update(kind="sod", n=(nl, nr), T=(tl, tr))
+            d = min((tl - tr) / (tl + tr), 1 / 3) if tl >= tr else max((tl - tr) / (tl + tr), -1 / 3)
+            spec.update(kind="sod", n=(nl, nr), T=(1 + d, 1 - d), T_drawn=(tl, tr))
         else:
             spec.update(kind="tg", u0=rng.uniform(0.01, 0.1))
         out.append(spec)
