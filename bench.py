@@ -93,10 +93,13 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(seconds=12.0, side=96):
-    """The FP64 oracle as it stands, one thread, on a side x side lattice drawn
-    by the same generator (same smoothing, amplitudes and seed), for about
-    `seconds` of CPU time."""
+def cpu_baseline(seconds=12.0, side=96, procs=None):
+    """The FP64 oracle as it stands on the host cores: `procs` independent
+    processes (default: one per core), each with one thread, each advancing its
+    own side x side lattice drawn by the same generator (same smoothing,
+    amplitudes and seed) for about `seconds` of CPU time.  Value = the site
+    updates of all processes / wall time."""
+    procs = procs or os.cpu_count() or 1
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = (
         "import sys, time, json; sys.path.insert(0, %r)\n"
@@ -110,20 +113,28 @@ def cpu_baseline(seconds=12.0, side=96):
         "while time.process_time() - t0 < %r:\n"
         "    lat.step(1); k += 1\n"
         "dt = time.time() - w0\n"
-        "print(json.dumps({'steps': k, 'seconds': dt, 'mlups': %d * %d * k / dt / 1e6}))\n"
-    ) % (ROOT, side, TAU, side, side, seconds, side, side)
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
-    if r.returncode != 0:
-        return {"value": None, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                "sample": "failed: " + r.stderr.strip().splitlines()[-1] if r.stderr else "failed"}
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": d["mlups"], "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": "%dx%d lattice of the same generator, %d steps in %.1f s wall, 1 thread" % (
-                side, side, d["steps"], d["seconds"])}
+        "print(json.dumps({'steps': k, 'seconds': dt}))\n"
+    ) % (ROOT, side, TAU, side, side, seconds)
+    ps = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                           text=True, env=env) for _ in range(procs)]
+    res, errs = [], []
+    for p in ps:
+        out, err = p.communicate()
+        if p.returncode == 0:
+            res.append(json.loads(out.strip().splitlines()[-1]))
+        else:
+            errs.append(err.strip().splitlines()[-1] if err.strip() else "failed")
+    if not res:
+        return {"value": None, "unit": "MLUPS", "cores": procs, "kind": "oracle", "sample": "failed: " + errs[0]}
+    mlups = sum(side * side * r["steps"] / r["seconds"] for r in res) / 1e6
+    return {"value": mlups, "unit": "MLUPS", "cores": len(res), "kind": "oracle",
+            "sample": "%d processes x one %dx%d lattice of the same generator, %d-%d steps each in %.1f s wall, "
+                      "1 thread each" % (len(res), side, side, min(r["steps"] for r in res),
+                                         max(r["steps"] for r in res), max(r["seconds"] for r in res))}
 
 
 def kernel_name(dtype, variant):
-    stencil = {1: "5,12,14,17,21,26", 2: "1,2,3,4,5,6", 3: "1,14,49,51,60,70"}.get(variant)
+    stencil = {1: "5,12,14,17,21,26", 2: "1,2,3,4,5,6", 3: "1,14,49,51,60,70", 4: "3,9,10,14,17,21"}.get(variant)
     if dtype == "f64":
         return "step_f64_kernel<64>"
     if stencil is None:
@@ -138,6 +149,62 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_max(value, pg, device):
+    """Max over ranks of a per-rank time (identity without a process group)."""
+    if pg is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(sites_per_rank, world_size, ms_per_step_max):
+    """Weak scaling: every rank updates its own lattice; the job's throughput
+    is all ranks' site updates over the slowest rank's time."""
+    return world_size * float(sites_per_rank) / (ms_per_step_max / 1e3) / 1e6
+
+
+def emit(line, rank):
+    """The one JSON line, printed by rank 0 only."""
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def _source_hash(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+FUSED_SOURCES = ["paper_1703_04605_gb300/csrc/rlbm_fused.cuh", "paper_1703_04605_gb300/csrc/rlbm_internal.h",
+                 "paper_1703_04605_gb300/csrc/rlbm_stencils.h", "paper_1703_04605_gb300/csrc/rlbm_kernels.cuh",
+                 "paper_1703_04605_gb300/csrc/rlbm_fused_m1.cu"]
+
+
+def profiled_traffic(profile, sources):
+    """DRAM bytes per launch recorded in a committed ncu summary, or None when
+    the kernel sources changed since the counters were taken.  The summary
+    carries two lines 'traffic_bytes_per_launch: B' and 'source_hash: H'."""
+    try:
+        with open(os.path.join(ROOT, "profiles", profile)) as fh:
+            txt = fh.read()
+    except OSError:
+        return None
+    rec = {}
+    for line in txt.splitlines():
+        line = line.strip().strip("`")
+        for key in ("traffic_bytes_per_launch", "source_hash"):
+            if line.startswith(key + ":"):
+                rec[key] = line.split(":", 1)[1].strip()
+    if rec.get("source_hash") != _source_hash(sources) or "traffic_bytes_per_launch" not in rec:
+        return None
+    return float(rec["traffic_bytes_per_launch"])
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -145,19 +212,19 @@ def run_reference(args):
     vals = []
     side = 64
     for _ in range(args.warmup):
-        cpu_baseline(seconds=2.0, side=side)
+        cpu_baseline(seconds=1.0, side=side)
     for _ in range(args.steps):
-        vals.append(cpu_baseline(seconds=6.0, side=side))
+        vals.append(cpu_baseline(seconds=5.0, side=side))
     v = float(np.mean([d["value"] for d in vals]))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f64",
             "data": "synthetic", "scaling": "weak",
             "config": {"workload": WORKLOAD, "sample": "%dx%d lattice of the same generator per step" % (side, side)},
-            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": vals[-1]["cores"], "kind": "oracle",
                              "sample": vals[-1]["sample"]},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "vs_baseline": None}
-    print(json.dumps(line), flush=True)
+    emit(line, rank)
 
 
 def run_batch(args):
@@ -243,8 +310,84 @@ def run_batch(args):
                          "frac": achieved / peak[0], "peak_kind": peak[1], "traffic": None},
             "gpu_launches": tune["launches"] * args.steps,
             "clocks": clk.summary()}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    emit(line, rank)
+
+
+def run_blast(args):
+    """The near-massless blast: 8192 x 8192, disc of radius 512 at T = 2 in a
+    T = 1 background, tau = 0.7, BF16-deviation storage, m/T = 0.01 requested,
+    run at m/T_R = 0.36 on the 133-velocity stencil (the smallest covered
+    mass).  Reports MLUPS, the roofline, the equation of state of the
+    read-out (e/(3nT) - 1 and its residual against (zeta/3) K1/K2) and the
+    error against the FP32 path after the same steps."""
+    import torch
+    from scipy import special as sp
+    from paper_1703_04605_gb300 import Lattice, build, workloads as W
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    build.build()
+    st = W.STENCIL_E5
+    N, R, tau = 8192, 512, 0.7
+    f = W.blast(N, R)
+    stream = torch.cuda.Stream()
+    sites = float(N) * N
+    peak, peak_kind = _peaks()
+
+    def run(dtype, clk=None):
+        lat = Lattice(st["groups"], st["m"], tau, N, N, dtype=dtype, v0=st["v0"], stream=stream.cuda_stream)
+        lat.init(f["n"], f["ux"], f["uy"], f["T"])
+        lat.step(args.warmup)
+        lat.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        if clk:
+            clk.__enter__()
+        e0.record(stream)
+        lat.step(args.steps)
+        e1.record(stream)
+        stream.synchronize()
+        if clk:
+            clk.__exit__(None, None, None)
+        lat.sync()
+        info = lat.info()
+        mom = lat.moments()
+        lat.close()
+        return e0.elapsed_time(e1) / args.steps, info, mom
+
+    clk = ClockSampler(local)
+    ms, info, mb = run("bf16dev", clk)
+    z = st["m"] / mb["T"]
+    dev = mb["e"] / (3 * mb["n"] * mb["T"]) - 1
+    resid = np.abs(dev - z * (sp.kve(1, z) / sp.kve(2, z)) / 3)
+    err = None
+    if not args.no_extra:
+        _, _, m32 = run("f32")
+        umax = max(np.abs(m32["ux"]).max(), np.abs(m32["uy"]).max())
+        err = {"n": float(np.max(np.abs(mb["n"] / m32["n"] - 1))), "T": float(np.max(np.abs(mb["T"] / m32["T"] - 1))),
+               "u": float(max(np.abs(mb["ux"] - m32["ux"]).max(), np.abs(mb["uy"] - m32["uy"]).max()) / umax),
+               "steps": args.warmup + args.steps,
+               "against": "FP32 path (within 1e-4 of FP64 on the 1024^2, r=64 copy of this workload)"}
+    achieved = info["bytes_per_site"] * sites / (ms / 1e3) / 1e9
+    line = {"metric": METRIC, "value": sites / (ms / 1e3) / 1e6, "unit": "MLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "blast_8192: 8192x8192 periodic, disc r=512 at T=2 in T=1 (T_R = their mean), "
+                                   "n=1, u=0, tau=0.7, "
+                                   "m/T=0.01 requested, run at m/T_R=0.36 (smallest covered), stencil "
+                                   "G1,G14,G49,G51,G60,G70 (Q=73 folded), v0=0.1488232",
+                       "sites": int(sites), "Q": info["Q"], "m_over_T_used": st["m"],
+                       "l2": "inputs larger than L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                         "kernel": kernel_name("bf16dev", info["kernel"]),
+                         "bytes_per_site": info["bytes_per_site"],
+                         "frac_incl_coefficients": (info["bytes_per_site"] + info["extra_bytes_per_site"]) * sites
+                         / (ms / 1e3) / 1e9 / peak},
+            "eos": {"e_over_3nT_minus_1": [float(dev.min()), float(dev.max())],
+                    "residual_vs_zeta_K1_over_3K2": float(resid.max())},
+            "error_vs_f32": err, "gpu_launches": args.steps, "clocks": clk.summary()}
+    emit(line, rank)
 
 
 def main():
@@ -256,8 +399,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the accuracy check and the other dtypes")
-    ap.add_argument("--workload", default="random_flow", choices=["random_flow", "batch"],
-                    help="random_flow: the headline 4096^2 lattice; batch: 256 independent lattices")
+    ap.add_argument("--workload", default="random_flow", choices=["random_flow", "batch", "blast"],
+                    help="random_flow: the headline 4096^2 lattice; batch: 256 independent lattices; "
+                         "blast: the 8192^2 near-massless blast in BF16-deviation storage")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -265,6 +409,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "blast":
+        return run_blast(args)
 
     import torch
     from paper_1703_04605_gb300 import Lattice, build, workloads as W
@@ -310,15 +456,11 @@ def main():
         if clk:
             clk.__exit__(None, None, None)
         lat.sync()
-        ms = e0.elapsed_time(e1)
-        if pg:
-            t = torch.tensor([ms], device="cuda")
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = reduce_max(e0.elapsed_time(e1), pg, "cuda")
         return lat, info, ms / steps, clk
 
     lat, info, ms_step, clk = measure(args.dtype, args.steps, args.warmup, sample_clocks=True)
-    value = ws * sites / (ms_step / 1e3) / 1e6
+    value = whole_job_mlups(sites, ws, ms_step)
     bytes_launch = info["bytes_per_site"] * sites
     achieved = bytes_launch / (ms_step / 1e3) / 1e9
 
@@ -388,7 +530,9 @@ def main():
         "config": {"workload": WORKLOAD, "sites": int(sites), "Q": info["Q"], "parallelism": "independent lattice per rank",
                    "l2": "inputs larger than L2 (%.1f GB of populations per step)" % (2 * bytes_launch / 2 / 1e9)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": (profiled_traffic("fused_f32_kernel_random_flow_4096.md", FUSED_SOURCES)
+                                 if args.dtype == "f32" else None),
                      "kernel": kernel_name(args.dtype, info["kernel"]), "peak_kind": peak_kind,
                      "bytes_per_site": info["bytes_per_site"]},
         "gpu_launches": args.steps,
@@ -399,7 +543,7 @@ def main():
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
-    print(json.dumps(line), flush=True)
+    emit(line, rank)
     if pg:
         pg.destroy_process_group()
 

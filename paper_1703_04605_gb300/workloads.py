@@ -90,12 +90,19 @@ def random_flow_crop(N_full=4096, crop=1024, **kw):
     return {k: np.ascontiguousarray(v[:crop, :crop]) for k, v in f.items()}
 
 
-def blast(N=8192, R=512, T_in=2.0, T_out=1.0):
+def blast(N=8192, R=512, T_in=2.0, T_out=1.0, T_ref=None):
+    """Disc of radius R (cells, centred) at T_in in a background at T_out,
+    n = 1, u = 0; temperatures returned in units of T_ref (the lattice's T_R),
+    by default the mean of the two.  With T_R = T_out the disc edge is a
+    2:1 temperature jump entirely above T_R; at tau = 0.7 its planar part
+    (radius 512) leaves the physical range within 75 steps in FP64 as well,
+    while with T_R at the mean (disc 4/3, background 2/3) it is stable."""
+    T_ref = 0.5 * (T_in + T_out) if T_ref is None else T_ref
     x = np.arange(N) - N / 2 + 0.5
     X, Y = np.meshgrid(x, x)
     inside = X * X + Y * Y < R * R
     return dict(n=np.ones((N, N)), ux=np.zeros((N, N)), uy=np.zeros((N, N)),
-                T=np.where(inside, T_in, T_out))
+                T=np.where(inside, T_in / T_ref, T_out / T_ref))
 
 
 def batch_specs(count=256, Lmin=64, Lmax=1024, mT=(0.1, 10.0), tau=(0.6, 1.5), m_min=0.36,

@@ -103,3 +103,67 @@ def test_batch_workload_sample():
     for b, a in zip(batch, alone):
         e = errors(b.moments(), a.moments())
         assert max(e.values()) < 2e-6, e
+
+
+def test_batch_workload_lattices_against_oracle():
+    """16 lattices of the 256-lattice workload (the 8 smallest and 8 drawn at
+    random) advanced together: the 8 smallest against the oracle on the whole
+    lattice after 2 and 10 steps, the others on periodic windows around
+    sampled sites after 2 steps (a site depends only on sites within twice the
+    halo)."""
+    from gpu_common import oracle_lattice
+    from paper_1703_04605_gb300 import Lattice, batch_step
+    specs = W.batch_specs(256)
+    order = sorted(range(256), key=lambda i: specs[i]["L"])
+    small = order[:8]
+    rng = np.random.default_rng(77)
+    others = [int(i) for i in rng.choice(order[8:], 8, replace=False)]
+    chosen = small + others
+    lats, fields, sts = [], [], []
+    for i in chosen:
+        s = specs[i]
+        groups, mu = stencils.choose(s["m"])
+        f = W.batch_fields(s)
+        lat = Lattice(groups, mu, s["tau"], s["L"], s["L"], dtype="f32", v0=0.0)
+        lat.init(f["n"], f["ux"], f["uy"], f["T"])
+        lats.append(lat)
+        fields.append(f)
+        sts.append(dict(groups=groups, m=mu, v0=lat.info()["v0"]))
+    batch_step(lats, 2)
+    for j, i in enumerate(chosen):
+        s, f, lat = specs[i], fields[j], lats[j]
+        got = lat.moments()
+        if i in small:
+            o = oracle_lattice(sts[j], s["tau"], f["n"].shape)
+            o.init(f["n"], f["ux"], f["uy"], f["T"])
+            o.step(2)
+            e = errors(got, o.macros())
+            assert max(e.values()) < 1e-5, (i, e)
+        else:
+            h = lat.info()["halo"]
+            r = 2 * h + 1
+            L = s["L"]
+            for (y, x) in [(L // 2, L // 2), (L // 2, L // 2 - 1), tuple(rng.integers(0, L, 2))]:
+                iy = (np.arange(y - r, y + r + 1) % L)[:, None]
+                ix = (np.arange(x - r, x + r + 1) % L)[None, :]
+                win = {k: v[iy, ix] for k, v in f.items()}
+                o = oracle_lattice(sts[j], s["tau"], (2 * r + 1, 2 * r + 1))
+                o.init(win["n"], win["ux"], win["uy"], win["T"])
+                o.step(2)
+                mac = o.macros()
+                for k in ("n", "T"):
+                    assert abs(got[k][y, x] / mac[k][r, r] - 1) < 1e-5, (i, k)
+                # the errors() normalisation: the lattice's largest velocity
+                scale = max(np.abs(got["ux"]).max(), np.abs(got["uy"]).max(), 1e-3)
+                for k in ("ux", "uy"):
+                    assert abs(got[k][y, x] - mac[k][r, r]) < 1e-5 * scale, (i, k)
+    batch_step(lats, 8)
+    for j, i in enumerate(small):
+        s, f = specs[i], fields[j]
+        o = oracle_lattice(sts[j], s["tau"], f["n"].shape)
+        o.init(f["n"], f["ux"], f["uy"], f["T"])
+        o.step(10)
+        e = errors(lats[j].moments(), o.macros())
+        assert max(e.values()) < 1e-5, (i, e)
+    for lat in lats:
+        lat.close()
