@@ -231,8 +231,9 @@ def run_batch(args):
     """256 independent periodic lattices (sides log-uniform in 64..1024, m/T
     log-uniform in 0.1..10 mapped onto the stencil library, tau in 0.6..1.5,
     Sod tubes and Taylor-Green vortices), FP32.  Batched arm: one batched call
-    of K steps (graph-captured launches) after a warm-up call that runs the
-    autotuner.  One-at-a-time arm: a second, freshly initialised copy of the
+    of K steps (replays of one CUDA graph holding every lattice's chain of
+    step kernels) after a warm-up call that runs the autotuner.
+    One-at-a-time arm: a second, freshly initialised copy of the
     same lattices, each advanced K steps by its own rlbm_step calls."""
     import torch
     from paper_1703_04605_gb300 import Lattice, batch_step, batch_tuning, build, stencils, workloads as W
@@ -274,7 +275,7 @@ def run_batch(args):
     for lat in lats:
         k = names.get(lat.info()["kernel"], "?")
         kinds[k] = kinds.get(k, 0) + 1
-    warm = max(args.warmup, 16)                # the first call also autotunes (12 steps)
+    warm = max(args.warmup, 48)                # the first call also autotunes (42 steps)
     batch_step(lats, warm)
     torch.cuda.synchronize()
     clk = ClockSampler(local)
@@ -308,7 +309,7 @@ def run_batch(args):
             "batched_over_one_at_a_time": ms_1 / ms_b,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak[0], "unit": "GB/s",
                          "frac": achieved / peak[0], "peak_kind": peak[1], "traffic": None},
-            "gpu_launches": tune["launches"] * args.steps,
+            "gpu_launches": tune["launches_per_step"] * args.steps,
             "clocks": clk.summary()}
     emit(line, rank)
 
@@ -395,7 +396,9 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64", "bf16dev"])
+    ap.add_argument("--side", type=int, default=N_SIDE,
+                    help="random_flow only: time a side x side crop of the 4096^2 field (profiling of small cases)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the accuracy check and the other dtypes")
@@ -430,13 +433,14 @@ def main():
         torch.cuda.synchronize()
 
     st = W.STENCIL_M1
-    f = W.random_flow(N_SIDE)
+    side = args.side
+    f = W.random_flow(N_SIDE) if side == N_SIDE else W.random_flow_crop(N_SIDE, side)
     stream = torch.cuda.Stream()
-    sites = float(N_SIDE) * N_SIDE
+    sites = float(side) * side
     peak, peak_kind = _peaks()
 
     def measure(dtype, steps, warmup, sample_clocks=False):
-        lat = Lattice(st["groups"], st["m"], TAU, N_SIDE, N_SIDE, dtype=dtype, v0=st["v0"],
+        lat = Lattice(st["groups"], st["m"], TAU, side, side, dtype=dtype, v0=st["v0"],
                       stream=stream.cuda_stream)
         info = lat.info()
         lat.init(f["n"], f["ux"], f["uy"], f["T"])
@@ -477,7 +481,7 @@ def main():
     if rank == 0 and not args.no_extra:
         got = lat.moments()
         nsteps = args.warmup + args.steps
-        with Lattice(st["groups"], st["m"], TAU, N_SIDE, N_SIDE, dtype="f64", v0=st["v0"]) as ref:
+        with Lattice(st["groups"], st["m"], TAU, side, side, dtype="f64", v0=st["v0"]) as ref:
             ref.init(f["n"], f["ux"], f["uy"], f["T"])
             ref.step(nsteps)
             rm = ref.moments()
@@ -526,13 +530,14 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sites": int(sites), "Q": info["Q"], "parallelism": "independent lattice per rank",
+        "vs_baseline": None, "dtype": {"bf16dev": "bf16"}.get(args.dtype, args.dtype), "data": "synthetic",
+        "config": {"workload": WORKLOAD if side == N_SIDE else "%dx%d crop of: %s" % (side, side, WORKLOAD),
+                   "sites": int(sites), "Q": info["Q"], "parallelism": "independent lattice per rank",
                    "l2": "inputs larger than L2 (%.1f GB of populations per step)" % (2 * bytes_launch / 2 / 1e9)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": (profiled_traffic("fused_f32_kernel_random_flow_4096.md", FUSED_SOURCES)
-                                 if args.dtype == "f32" else None),
+                                 if args.dtype == "f32" and side == N_SIDE else None),
                      "kernel": kernel_name(args.dtype, info["kernel"]), "peak_kind": peak_kind,
                      "bytes_per_site": info["bytes_per_site"]},
         "gpu_launches": args.steps,

@@ -152,29 +152,30 @@ void rlbm_destroy(rlbm_ctx* ctx);
 
 /* Advance count contexts by nsteps each, as one batch (the independent
  * lattices of a parameter sweep or an ensemble).  Equivalent to calling
- * rlbm_step(ctxs[i], nsteps) for every i, but the lattices of one stencil
- * advance together in the same launches (up to 30 lattices per launch, their
- * parameters in the launch's constant bank), and the launches of two steps
- * are captured once into a CUDA graph that is replayed.  An autotuner picks
- * the occupancy variant and the number of lattices per launch by timing the
- * first steps of the first call for a given batch (those steps count towards
- * nsteps), and caches the choice.
- * Requirements: every context initialised, FP32 storage, a compiled stencil
- * (rlbm_info.kernel != 0), all on the same CUDA stream, no context listed
- * twice.  Asynchronous on that stream (a NULL stream is bridged to an
- * internal stream with events).  Errors: EINVAL (violated requirement),
- * ENOTSUP, ECUDA. */
+ * rlbm_step(ctxs[i], nsteps) for every i, with identical results.  The steps
+ * run as replays of one CUDA graph per batch that holds, for every lattice, a
+ * chain of G step kernels (step k+1 of a lattice depends on its step k) and
+ * no dependency between lattices, so the GPU overlaps the lattices' kernels;
+ * each kernel is the single-lattice step kernel with that lattice's
+ * parameters.  An autotuner picks G in {2, 8, 32} by timing one replay of
+ * each on the first call for a batch with nsteps >= 42 (those steps count
+ * towards nsteps) and caches the choice; rlbm_batch_tuning reports it.
+ * Graphs are cached per batch and buffer parity; rlbm_init or rlbm_destroy of
+ * a member drops them.  Requirements: every context initialised, FP32 or
+ * BF16-deviation storage, a compiled stencil (rlbm_info.kernel != 0), all on
+ * the same CUDA stream, no context listed twice.  Asynchronous on that stream
+ * (a NULL stream is bridged to an internal stream with events).  Not
+ * thread-safe against rlbm_step on the same contexts.  The paper has no
+ * counterpart (it advances one lattice at a time).  Errors: EINVAL (violated
+ * requirement), ENOTSUP, ECUDA. */
 rlbm_status rlbm_batch_step(rlbm_ctx* const* ctxs, int count, int nsteps);
 
-/* The autotuner's choice for a batch that rlbm_batch_step has already
- * advanced (same contexts, same order): *minb = minimum resident blocks per
- * SM of the kernel variant (4 or 5), *per_launch = lattices per launch,
- * *launches = kernel launches of one step (one per stencil kind and chunk of
- * per_launch lattices).  Any output pointer may be NULL.  Never touches the
- * device.  Errors: EINVAL (bad arguments, or no choice cached for this
- * batch).  The paper has no counterpart; it reports how the batch runs. */
-rlbm_status rlbm_batch_tuning(rlbm_ctx* const* ctxs, int count, int* minb, int* per_launch,
-                              int* launches);
+/* The autotuner's choice for a batch that rlbm_batch_step has tuned (same
+ * contexts, same order): *steps_per_graph = G, *launches_per_step = kernel
+ * launches of one step (one per lattice).  Either output pointer may be
+ * NULL.  Never touches the device.  Errors: EINVAL (bad arguments, or no
+ * choice cached for this batch). */
+rlbm_status rlbm_batch_tuning(rlbm_ctx* const* ctxs, int count, int* steps_per_graph, int* launches_per_step);
 
 /* ---- read-out without memory allocation -------------------------------
  * The paper has no counterpart of this entry point; it serves callers that

@@ -77,8 +77,7 @@ def load():
         "rlbm_bessel_ratio": (C.c_double, [C.c_double, C.c_int]),
         "rlbm_version": (C.c_char_p, []),
         "rlbm_batch_step": (C.c_int, [C.POINTER(P), C.c_int, C.c_int]),
-        "rlbm_batch_tuning": (C.c_int, [C.POINTER(P), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
-                                        C.POINTER(C.c_int)]),
+        "rlbm_batch_tuning": (C.c_int, [C.POINTER(P), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "rlbm_moments_noalloc": (C.c_int, [ip, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, P, dp,
                                            C.c_uint, P]),
     }

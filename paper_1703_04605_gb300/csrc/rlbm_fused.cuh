@@ -313,28 +313,12 @@ __global__ void __launch_bounds__(128, (Def::Q <= 64 && !BF) ? 5 : 4) fused_f32_
   report(fl, p.err);
 }
 
-template <class Def, bool BF, int MINB>
-__global__ void __launch_bounds__(128, MINB) fused_batch_kernel(const __grid_constant__ BatchParams bp) {
-  const int b = blockIdx.x;
-  int l = 0;
-#pragma unroll 1
-  while (l + 1 < bp.n && bp.start[l + 1] <= b) ++l;
-  const BatchLattice& L = bp.lat[l];
-  const int site = (b - bp.start[l]) * 128 + threadIdx.x;
-  unsigned fl = 0;
-  if (site < L.p.Nx * L.p.Ny) fused_site<Def, BF>(L.p, L.fin, L.fout, site, fl);
-  report(fl, L.p.err);
-}
-
+// Entry point of the step kernel of a stencil, for CUDA graph kernel nodes
+// (rlbm_batch_step); the node's grid is (Nx Ny + 127)/128 blocks of 128.
 template <class Def>
-cudaError_t launch_batch_impl(const BatchParams& bp, int minb, cudaStream_t s) {
-  const unsigned grid = (unsigned)bp.start[bp.n];
-  if (grid == 0) return cudaSuccess;
-  if (minb == 5) fused_batch_kernel<Def, false, 5><<<grid, 128, 0, s>>>(bp);
-  else fused_batch_kernel<Def, false, 4><<<grid, 128, 0, s>>>(bp);
-  return cudaGetLastError();
+const void* fused_kernel_fn_impl(bool bf16) {
+  return bf16 ? (const void*)&fused_f32_kernel<Def, true> : (const void*)&fused_f32_kernel<Def, false>;
 }
-
 
 }  // namespace rlbm
 

@@ -17,7 +17,7 @@ cudaError_t launch_bf16_io<StencilE5>(int what, const FusedParams& fp, const Ste
   return launch_bf16_io_impl<StencilE5>(what, fp, p, fd, cur, prev, ccur, cprev, mo, s);
 }
 template <>
-cudaError_t launch_batch<StencilE5>(const BatchParams& bp, int minb, cudaStream_t s) {
-  return launch_batch_impl<StencilE5>(bp, minb, s);
+const void* fused_kernel_fn<StencilE5>(bool bf16) {
+  return fused_kernel_fn_impl<StencilE5>(bf16);
 }
 }  // namespace rlbm

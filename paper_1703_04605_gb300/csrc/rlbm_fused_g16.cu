@@ -17,7 +17,7 @@ cudaError_t launch_bf16_io<StencilG16>(int what, const FusedParams& fp, const St
   return launch_bf16_io_impl<StencilG16>(what, fp, p, fd, cur, prev, ccur, cprev, mo, s);
 }
 template <>
-cudaError_t launch_batch<StencilG16>(const BatchParams& bp, int minb, cudaStream_t s) {
-  return launch_batch_impl<StencilG16>(bp, minb, s);
+const void* fused_kernel_fn<StencilG16>(bool bf16) {
+  return fused_kernel_fn_impl<StencilG16>(bf16);
 }
 }  // namespace rlbm

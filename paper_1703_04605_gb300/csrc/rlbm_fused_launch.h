@@ -18,19 +18,18 @@ cudaError_t launch_fused<StencilE5>(const FusedParams&, const void*, void*, bool
 template <>
 cudaError_t launch_fused<StencilS2>(const FusedParams&, const void*, void*, bool, cudaStream_t);
 
-// Batched FP32 step over up to kBatchMax lattices of one stencil (minb: 4 or 5
-// resident blocks per SM, i.e. 128 or 96 registers).
-struct BatchParams;
+// The step kernel itself (FusedParams, const void* fin, void* fout), for graph
+// kernel nodes; grid (Nx Ny + 127)/128, block 128, no dynamic shared memory.
 template <class Def>
-cudaError_t launch_batch(const BatchParams& bp, int minb, cudaStream_t s);
+const void* fused_kernel_fn(bool bf16);
 template <>
-cudaError_t launch_batch<StencilM1>(const BatchParams&, int, cudaStream_t);
+const void* fused_kernel_fn<StencilM1>(bool);
 template <>
-cudaError_t launch_batch<StencilG16>(const BatchParams&, int, cudaStream_t);
+const void* fused_kernel_fn<StencilG16>(bool);
 template <>
-cudaError_t launch_batch<StencilE5>(const BatchParams&, int, cudaStream_t);
+const void* fused_kernel_fn<StencilE5>(bool);
 template <>
-cudaError_t launch_batch<StencilS2>(const BatchParams&, int, cudaStream_t);
+const void* fused_kernel_fn<StencilS2>(bool);
 // BF16 deviation storage: what = 0 init (fields -> coefficients, S_0, S_{-1}),
 // what = 1 read-out of the pull of prev.
 template <class Def>

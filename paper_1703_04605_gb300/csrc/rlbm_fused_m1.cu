@@ -17,7 +17,7 @@ cudaError_t launch_bf16_io<StencilM1>(int what, const FusedParams& fp, const Ste
   return launch_bf16_io_impl<StencilM1>(what, fp, p, fd, cur, prev, ccur, cprev, mo, s);
 }
 template <>
-cudaError_t launch_batch<StencilM1>(const BatchParams& bp, int minb, cudaStream_t s) {
-  return launch_batch_impl<StencilM1>(bp, minb, s);
+const void* fused_kernel_fn<StencilM1>(bool bf16) {
+  return fused_kernel_fn_impl<StencilM1>(bf16);
 }
 }  // namespace rlbm

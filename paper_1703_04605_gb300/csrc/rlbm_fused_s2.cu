@@ -17,7 +17,7 @@ cudaError_t launch_bf16_io<StencilS2>(int what, const FusedParams& fp, const Ste
   return launch_bf16_io_impl<StencilS2>(what, fp, p, fd, cur, prev, ccur, cprev, mo, s);
 }
 template <>
-cudaError_t launch_batch<StencilS2>(const BatchParams& bp, int minb, cudaStream_t s) {
-  return launch_batch_impl<StencilS2>(bp, minb, s);
+const void* fused_kernel_fn<StencilS2>(bool bf16) {
+  return fused_kernel_fn_impl<StencilS2>(bf16);
 }
 }  // namespace rlbm

@@ -267,8 +267,8 @@ rlbm_status rlbm_create(const rlbm_stencil* st, double m, double tau, int Nx, in
     if (!c->fused) {
       release(c.get());
       return fail(nullptr, RLBM_ENOTSUP,
-                  "BF16 deviation storage needs a compiled stencil ({5,12,14,17,21,26}, {1..6} or "
-                  "{1,14,49,51,60,70}) and Nx, Ny >= its halo");
+                  "BF16 deviation storage needs a compiled stencil ({5,12,14,17,21,26}, {1..6}, "
+                  "{1,14,49,51,60,70} or {3,9,10,14,17,21}) and Nx, Ny >= its halo");
     }
     const size_t cbytes = (size_t)6 * (size_t)c->plane * 8;
     for (int b = 0; b < 2; ++b) {
@@ -468,82 +468,133 @@ double rlbm_bessel_ratio(double zeta, int precision) { return ratio_eval_host(ze
 }  // extern "C"
 
 // ------------------------------------------------------------------ batches
+// Independent lattices advanced together: one CUDA graph per batch holds, for
+// every lattice, a chain of G step-kernel nodes (step k+1 depends on step k
+// of the same lattice) and no edge between lattices, so the GPU overlaps the
+// chains; each node runs the single-lattice kernel with that lattice's
+// parameters in its own constant bank.  G (steps per graph) is autotuned.
 namespace {
 
-struct BatchLaunch {
-  int kind;
-  BatchParams bp;
+const void* kernel_of(const rlbm_ctx* c) {
+  const bool bf = c->dtype == RLBM_BF16_DEV;
+  switch (c->fused) {
+    case 1: return fused_kernel_fn<StencilM1>(bf);
+    case 2: return fused_kernel_fn<StencilG16>(bf);
+    case 3: return fused_kernel_fn<StencilE5>(bf);
+    default: return fused_kernel_fn<StencilS2>(bf);
+  }
+}
+
+// Arguments of the k-th step from now (buffers by parity).
+struct NodeArgs {
+  FusedParams p;
+  const void* fin;
+  void* fout;
 };
 
+NodeArgs args_of(const rlbm_ctx* c, int k) {
+  const int cur = c->cur ^ (k & 1);
+  NodeArgs a;
+  a.p = *c->fp;
+  a.p.cin = c->coef[cur];
+  a.p.cout = c->coef[1 - cur];
+  a.fin = c->buf[cur];
+  a.fout = c->buf[1 - cur];
+  return a;
+}
+
+unsigned grid_of(const rlbm_ctx* c) { return (unsigned)(((long long)c->Nx * c->Ny + 127) / 128); }
+
 struct BatchPlan {
-  std::vector<rlbm_ctx*> ctxs;
-  std::vector<int> parity;                 // cur of each context when built
-  int minb = 5, lmax = kBatchMax;
-  cudaGraphExec_t two = nullptr;           // two consecutive steps
-  std::vector<BatchLaunch> step[2];
+  int gsteps = 0;
+  cudaGraphExec_t exec = nullptr;
 };
 
 std::mutex g_batch_mutex;
-std::map<std::string, int> g_tuned;        // batch signature -> (minb << 8) | lmax
-std::map<std::string, std::unique_ptr<BatchPlan>> g_plans;
+std::map<std::string, int> g_tuned;          // batch signature -> steps per graph
+std::map<std::string, BatchPlan> g_plans;    // signature with parities and G -> graph
 
 std::string signature(rlbm_ctx* const* ctxs, int n, bool with_parity) {
   std::string s;
   for (int i = 0; i < n; ++i) {
     char b[64];
-    std::snprintf(b, sizeof b, "%p:%d:%d;", (void*)ctxs[i], ctxs[i]->fused, with_parity ? ctxs[i]->cur : 0);
+    std::snprintf(b, sizeof b, "%p:%d:%d:%d;", (void*)ctxs[i], ctxs[i]->fused, (int)ctxs[i]->dtype,
+                  with_parity ? ctxs[i]->cur : 0);
     s += b;
   }
   return s;
 }
 
-cudaError_t launch_kind(int kind, const BatchParams& bp, int minb, cudaStream_t s) {
-  switch (kind) {
-    case 1: return launch_batch<StencilM1>(bp, minb, s);
-    case 2: return launch_batch<StencilG16>(bp, minb, s);
-    case 3: return launch_batch<StencilE5>(bp, minb, s);
-    default: return launch_batch<StencilS2>(bp, minb, s);
-  }
-}
-
-// Launches of one step: lattices grouped by stencil, largest first, at most
-// lmax per launch.  k = 0 or 1 selects the buffer parity relative to now.
-std::vector<BatchLaunch> build_step(const std::vector<rlbm_ctx*>& v, int k, int lmax) {
-  std::vector<rlbm_ctx*> order(v);
-  std::stable_sort(order.begin(), order.end(), [](rlbm_ctx* a, rlbm_ctx* b) {
-    if (a->fused != b->fused) return a->fused < b->fused;
+// Lattices by decreasing size: the chains of the largest lattices are
+// created (and so issued) first.
+std::vector<rlbm_ctx*> by_size(const std::vector<rlbm_ctx*>& v) {
+  std::vector<rlbm_ctx*> o(v);
+  std::stable_sort(o.begin(), o.end(), [](rlbm_ctx* a, rlbm_ctx* b) {
     return (long long)a->Nx * a->Ny > (long long)b->Nx * b->Ny;
   });
-  std::vector<BatchLaunch> out;
-  for (size_t i = 0; i < order.size();) {
-    BatchLaunch L;
-    std::memset(&L.bp, 0, sizeof L.bp);
-    L.kind = order[i]->fused;
-    int n = 0, blocks = 0;
-    while (i < order.size() && n < lmax && order[i]->fused == L.kind) {
-      rlbm_ctx* c = order[i];
-      const int cur = c->cur ^ k;
-      BatchLattice& bl = L.bp.lat[n];
-      bl.p = *c->fp;
-      bl.fin = c->buf[cur];
-      bl.fout = c->buf[1 - cur];
-      L.bp.start[n] = blocks;
-      blocks += (int)(((long long)c->Nx * c->Ny + 127) / 128);
-      ++n;
-      ++i;
-    }
-    L.bp.n = n;
-    L.bp.start[n] = blocks;
-    out.push_back(L);
-  }
-  return out;
+  return o;
 }
 
-cudaError_t run_launches(const std::vector<BatchLaunch>& ls, int minb, cudaStream_t s) {
-  for (const BatchLaunch& L : ls) {
-    cudaError_t e = launch_kind(L.kind, L.bp, minb, s);
+cudaError_t build_graph(const std::vector<rlbm_ctx*>& v, int gsteps, cudaStream_t s, BatchPlan& plan) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return e;
+  for (rlbm_ctx* c : by_size(v)) {
+    cudaGraphNode_t prev = nullptr;
+    for (int k = 0; k < gsteps && e == cudaSuccess; ++k) {
+      NodeArgs a = args_of(c, k);
+      void* params[3] = {&a.p, &a.fin, &a.fout};
+      cudaKernelNodeParams kp = {};
+      kp.func = const_cast<void*>(kernel_of(c));
+      kp.gridDim = dim3(grid_of(c));
+      kp.blockDim = dim3(128);
+      kp.sharedMemBytes = 0;
+      kp.kernelParams = params;
+      cudaGraphNode_t node = nullptr;
+      e = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+      prev = node;
+    }
+    if (e != cudaSuccess) break;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&plan.exec, g, 0);
+  if (e == cudaSuccess) e = cudaGraphUpload(plan.exec, s);
+  cudaGraphDestroy(g);
+  plan.gsteps = gsteps;
+  return e;
+}
+
+cudaError_t single_step(const std::vector<rlbm_ctx*>& v, cudaStream_t s) {
+  for (rlbm_ctx* c : by_size(v)) {
+    NodeArgs a = args_of(c, 0);
+    void* params[3] = {&a.p, &a.fin, &a.fout};
+    cudaError_t e = cudaLaunchKernel(kernel_of(c), dim3(grid_of(c)), dim3(128), params, 0, s);
     if (e != cudaSuccess) return e;
   }
+  return cudaSuccess;
+}
+
+void advance_all(const std::vector<rlbm_ctx*>& v, int k) {
+  for (rlbm_ctx* c : v) {
+    c->cur ^= (k & 1);
+    c->t += k;
+  }
+}
+
+// The graph for the contexts' current parities and G, built on first use.
+cudaError_t plan_for(rlbm_ctx* const* ctxs, int count, const std::vector<rlbm_ctx*>& v, int gsteps,
+                     cudaStream_t s, BatchPlan** out) {
+  const std::string key = signature(ctxs, count, true) + "/" + std::to_string(gsteps);
+  auto it = g_plans.find(key);
+  if (it == g_plans.end()) {
+    BatchPlan plan;
+    cudaError_t e = build_graph(v, gsteps, s, plan);
+    if (e != cudaSuccess) {
+      if (plan.exec) cudaGraphExecDestroy(plan.exec);
+      return e;
+    }
+    it = g_plans.emplace(key, plan).first;
+  }
+  *out = &it->second;
   return cudaSuccess;
 }
 
@@ -555,7 +606,7 @@ static void batch_forget(const rlbm_ctx* c) {
   std::snprintf(b, sizeof b, "%p:", (const void*)c);
   for (auto it = g_plans.begin(); it != g_plans.end();) {
     if (it->first.find(b) != std::string::npos) {
-      if (it->second->two) cudaGraphExecDestroy(it->second->two);
+      if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
       it = g_plans.erase(it);
     } else {
       ++it;
@@ -573,8 +624,8 @@ extern "C" rlbm_status rlbm_batch_step(rlbm_ctx* const* ctxs, int count, int nst
   for (int i = 0; i < count; ++i) {
     rlbm_ctx* c = ctxs[i];
     if (!c || !c->initialised) return fail(nullptr, RLBM_EINVAL, "batch: a context is missing or not initialised");
-    if (c->dtype != RLBM_F32 || !c->fused)
-      return fail(nullptr, RLBM_ENOTSUP, "batch: every context needs FP32 storage and a compiled stencil");
+    if ((c->dtype != RLBM_F32 && c->dtype != RLBM_BF16_DEV) || !c->fused)
+      return fail(nullptr, RLBM_ENOTSUP, "batch: every context needs FP32 or BF16 storage and a compiled stencil");
     if (c->stream != ctxs[0]->stream) return fail(nullptr, RLBM_EINVAL, "batch: contexts on different streams");
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == c) return fail(nullptr, RLBM_EINVAL, "batch: a context is listed twice");
@@ -582,14 +633,14 @@ extern "C" rlbm_status rlbm_batch_step(rlbm_ctx* const* ctxs, int count, int nst
   if (nsteps == 0) return RLBM_OK;
   std::vector<rlbm_ctx*> v(ctxs, ctxs + count);
   cudaStream_t user = ctxs[0]->stream;
-  // stream capture needs a non-legacy stream: bridge a NULL stream with events
+  // graph launches need a non-legacy stream: bridge a NULL stream with events
   static cudaStream_t bridge = nullptr;
   cudaStream_t s = user;
   struct Events {
-    cudaEvent_t in = nullptr, out = nullptr;
+    cudaEvent_t in = nullptr, out = nullptr, a = nullptr, b = nullptr;
     ~Events() {
-      if (in) cudaEventDestroy(in);
-      if (out) cudaEventDestroy(out);
+      for (cudaEvent_t e : {in, out, a, b})
+        if (e) cudaEventDestroy(e);
     }
   } ev;
   cudaError_t e = cudaSuccess;
@@ -602,89 +653,58 @@ extern "C" rlbm_status rlbm_batch_step(rlbm_ctx* const* ctxs, int count, int nst
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch stream bridge");
     s = bridge;
   }
-  auto advance = [&](int k) {
-    for (rlbm_ctx* c : v) {
-      c->cur ^= (k & 1);
-      c->t += k;
-    }
-  };
   const std::string sig = signature(ctxs, count, false);
   int done = 0;
-  // autotune on the first steps of the first call for this batch
+  int G = 0;
   auto tuned = g_tuned.find(sig);
-  int minb = 5, lmax = kBatchMax;
   if (tuned != g_tuned.end()) {
-    minb = tuned->second >> 8;
-    lmax = tuned->second & 0xff;
+    G = tuned->second;
   } else {
-    const int cand_minb[2] = {5, 4};
-    const int cand_lmax[3] = {8, 16, kBatchMax};
-    const int per = 2;
-    if (nsteps >= per * 6 + 1) {
+    // autotune: one replay of each candidate graph, timed; those steps count
+    const int cand[3] = {2, 8, 32};
+    const int total = cand[0] + cand[1] + cand[2];
+    if (nsteps >= total) {
+      e = cudaEventCreate(&ev.a);
+      if (e == cudaSuccess) e = cudaEventCreate(&ev.b);
       float best = 1e30f;
-      cudaEvent_t a, b;
-      cudaEventCreate(&a);
-      cudaEventCreate(&b);
-      for (int im = 0; im < 2 && e == cudaSuccess; ++im)
-        for (int il = 0; il < 3; ++il) {
-          cudaEventRecord(a, s);
-          for (int k = 0; k < per; ++k) {
-            e = run_launches(build_step(v, 0, cand_lmax[il]), cand_minb[im], s);
-            if (e != cudaSuccess) break;
-            advance(1);
-          }
-          cudaEventRecord(b, s);
-          cudaEventSynchronize(b);
-          float ms = 0;
-          cudaEventElapsedTime(&ms, a, b);
-          done += per;
-          if (e != cudaSuccess) break;
-          if (ms < best) {
-            best = ms;
-            minb = cand_minb[im];
-            lmax = cand_lmax[il];
-          }
+      for (int g : cand) {
+        BatchPlan* pl = nullptr;
+        if (e == cudaSuccess) e = plan_for(ctxs, count, v, g, s, &pl);
+        if (e == cudaSuccess) e = cudaEventRecord(ev.a, s);
+        if (e == cudaSuccess) e = cudaGraphLaunch(pl->exec, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev.b, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev.b);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev.a, ev.b);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch autotune");
+        advance_all(v, g);
+        done += g;
+        if (ms / g < best) {
+          best = ms / g;
+          G = g;
         }
-      cudaEventDestroy(a);
-      cudaEventDestroy(b);
-      if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch autotune");
+      }
+      g_tuned[sig] = G;
+    } else {
+      G = nsteps >= cand[1] ? cand[1] : cand[0];   // too few steps to tune: not cached
     }
-    g_tuned[sig] = (minb << 8) | lmax;
   }
-  // graph of two consecutive steps for the current buffer parities
-  const std::string psig = signature(ctxs, count, true) + std::to_string(minb) + "/" + std::to_string(lmax);
-  auto it = g_plans.find(psig);
-  if (it == g_plans.end() && nsteps - done >= 2) {
-    std::unique_ptr<BatchPlan> plan(new BatchPlan);
-    plan->ctxs = v;
-    plan->minb = minb;
-    plan->lmax = lmax;
-    plan->step[0] = build_step(v, 0, lmax);
-    plan->step[1] = build_step(v, 1, lmax);
-    cudaGraph_t g = nullptr;
-    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-      cudaError_t e1 = run_launches(plan->step[0], minb, s);
-      cudaError_t e2 = run_launches(plan->step[1], minb, s);
-      e = cudaStreamEndCapture(s, &g);
-      if (e == cudaSuccess && e1 != cudaSuccess) e = e1;
-      if (e == cudaSuccess && e2 != cudaSuccess) e = e2;
+  for (int g : {G, 2}) {
+    if (nsteps - done < g) continue;
+    BatchPlan* pl = nullptr;
+    e = plan_for(ctxs, count, v, g, s, &pl);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch graph");
+    while (nsteps - done >= g) {
+      e = cudaGraphLaunch(pl->exec, s);
+      if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch graph launch");
+      advance_all(v, g);   // g is even: parities unchanged, the same graph serves again
+      done += g;
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&plan->two, g, 0);
-    if (g) cudaGraphDestroy(g);
-    if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch graph capture");
-    it = g_plans.emplace(psig, std::move(plan)).first;
-  }
-  while (nsteps - done >= 2) {
-    e = cudaGraphLaunch(it->second->two, s);
-    if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch graph launch");
-    advance(2);   // parity unchanged, so the same graph serves the next pair
-    done += 2;
   }
   if (nsteps - done == 1) {
-    e = run_launches(build_step(v, 0, lmax), minb, s);
+    e = single_step(v, s);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch step");
-    advance(1);
+    advance_all(v, 1);
     done += 1;
   }
   if (!user) {
@@ -695,21 +715,15 @@ extern "C" rlbm_status rlbm_batch_step(rlbm_ctx* const* ctxs, int count, int nst
   return RLBM_OK;
 }
 
-extern "C" rlbm_status rlbm_batch_tuning(rlbm_ctx* const* ctxs, int count, int* minb, int* per_launch,
-                                         int* launches) {
+extern "C" rlbm_status rlbm_batch_tuning(rlbm_ctx* const* ctxs, int count, int* steps_per_graph,
+                                         int* launches_per_step) {
   if (!ctxs || count < 1) return fail(nullptr, RLBM_EINVAL, "batch tuning: bad arguments");
   for (int i = 0; i < count; ++i)
     if (!ctxs[i]) return fail(nullptr, RLBM_EINVAL, "batch tuning: a context is missing");
   std::lock_guard<std::mutex> lock(g_batch_mutex);
   auto tuned = g_tuned.find(signature(ctxs, count, false));
-  if (tuned == g_tuned.end()) return fail(nullptr, RLBM_EINVAL, "batch tuning: this batch has not run");
-  const int lmax = tuned->second & 0xff;
-  std::map<int, int> per_kind;
-  for (int i = 0; i < count; ++i) per_kind[ctxs[i]->fused] += 1;
-  int n = 0;
-  for (const auto& kv : per_kind) n += (kv.second + lmax - 1) / lmax;
-  if (minb) *minb = tuned->second >> 8;
-  if (per_launch) *per_launch = lmax;
-  if (launches) *launches = n;
+  if (tuned == g_tuned.end()) return fail(nullptr, RLBM_EINVAL, "batch tuning: this batch has not been tuned");
+  if (steps_per_graph) *steps_per_graph = tuned->second;
+  if (launches_per_step) *launches_per_step = count;
   return RLBM_OK;
 }

@@ -121,21 +121,6 @@ struct FusedParams {
   void* cout;
 };
 
-// Batched launches: many independent lattices of one stencil in one launch.  Lattice l owns
-// blocks [start[l], start[l+1]); its parameters sit in the launch's constant
-// bank (read with a block-uniform index).
-struct BatchLattice {
-  FusedParams p;
-  const void* fin;
-  void* fout;
-};
-constexpr int kBatchMax = 30;
-struct BatchParams {
-  int n;
-  int start[kBatchMax + 1];
-  BatchLattice lat[kBatchMax];
-};
-
 // Device error bits (OR-ed into *err).
 enum : unsigned {
   ERR_LANDAU = 1u,   // Landau frame: non-finite or |u| >= 1

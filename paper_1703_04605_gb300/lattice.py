@@ -107,10 +107,10 @@ def batch_step(lattices, k=1):
 
 
 def batch_tuning(lattices):
-    """The autotuner's choice for a batch already advanced by batch_step:
-    dict(minb, per_launch, launches) -- launches = kernel launches per step."""
+    """The autotuner's choice for a batch already tuned by batch_step:
+    dict(steps_per_graph, launches_per_step)."""
     L = A.load()
     arr = (C.c_void_p * len(lattices))(*[lat._ctx.value for lat in lattices])
-    out = [C.c_int(0) for _ in range(3)]
+    out = [C.c_int(0) for _ in range(2)]
     A.check(L.rlbm_batch_tuning(arr, len(lattices), *[C.byref(o) for o in out]))
-    return dict(minb=out[0].value, per_launch=out[1].value, launches=out[2].value)
+    return dict(steps_per_graph=out[0].value, launches_per_step=out[1].value)

@@ -124,7 +124,7 @@ def test_null_context_calls(lib):
     assert lib.rlbm_moments_size(None, 1) == 0
     lib.rlbm_destroy(None)
     assert lib.rlbm_batch_step(None, 1, 1) == A.RLBM_EINVAL
-    assert lib.rlbm_batch_tuning(None, 1, None, None, None) == A.RLBM_EINVAL
+    assert lib.rlbm_batch_tuning(None, 1, None, None) == A.RLBM_EINVAL
     null2 = (C.c_void_p * 2)(None, None)
     assert lib.rlbm_batch_step(null2, 2, 1) == A.RLBM_EINVAL
-    assert lib.rlbm_batch_tuning(null2, 2, None, None, None) == A.RLBM_EINVAL
+    assert lib.rlbm_batch_tuning(null2, 2, None, None) == A.RLBM_EINVAL
