@@ -227,6 +227,43 @@ def run_reference(args):
     emit(line, rank)
 
 
+def batch_error_vs_f64(specs, lats, nsteps, stream):
+    """Untimed: every lattice of the batch advanced nsteps on the FP64 path
+    from the same fields, against the batched FP32 result.  n and T: max
+    relative error; u: max |du| over the larger of the lattice's largest FP64
+    velocity and its initial velocity scale (u0 for a vortex, 0.05 for a
+    tube, whose flow can die out within the run)."""
+    from paper_1703_04605_gb300 import Lattice, stencils, workloads as W
+    worst = {"n": 0.0, "T": 0.0, "u": 0.0}
+    where = {}
+    over = 0
+    listed = []
+    for i, (s, lat) in enumerate(zip(specs, lats)):
+        groups, mu = stencils.choose(s["m"])
+        f = W.batch_fields(s)
+        got = lat.moments()
+        with Lattice(groups, mu, s["tau"], s["L"], s["L"], dtype="f64", v0=lat.info()["v0"],
+                     stream=stream.cuda_stream) as ref:
+            ref.init(f["n"], f["ux"], f["uy"], f["T"])
+            ref.step(nsteps)
+            rm = ref.moments()
+        scale = max(np.abs(rm["ux"]).max(), np.abs(rm["uy"]).max(), s.get("u0", 0.05))
+        e = {"n": float(np.max(np.abs(got["n"] / rm["n"] - 1))),
+             "T": float(np.max(np.abs(got["T"] / rm["T"] - 1))),
+             "u": float(max(np.abs(got["ux"] - rm["ux"]).max(), np.abs(got["uy"] - rm["uy"]).max()) / scale)}
+        if max(e.values()) > 1e-5:
+            over += 1
+            listed.append([i, s["kind"], s["L"], round(s["m"], 3), round(s["tau"], 3),
+                           float("%.2g" % e["n"]), float("%.2g" % e["T"]), float("%.2g" % e["u"])])
+        for k in worst:
+            if e[k] > worst[k]:
+                worst[k] = e[k]
+                where[k] = {"lattice": i, "kind": s["kind"], "L": s["L"], "m": round(s["m"], 3),
+                            "tau": round(s["tau"], 3)}
+    return dict(worst, steps=nsteps, lattices=len(specs), lattices_over_1e_5=over, worst_at=where,
+                over_1e_5=listed, against="FP64 path of this library, every lattice")
+
+
 def run_batch(args):
     """256 independent periodic lattices (sides log-uniform in 64..1024, m/T
     log-uniform in 0.1..10 mapped onto the stencil library, tau in 0.6..1.5,
@@ -283,6 +320,9 @@ def run_batch(args):
     for lat in lats:
         lat.sync()                             # every lattice still physical
     tune = batch_tuning(lats)
+    check = None
+    if args.check_f64:
+        check = batch_error_vs_f64(specs, lats, warm + args.steps, stream)
     for lat in lats:
         lat.close()
 
@@ -309,6 +349,7 @@ def run_batch(args):
             "batched_over_one_at_a_time": ms_1 / ms_b,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak[0], "unit": "GB/s",
                          "frac": achieved / peak[0], "peak_kind": peak[1], "traffic": None},
+            "error_vs_f64": check,
             "gpu_launches": tune["launches_per_step"] * args.steps,
             "clocks": clk.summary()}
     emit(line, rank)
@@ -402,6 +443,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the accuracy check and the other dtypes")
+    ap.add_argument("--check-f64", action="store_true",
+                    help="batch only: compare every lattice with the FP64 path after the run (untimed, minutes)")
     ap.add_argument("--workload", default="random_flow", choices=["random_flow", "batch", "blast"],
                     help="random_flow: the headline 4096^2 lattice; batch: 256 independent lattices; "
                          "blast: the 8192^2 near-massless blast in BF16-deviation storage")
