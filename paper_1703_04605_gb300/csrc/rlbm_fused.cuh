@@ -301,10 +301,17 @@ __device__ __forceinline__ void fused_site(const FusedParams& p, const void* __r
   }
 }
 
-// Five resident blocks of 128 threads (96 registers) for Q <= 64 in FP32, four
-// (128 registers) for larger stencils and for BF16 storage, which would spill.
+// Resident blocks of 128 threads per SM (so registers per thread), measured
+// per stencil size on GB300: Q <= 40: 6 in FP32 (80 registers), 5 in BF16;
+// Q <= 64: 5 in FP32 (96 registers), 4 in BF16; larger stencils 4 (128
+// registers), where fewer registers would spill.
 template <class Def, bool BF>
-__global__ void __launch_bounds__(128, (Def::Q <= 64 && !BF) ? 5 : 4) fused_f32_kernel(const __grid_constant__ FusedParams p,
+constexpr int fused_min_blocks() {
+  return Def::Q <= 40 ? (BF ? 5 : 6) : ((Def::Q <= 64 && !BF) ? 5 : 4);
+}
+
+template <class Def, bool BF>
+__global__ void __launch_bounds__(128, fused_min_blocks<Def, BF>()) fused_f32_kernel(const __grid_constant__ FusedParams p,
                                                         const void* __restrict__ fin,
                                                         void* __restrict__ fout) {
   const int site = blockIdx.x * blockDim.x + threadIdx.x;
