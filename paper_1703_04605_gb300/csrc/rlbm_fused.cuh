@@ -91,31 +91,42 @@ __device__ __forceinline__ void fused_load(float (&d)[Def::Q], const void* __res
   }
 }
 
-template <class Def, int I>
-__device__ __forceinline__ void fused_acc(const float (&d)[Def::Q], float (&s)[6][6]) {
-  constexpr int g = Def::F.grp[I], nx = Def::F.nx[I], ny = Def::F.ny[I];
-  const float v = d[I];
-  s[g][0] += v;
-  if constexpr (nx != 0) s[g][1] = fmaf((float)nx, v, s[g][1]);
-  if constexpr (ny != 0) s[g][2] = fmaf((float)ny, v, s[g][2]);
-  if constexpr (nx != 0) s[g][3] = fmaf((float)(nx * nx), v, s[g][3]);
-  if constexpr (nx != 0 && ny != 0) s[g][4] = fmaf((float)(nx * ny), v, s[g][4]);
-  if constexpr (ny != 0) s[g][5] = fmaf((float)(ny * ny), v, s[g][5]);
+// Group sums of one reflection orbit (members (+,+), (-,+), (+,-), (-,-) of
+// |n_x|, |n_y|): s[g] = sum d, sum n_x d, sum n_y d, sum n_x^2 d, sum n_x n_y d,
+// sum n_y^2 d, formed from the butterflies d0 +- d1, d2 +- d3.
+template <class Def, int K>
+__device__ __forceinline__ void fused_acc_orbit(const float (&d)[Def::Q], float (&s)[6][6]) {
+  constexpr int kind = Def::O.kind[K], g = Def::O.grp[K], ax = Def::O.ax[K], ay = Def::O.ay[K];
+  constexpr int i0 = Def::O.idx[K][0], i1 = Def::O.idx[K][1], i2 = Def::O.idx[K][2], i3 = Def::O.idx[K][3];
+  if constexpr (kind == 1) {
+    s[g][0] += d[i0];
+  } else if constexpr (kind == 2) {
+    const float S = d[i0] + d[i1], D = d[i0] - d[i1];
+    s[g][0] += S;
+    s[g][1] = fmaf((float)ax, D, s[g][1]);
+    s[g][3] = fmaf((float)(ax * ax), S, s[g][3]);
+  } else if constexpr (kind == 3) {
+    const float S = d[i0] + d[i2], D = d[i0] - d[i2];
+    s[g][0] += S;
+    s[g][2] = fmaf((float)ay, D, s[g][2]);
+    s[g][5] = fmaf((float)(ay * ay), S, s[g][5]);
+  } else {
+    const float p = d[i0] + d[i1], q = d[i0] - d[i1], r = d[i2] + d[i3], w = d[i2] - d[i3];
+    const float S = p + r;
+    s[g][0] += S;
+    s[g][1] = fmaf((float)ax, q + w, s[g][1]);
+    s[g][2] = fmaf((float)ay, p - r, s[g][2]);
+    s[g][3] = fmaf((float)(ax * ax), S, s[g][3]);
+    s[g][4] = fmaf((float)(ax * ay), q - w, s[g][4]);
+    s[g][5] = fmaf((float)(ay * ay), S, s[g][5]);
+  }
 }
 
+// Relaxation and store of population I with equilibrium value e (f^eq - r).
 template <class Def, bool BF, int I>
-__device__ __forceinline__ void fused_collide(const float (&d)[Def::Q], const float (&c)[6][6],
-                                              const uint2 (&cq)[6], float a0, float ax, float ay,
-                                              void* __restrict__ out, long long plane) {
+__device__ __forceinline__ void fused_relax(const float (&d)[Def::Q], float e, const uint2 (&cq)[6], float a0,
+                                            float ax, float ay, void* __restrict__ out, long long plane) {
   constexpr int g = Def::F.grp[I], nx = Def::F.nx[I], ny = Def::F.ny[I], mult = Def::F.mult[I];
-  // group polynomial alpha + bx nx + by ny + qxx nx^2 + qyy ny^2 + qxy nx ny
-  float e = c[g][0];
-  if constexpr (nx != 0) e = fmaf((float)nx, c[g][1], e);
-  if constexpr (ny != 0) e = fmaf((float)ny, c[g][2], e);
-  if constexpr (nx != 0) e = fmaf((float)(nx * nx), c[g][3], e);
-  if constexpr (ny != 0) e = fmaf((float)(ny * ny), c[g][4], e);
-  if constexpr (nx != 0 && ny != 0) e = fmaf((float)(nx * ny), c[g][5], e);
-  if constexpr (mult != 1) e *= (float)mult;
   // weight p_i.U/(p_i^0 tau) = (U0 - v0 (nx Ux + ny Uy))/tau
   float om = a0;
   if constexpr (nx != 0) om = fmaf(-(float)nx, ax, om);
@@ -131,6 +142,40 @@ __device__ __forceinline__ void fused_collide(const float (&d)[Def::Q], const fl
   }
 }
 
+// Equilibrium of one reflection orbit: the group polynomial
+// mult (c0 + c1 n_x + c2 n_y + c3 n_x^2 + c4 n_y^2 + c5 n_x n_y) split into the
+// part even in both n_x and n_y and the odd terms the members share.
+template <class Def, bool BF, int K>
+__device__ __forceinline__ void fused_collide_orbit(const float (&d)[Def::Q], const float (&c)[6][6],
+                                                    const uint2 (&cq)[6], float a0, float ax_, float ay_,
+                                                    void* __restrict__ out, long long plane) {
+  constexpr int kind = Def::O.kind[K], g = Def::O.grp[K], ax = Def::O.ax[K], ay = Def::O.ay[K];
+  constexpr int i0 = Def::O.idx[K][0], i1 = Def::O.idx[K][1], i2 = Def::O.idx[K][2], i3 = Def::O.idx[K][3];
+  constexpr float m = (float)Def::O.mult[K];
+  float E0 = m * c[g][0];
+  if constexpr (ax != 0) E0 = fmaf(m * (float)(ax * ax), c[g][3], E0);
+  if constexpr (ay != 0) E0 = fmaf(m * (float)(ay * ay), c[g][4], E0);
+  if constexpr (kind == 1) {
+    fused_relax<Def, BF, i0>(d, E0, cq, a0, ax_, ay_, out, plane);
+  } else if constexpr (kind == 2) {
+    const float X = (m * (float)ax) * c[g][1];
+    fused_relax<Def, BF, i0>(d, E0 + X, cq, a0, ax_, ay_, out, plane);
+    fused_relax<Def, BF, i1>(d, E0 - X, cq, a0, ax_, ay_, out, plane);
+  } else if constexpr (kind == 3) {
+    const float Y = (m * (float)ay) * c[g][2];
+    fused_relax<Def, BF, i0>(d, E0 + Y, cq, a0, ax_, ay_, out, plane);
+    fused_relax<Def, BF, i2>(d, E0 - Y, cq, a0, ax_, ay_, out, plane);
+  } else {
+    const float X = (m * (float)ax) * c[g][1], Y = (m * (float)ay) * c[g][2];
+    const float Z = (m * (float)(ax * ay)) * c[g][5];
+    const float EP = E0 + Z, EM = E0 - Z, XP = X + Y, XM = X - Y;
+    fused_relax<Def, BF, i0>(d, EP + XP, cq, a0, ax_, ay_, out, plane);
+    fused_relax<Def, BF, i1>(d, EM - XM, cq, a0, ax_, ay_, out, plane);
+    fused_relax<Def, BF, i2>(d, EM + XM, cq, a0, ax_, ay_, out, plane);
+    fused_relax<Def, BF, i3>(d, EP - XP, cq, a0, ax_, ay_, out, plane);
+  }
+}
+
 template <class Def, bool BF, int... Is>
 __device__ __forceinline__ void fused_load_all(std::integer_sequence<int, Is...>, float (&d)[Def::Q],
                                                const void* __restrict__ fin, const uint2* __restrict__ cin,
@@ -138,17 +183,69 @@ __device__ __forceinline__ void fused_load_all(std::integer_sequence<int, Is...>
   (fused_load<Def, BF, Is>(d, fin, cin, plane, pitch, x, y, Nx, Ny), ...);
 }
 
-template <class Def, int... Is>
-__device__ __forceinline__ void fused_acc_all(std::integer_sequence<int, Is...>, const float (&d)[Def::Q],
+template <class Def, int... Ks>
+__device__ __forceinline__ void fused_acc_all(std::integer_sequence<int, Ks...>, const float (&d)[Def::Q],
                                               float (&s)[6][6]) {
-  (fused_acc<Def, Is>(d, s), ...);
+  (fused_acc_orbit<Def, Ks>(d, s), ...);
+}
+
+template <class Def, bool BF, int... Ks>
+__device__ __forceinline__ void fused_collide_all(std::integer_sequence<int, Ks...>, const float (&d)[Def::Q],
+                                                  const float (&c)[6][6], const uint2 (&cq)[6], float a0,
+                                                  float ax, float ay, void* __restrict__ out, long long plane) {
+  (fused_collide_orbit<Def, BF, Ks>(d, c, cq, a0, ax, ay, out, plane), ...);
+}
+
+// Per-population forms of the two loops (the stencil's reflection orbits are
+// not used): fewer values live at once, which the 96-register FP32 kernel of
+// stencils with 50 <= Q <= 64 needs to avoid spills.
+template <class Def, int I>
+__device__ __forceinline__ void fused_acc_pop(const float (&d)[Def::Q], float (&s)[6][6]) {
+  constexpr int g = Def::F.grp[I], nx = Def::F.nx[I], ny = Def::F.ny[I];
+  const float v = d[I];
+  s[g][0] += v;
+  if constexpr (nx != 0) s[g][1] = fmaf((float)nx, v, s[g][1]);
+  if constexpr (ny != 0) s[g][2] = fmaf((float)ny, v, s[g][2]);
+  if constexpr (nx != 0) s[g][3] = fmaf((float)(nx * nx), v, s[g][3]);
+  if constexpr (nx != 0 && ny != 0) s[g][4] = fmaf((float)(nx * ny), v, s[g][4]);
+  if constexpr (ny != 0) s[g][5] = fmaf((float)(ny * ny), v, s[g][5]);
+}
+
+template <class Def, bool BF, int I>
+__device__ __forceinline__ void fused_collide_pop(const float (&d)[Def::Q], const float (&c)[6][6],
+                                                  const uint2 (&cq)[6], float a0, float ax, float ay,
+                                                  void* __restrict__ out, long long plane) {
+  constexpr int g = Def::F.grp[I], nx = Def::F.nx[I], ny = Def::F.ny[I], mult = Def::F.mult[I];
+  float e = c[g][0];
+  if constexpr (nx != 0) e = fmaf((float)nx, c[g][1], e);
+  if constexpr (ny != 0) e = fmaf((float)ny, c[g][2], e);
+  if constexpr (nx != 0) e = fmaf((float)(nx * nx), c[g][3], e);
+  if constexpr (ny != 0) e = fmaf((float)(ny * ny), c[g][4], e);
+  if constexpr (nx != 0 && ny != 0) e = fmaf((float)(nx * ny), c[g][5], e);
+  if constexpr (mult != 1) e *= (float)mult;
+  fused_relax<Def, BF, I>(d, e, cq, a0, ax, ay, out, plane);
+}
+
+// Orbit form or per-population form, chosen per kernel from measurements on
+// GB300: the orbit form saves about 5 instructions per population (E5 FP32
+// and S2 FP32/BF16 3-4 % faster) but keeps more values live, which makes the
+// 96-register FP32 kernel of M1 (Q = 58) spill and run 23 % slower.
+template <class Def, bool BF>
+__host__ __device__ constexpr bool fused_use_orbits() {
+  return BF || Def::Q < 50 || Def::Q > 64;
+}
+
+template <class Def, int... Is>
+__device__ __forceinline__ void fused_acc_pop_all(std::integer_sequence<int, Is...>, const float (&d)[Def::Q],
+                                                  float (&s)[6][6]) {
+  (fused_acc_pop<Def, Is>(d, s), ...);
 }
 
 template <class Def, bool BF, int... Is>
-__device__ __forceinline__ void fused_collide_all(std::integer_sequence<int, Is...>, const float (&d)[Def::Q],
-                                                  const float (&c)[6][6], const uint2 (&cq)[6], float a0,
-                                                  float ax, float ay, void* __restrict__ out, long long plane) {
-  (fused_collide<Def, BF, Is>(d, c, cq, a0, ax, ay, out, plane), ...);
+__device__ __forceinline__ void fused_collide_pop_all(std::integer_sequence<int, Is...>, const float (&d)[Def::Q],
+                                                      const float (&c)[6][6], const uint2 (&cq)[6], float a0,
+                                                      float ax, float ay, void* __restrict__ out, long long plane) {
+  (fused_collide_pop<Def, BF, Is>(d, c, cq, a0, ax, ay, out, plane), ...);
 }
 
 // One site update (see the header comment); p describes the lattice.
@@ -168,7 +265,9 @@ __device__ __forceinline__ void fused_site(const FusedParams& p, const void* __r
     for (int g = 0; g < 6; ++g)
 #pragma unroll
       for (int k = 0; k < 6; ++k) s[g][k] = 0.0f;
-    fused_acc_all<Def>(Seq{}, d, s);
+    using Orb = std::make_integer_sequence<int, Def::O.K>;
+    if constexpr (fused_use_orbits<Def, BF>()) fused_acc_all<Def>(Orb{}, d, s);
+    else fused_acc_pop_all<Def>(Seq{}, d, s);
 
     // deviation moments N0 Nx Ny T00 T0x T0y Txx Txy Tyy (reference excluded)
     float M[9];
@@ -297,7 +396,8 @@ __device__ __forceinline__ void fused_site(const FusedParams& p, const void* __r
     }
     void* out = BF ? static_cast<void*>(static_cast<unsigned short*>(fout) + here)
                    : static_cast<void*>(static_cast<float*>(fout) + here);
-    fused_collide_all<Def, BF>(Seq{}, d, c, cq, a0, ax, ay, out, p.plane);
+    if constexpr (fused_use_orbits<Def, BF>()) fused_collide_all<Def, BF>(Orb{}, d, c, cq, a0, ax, ay, out, p.plane);
+    else fused_collide_pop_all<Def, BF>(Seq{}, d, c, cq, a0, ax, ay, out, p.plane);
   }
 }
 

@@ -113,6 +113,59 @@ constexpr Folded fold_stencil(int g0, int g1, int g2, int g3, int g4, int g5) {
   return F;
 }
 
+// Reflection orbits of a folded stencil: the populations of one group with
+// the same |n_x|, |n_y| and n_z^2 under n_x -> -n_x and n_y -> -n_y.  kind 4:
+// quartet, members (+,+), (-,+), (+,-), (-,-); kind 2: (+a_x, 0), (-a_x, 0);
+// kind 3: (0, +a_y), (0, -a_y); kind 1: the single population (0, 0).
+struct Orbits {
+  int K;
+  int kind[kMaxFolded], grp[kMaxFolded], ax[kMaxFolded], ay[kMaxFolded], mult[kMaxFolded];
+  int idx[kMaxFolded][4];
+};
+
+constexpr int find_pop(const Folded& F, int g, int nx, int ny, int nz2) {
+  for (int i = 0; i < F.Q; ++i)
+    if (F.grp[i] == g && F.nx[i] == nx && F.ny[i] == ny && F.nz2[i] == nz2) return i;
+  return -1;
+}
+
+constexpr Orbits make_orbits(const Folded& F) {
+  Orbits O{};
+  O.K = 0;
+  for (int i = 0; i < F.Q; ++i) {
+    const int nx = F.nx[i], ny = F.ny[i];
+    if (nx < 0 || ny < 0) continue;   // the (+,+) member represents the orbit
+    const int k = O.K++;
+    O.grp[k] = F.grp[i];
+    O.ax[k] = nx;
+    O.ay[k] = ny;
+    O.mult[k] = F.mult[i];
+    O.kind[k] = (nx > 0 && ny > 0) ? 4 : (nx > 0) ? 2 : (ny > 0) ? 3 : 1;
+    O.idx[k][0] = i;
+    O.idx[k][1] = find_pop(F, F.grp[i], -nx, ny, F.nz2[i]);
+    O.idx[k][2] = find_pop(F, F.grp[i], nx, -ny, F.nz2[i]);
+    O.idx[k][3] = find_pop(F, F.grp[i], -nx, -ny, F.nz2[i]);
+  }
+  return O;
+}
+
+// Every population in exactly one orbit, with the multiplicity of its
+// representative (the orbits are closed under the reflections).
+constexpr bool orbits_cover(const Folded& F, const Orbits& O) {
+  int seen[kMaxFolded] = {};
+  for (int k = 0; k < O.K; ++k) {
+    const int n = O.kind[k] == 4 ? 4 : (O.kind[k] == 1 ? 1 : 2);
+    for (int j = 0; j < n; ++j) {
+      const int i = (O.kind[k] == 3 && j == 1) ? O.idx[k][2] : O.idx[k][j];
+      if (i < 0 || F.mult[i] != O.mult[k]) return false;
+      seen[i] += 1;
+    }
+  }
+  for (int i = 0; i < F.Q; ++i)
+    if (seen[i] != 1) return false;
+  return true;
+}
+
 // Stencils with compiled fused kernels (group ids ascending).
 template <int G0, int G1, int G2, int G3, int G4, int G5>
 struct StencilDef {
@@ -120,6 +173,8 @@ struct StencilDef {
   static constexpr Folded F = fold_stencil(G0, G1, G2, G3, G4, G5);
   static constexpr int Q = F.Q;
   static constexpr int halo = F.halo;
+  static constexpr Orbits O = make_orbits(F);
+  static_assert(orbits_cover(F, O), "reflection orbits must partition the folded stencil");
 };
 
 using StencilM1 = StencilDef<5, 12, 14, 17, 21, 26>;    // m/T_R ~ 1
