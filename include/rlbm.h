@@ -132,6 +132,7 @@ rlbm_status rlbm_step(rlbm_ctx* ctx, int nsteps);
 #define RLBM_M_E    0x10u  /* energy density e (Eq. 20)        */
 #define RLBM_M_NVEC 0x20u  /* N^a, 3 planes                    */
 #define RLBM_M_TMN  0x40u  /* T^ab, 6 planes                   */
+#define RLBM_M_UZ   0x80u  /* u_z = U^z / U^0 (3D lattices only) */
 rlbm_status rlbm_moments(rlbm_ctx* ctx, double* out, unsigned mask);
 
 /* Number of doubles rlbm_moments writes for a mask (0 on a NULL ctx). */
@@ -176,6 +177,55 @@ rlbm_status rlbm_batch_step(rlbm_ctx* const* ctxs, int count, int nsteps);
  * NULL.  Never touches the device.  Errors: EINVAL (bad arguments, or no
  * choice cached for this batch). */
 rlbm_status rlbm_batch_tuning(rlbm_ctx* const* ctxs, int count, int* steps_per_graph, int* launches_per_step);
+
+/* ---- native 3D lattices ----------------------------------------------
+ * The paper's model is three-dimensional (Sec. II-III, App. C); these entry
+ * points run it on an Nx x Ny x Nz periodic lattice with the unfolded
+ * stencil (every vector of the six Table I orbits, signed n_z), all three
+ * velocity components and the 14 polynomials of App. A.  They use generic
+ * kernels (any six-group stencil): FP64 storage (f_i), or FP32 storage of
+ * d_i = f_i - r_i with FP32 accumulation; the site solve (Landau frame by
+ * Newton iteration on the three velocities, Eq. 20; EOS, Eq. 28) is FP64.
+ * Fields are [Nz][Ny][Nx] arrays, x fastest.  A separate context type. */
+typedef struct rlbm_ctx3 rlbm_ctx3;
+
+typedef struct {
+  int Nx, Ny, Nz;
+  int Q;                    /* populations of the unfolded stencil            */
+  int halo;                 /* largest |n| component                          */
+  rlbm_dtype dtype;
+  double m, tau, v0;
+  long long t;
+  size_t bytes_per_site;    /* 2 Q sizeof(storage)                            */
+  size_t device_bytes;
+} rlbm3_info;
+
+/* As rlbm_create, with Nz >= 1; dtype RLBM_F64 or RLBM_F32 (ENOTSUP for
+ * BF16).  More than 160 populations: ENOTSUP. */
+rlbm_status rlbm3_create(const rlbm_stencil* st, double m, double tau, int Nx, int Ny, int Nz,
+                         rlbm_dtype dtype, void* cuda_stream, rlbm_ctx3** out);
+
+/* f = f^eq(n, U, T) (Eq. 16), t = 0.  Host FP64 arrays of Nx*Ny*Nz values;
+ * n > 0, T > 0, |u| < 1 checked (EINVAL names the first bad site). */
+rlbm_status rlbm3_init(rlbm_ctx3* ctx, const double* n, const double* ux, const double* uy,
+                       const double* uz, const double* T);
+
+/* nsteps steps (Eq. 49), asynchronous on the context's stream. */
+rlbm_status rlbm3_step(rlbm_ctx3* ctx, int nsteps);
+
+/* Macroscopic fields of the pre-collision state at t into host memory, one
+ * Nx*Ny*Nz plane per scalar, in the order of the mask bits: RLBM_M_N, _UX,
+ * _UY, _T, _E, _NVEC (4 planes N^0..N^z), _TMN (10 planes T^00 T^0x T^0y
+ * T^0z T^xx T^xy T^xz T^yy T^yz T^zz), _UZ.  Synchronises the stream and
+ * reports sticky device errors (ENONPHYS). */
+rlbm_status rlbm3_moments(rlbm_ctx3* ctx, double* out, unsigned mask);
+size_t rlbm3_moments_size(const rlbm_ctx3* ctx, unsigned mask);
+
+rlbm_status rlbm3_sync(rlbm_ctx3* ctx);
+rlbm_status rlbm3_get_info(const rlbm_ctx3* ctx, rlbm3_info* info);
+/* Last failure on ctx, or of the last failed rlbm3_create when ctx is NULL. */
+const char* rlbm3_last_error(const rlbm_ctx3* ctx);
+void rlbm3_destroy(rlbm_ctx3* ctx);
 
 /* ---- read-out without memory allocation -------------------------------
  * The paper has no counterpart of this entry point; it serves callers that

@@ -12,15 +12,20 @@ RLBM_OK, RLBM_EINVAL, RLBM_ENOQUAD, RLBM_ENOMEM, RLBM_ECUDA, RLBM_ENONPHYS, RLBM
 STATUS_NAMES = ["OK", "EINVAL", "ENOQUAD", "ENOMEM", "ECUDA", "ENONPHYS", "ETIMEOUT", "ENOTSUP"]
 DTYPES = {"f64": 0, "f32": 1, "bf16dev": 2}
 
-M_N, M_UX, M_UY, M_T, M_E, M_NVEC, M_TMN = 0x01, 0x02, 0x04, 0x08, 0x10, 0x20, 0x40
+M_N, M_UX, M_UY, M_T, M_E, M_NVEC, M_TMN, M_UZ = 0x01, 0x02, 0x04, 0x08, 0x10, 0x20, 0x40, 0x80
 MASK_PLANES = [(M_N, ["n"]), (M_UX, ["ux"]), (M_UY, ["uy"]), (M_T, ["T"]), (M_E, ["e"]),
                (M_NVEC, ["N0", "Nx", "Ny"]), (M_TMN, ["T00", "T0x", "T0y", "Txx", "Txy", "Tyy"])]
+MASK_PLANES3 = [(M_N, ["n"]), (M_UX, ["ux"]), (M_UY, ["uy"]), (M_T, ["T"]), (M_E, ["e"]),
+                (M_NVEC, ["N0", "Nx", "Ny", "Nz"]),
+                (M_TMN, ["T00", "T0x", "T0y", "T0z", "Txx", "Txy", "Txz", "Tyy", "Tyz", "Tzz"]), (M_UZ, ["uz"])]
 
 # every entry point declared in include/rlbm.h
 EXPORTS = ["rlbm_create", "rlbm_init", "rlbm_init_device", "rlbm_step", "rlbm_moments",
            "rlbm_moments_size", "rlbm_sync", "rlbm_get_info", "rlbm_last_error", "rlbm_destroy",
            "rlbm_quadrature_weights", "rlbm_quadrature_window", "rlbm_bessel_ratio", "rlbm_version",
-           "rlbm_moments_noalloc", "rlbm_batch_step", "rlbm_batch_tuning"]
+           "rlbm_moments_noalloc", "rlbm_batch_step", "rlbm_batch_tuning",
+           "rlbm3_create", "rlbm3_init", "rlbm3_step", "rlbm3_moments", "rlbm3_moments_size", "rlbm3_sync",
+           "rlbm3_get_info", "rlbm3_last_error", "rlbm3_destroy"]
 
 
 class Stencil(C.Structure):
@@ -32,6 +37,12 @@ class Info(C.Structure):
                 ("dtype", C.c_int), ("m", C.c_double), ("tau", C.c_double), ("v0", C.c_double),
                 ("w_group", C.c_double * 6), ("t", C.c_longlong), ("bytes_per_site", C.c_size_t),
                 ("extra_bytes_per_site", C.c_size_t), ("device_bytes", C.c_size_t), ("kernel", C.c_int)]
+
+
+class Info3(C.Structure):
+    _fields_ = [("Nx", C.c_int), ("Ny", C.c_int), ("Nz", C.c_int), ("Q", C.c_int), ("halo", C.c_int),
+                ("dtype", C.c_int), ("m", C.c_double), ("tau", C.c_double), ("v0", C.c_double),
+                ("t", C.c_longlong), ("bytes_per_site", C.c_size_t), ("device_bytes", C.c_size_t)]
 
 
 class RLBMError(RuntimeError):
@@ -80,6 +91,16 @@ def load():
         "rlbm_batch_tuning": (C.c_int, [C.POINTER(P), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "rlbm_moments_noalloc": (C.c_int, [ip, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, P, dp,
                                            C.c_uint, P]),
+        "rlbm3_create": (C.c_int, [C.POINTER(Stencil), C.c_double, C.c_double, C.c_int, C.c_int, C.c_int,
+                                   C.c_int, P, C.POINTER(P)]),
+        "rlbm3_init": (C.c_int, [P, dp, dp, dp, dp, dp]),
+        "rlbm3_step": (C.c_int, [P, C.c_int]),
+        "rlbm3_moments": (C.c_int, [P, dp, C.c_uint]),
+        "rlbm3_moments_size": (C.c_size_t, [P, C.c_uint]),
+        "rlbm3_sync": (C.c_int, [P]),
+        "rlbm3_get_info": (C.c_int, [P, C.POINTER(Info3)]),
+        "rlbm3_last_error": (C.c_char_p, [P]),
+        "rlbm3_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -89,9 +110,10 @@ def load():
     return L
 
 
-def check(status, ctx=None):
+def check(status, ctx=None, three_d=False):
     if status != RLBM_OK:
-        msg = load().rlbm_last_error(ctx)
+        L = load()
+        msg = (L.rlbm3_last_error if three_d else L.rlbm_last_error)(ctx)
         raise RLBMError(status, msg.decode() if msg else "")
 
 

@@ -1,0 +1,289 @@
+// C ABI of the native 3D lattices (include/rlbm.h, "native 3D lattices").
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "rlbm_stencil.h"
+
+using namespace rlbm;
+
+struct rlbm_ctx3 {
+  int Nx = 0, Ny = 0, Nz = 0;
+  rlbm_dtype dtype = RLBM_F64;
+  cudaStream_t stream = nullptr;
+  double m = 0, tau = 0;
+  StencilBuild3 sb;
+  int Q = 0;
+  long long pitch = 0, plane = 0;
+  size_t elem = 0;
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;                 // buffer the next step pulls from
+  long long t = 0;
+  unsigned* d_err = nullptr;
+  double* d_rt64 = nullptr;
+  int* d_shift = nullptr;
+  double* d_tab64 = nullptr;
+  float* d_tab32 = nullptr;
+  double* d_fields = nullptr;  // 5 planes for rlbm3_init
+  double* d_out = nullptr;
+  size_t out_cap = 0;
+  size_t device_bytes = 0;
+  bool initialised = false;
+  Step3Params p{};
+  std::string last_error;
+};
+
+namespace {
+
+thread_local std::string g_create_error3;
+
+rlbm_status fail3(rlbm_ctx3* c, rlbm_status s, const std::string& msg) {
+  if (c) c->last_error = msg;
+  else g_create_error3 = msg;
+  return s;
+}
+
+rlbm_status cuda_fail3(rlbm_ctx3* c, cudaError_t e, const char* where) {
+  return fail3(c, RLBM_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+void release3(rlbm_ctx3* c) {
+  if (c->buf[0] || c->buf[1]) cudaStreamSynchronize(c->stream);
+  for (void* p : {c->buf[0], c->buf[1], (void*)c->d_err, (void*)c->d_rt64, (void*)c->d_shift, (void*)c->d_tab64,
+                  (void*)c->d_tab32, (void*)c->d_fields, (void*)c->d_out})
+    if (p) cudaFree(p);
+  c->buf[0] = c->buf[1] = nullptr;
+}
+
+// Reference r_i of the FP32 storage at density nref (FP64 storage: none).
+void set_reference3(rlbm_ctx3* c, double nref) {
+  if (c->dtype == RLBM_F64) nref = 0.0;
+  c->p.nref = nref;
+  c->p.b0ref = nref * c->sb.sb.b0ref1;
+  for (int k = 0; k < 14; ++k) c->p.mref[k] = nref * c->sb.mref1[k];
+}
+
+rlbm_status check_error3(rlbm_ctx3* c) {
+  unsigned h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, c->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail3(c, e, "device synchronisation");
+  if (h) {
+    cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream);
+    cudaStreamSynchronize(c->stream);
+    std::string msg = "non-physical site(s):";
+    if (h & ERR_LANDAU) msg += " Landau frame failed or |u| >= 1;";
+    if (h & ERR_DENSITY) msg += " n <= 0;";
+    if (h & ERR_EOS) msg += " e/n <= m or T <= 0;";
+    if (h & ERR_ZETA) msg += " zeta = m/T invalid;";
+    return fail3(c, RLBM_ENONPHYS, msg);
+  }
+  return RLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rlbm_status rlbm3_create(const rlbm_stencil* st, double m, double tau, int Nx, int Ny, int Nz,
+                         rlbm_dtype dtype, void* cuda_stream, rlbm_ctx3** out) {
+  if (!out) return fail3(nullptr, RLBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (Nx < 1 || Ny < 1 || Nz < 1) return fail3(nullptr, RLBM_EINVAL, "Nx, Ny and Nz must be >= 1");
+  if (!(tau > 0.5) || !std::isfinite(tau)) return fail3(nullptr, RLBM_EINVAL, "tau must exceed 1/2");
+  if (dtype == RLBM_BF16_DEV) return fail3(nullptr, RLBM_ENOTSUP, "3D lattices store FP64 or FP32");
+  if (dtype != RLBM_F64 && dtype != RLBM_F32) return fail3(nullptr, RLBM_EINVAL, "unknown dtype");
+  std::unique_ptr<rlbm_ctx3> c(new (std::nothrow) rlbm_ctx3);
+  if (!c) return fail3(nullptr, RLBM_ENOMEM, "host allocation failed");
+  std::string err;
+  rlbm_status s = build_stencil3d(st, m, &c->sb, &err);
+  if (s != RLBM_OK) return fail3(nullptr, s, err);
+  c->Nx = Nx;
+  c->Ny = Ny;
+  c->Nz = Nz;
+  c->dtype = dtype;
+  c->m = m;
+  c->tau = tau;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->Q = (int)c->sb.pops.size();
+  c->elem = dtype == RLBM_F64 ? sizeof(double) : sizeof(float);
+  c->pitch = ((long long)Nx + 31) / 32 * 32;
+  c->plane = c->pitch * Ny * Nz;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) return fail3(nullptr, RLBM_ECUDA, "no CUDA device available");
+  // constant table [kPop3][Q] and shifts [3][Q]
+  const int Q = c->Q;
+  std::vector<double> t64((size_t)kPop3 * Q);
+  std::vector<float> t32((size_t)kPop3 * Q);
+  std::vector<int> sh((size_t)3 * Q);
+  for (int i = 0; i < Q; ++i) {
+    const Pop3& q = c->sb.pops[i];
+    for (int k = 0; k < kPop3; ++k) {
+      t64[(size_t)k * Q + i] = q.c[k];
+      t32[(size_t)k * Q + i] = (float)q.c[k];
+    }
+    sh[i] = ((q.nx % Nx) + Nx) % Nx;
+    sh[Q + i] = ((q.ny % Ny) + Ny) % Ny;
+    sh[2 * Q + i] = ((q.nz % Nz) + Nz) % Nz;
+  }
+  const size_t fbytes = (size_t)Q * (size_t)c->plane * c->elem;
+  const size_t nsite = (size_t)Nx * Ny * Nz;
+  const auto& r64 = ratio_table64();
+  bool ok = cudaMalloc(&c->buf[0], fbytes) == cudaSuccess && cudaMalloc(&c->buf[1], fbytes) == cudaSuccess &&
+            cudaMalloc(&c->d_err, sizeof(unsigned)) == cudaSuccess &&
+            cudaMalloc(&c->d_rt64, r64.size() * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->d_shift, sh.size() * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&c->d_tab64, t64.size() * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->d_tab32, t32.size() * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&c->d_fields, 5 * nsite * sizeof(double)) == cudaSuccess;
+  if (!ok) {
+    release3(c.get());
+    return fail3(nullptr, RLBM_ENOMEM, "device allocation failed");
+  }
+  c->device_bytes = 2 * fbytes + r64.size() * 8 + sh.size() * 4 + t64.size() * 12 + 5 * nsite * 8 + 4;
+  e = cudaMemcpy(c->d_rt64, r64.data(), r64.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_shift, sh.data(), sh.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_tab64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_tab32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(unsigned));
+  if (e != cudaSuccess) {
+    release3(c.get());
+    return fail3(nullptr, RLBM_ECUDA, std::string("upload: ") + cudaGetErrorString(e));
+  }
+  Step3Params& p = c->p;
+  p.Nx = Nx;
+  p.Ny = Ny;
+  p.Nz = Nz;
+  p.Q = Q;
+  p.pitch = c->pitch;
+  p.plane = c->plane;
+  p.inv_tau = 1.0 / tau;
+  p.sc = c->sb.sb.sc;
+  p.rt64 = c->d_rt64;
+  p.shift = c->d_shift;
+  p.tab64 = c->d_tab64;
+  p.tab32 = c->d_tab32;
+  p.err = c->d_err;
+  set_reference3(c.get(), 1.0);
+  *out = c.release();
+  return RLBM_OK;
+}
+
+rlbm_status rlbm3_init(rlbm_ctx3* c, const double* n, const double* ux, const double* uy, const double* uz,
+                       const double* T) {
+  if (!c) return RLBM_EINVAL;
+  if (!n || !ux || !uy || !uz || !T) return fail3(c, RLBM_EINVAL, "NULL field pointer");
+  const size_t N = (size_t)c->Nx * c->Ny * c->Nz;
+  double nsum = 0;
+  for (size_t s = 0; s < N; ++s) {
+    const double v2 = ux[s] * ux[s] + uy[s] * uy[s] + uz[s] * uz[s];
+    if (!(n[s] > 0) || !(T[s] > 0) || !(v2 < 1) || !std::isfinite(n[s]) || !std::isfinite(T[s])) {
+      char b[200];
+      std::snprintf(b, sizeof b, "invalid field at site %zu (x=%zu, y=%zu, z=%zu): need n>0, T>0, |u|<1", s,
+                    s % (size_t)c->Nx, (s / (size_t)c->Nx) % (size_t)c->Ny, s / ((size_t)c->Nx * c->Ny));
+      return fail3(c, RLBM_EINVAL, b);
+    }
+    nsum += n[s];
+  }
+  set_reference3(c, nsum / (double)N);
+  const double* src[5] = {n, ux, uy, uz, T};
+  for (int k = 0; k < 5; ++k) {
+    cudaError_t e = cudaMemcpyAsync(c->d_fields + k * N, src[k], N * sizeof(double), cudaMemcpyHostToDevice,
+                                    c->stream);
+    if (e != cudaSuccess) return cuda_fail3(c, e, "field upload");
+  }
+  Field3Ptrs fp{c->d_fields, c->d_fields + N, c->d_fields + 2 * N, c->d_fields + 3 * N, c->d_fields + 4 * N};
+  cudaError_t e = launch_init3d(c->dtype, c->p, fp, c->buf[0], c->buf[1], c->stream);
+  if (e != cudaSuccess) return cuda_fail3(c, e, "init launch");
+  c->cur = 0;
+  c->t = 0;
+  c->initialised = true;
+  return check_error3(c);
+}
+
+rlbm_status rlbm3_step(rlbm_ctx3* c, int nsteps) {
+  if (!c) return RLBM_EINVAL;
+  if (nsteps < 0) return fail3(c, RLBM_EINVAL, "nsteps < 0");
+  if (!c->initialised) return fail3(c, RLBM_EINVAL, "rlbm3_init has not been called");
+  for (int k = 0; k < nsteps; ++k) {
+    cudaError_t e = launch_step3d(c->dtype, c->p, c->buf[c->cur], c->buf[1 - c->cur], c->stream);
+    if (e != cudaSuccess) return cuda_fail3(c, e, "step launch");
+    c->cur = 1 - c->cur;
+    ++c->t;
+  }
+  return RLBM_OK;
+}
+
+size_t rlbm3_moments_size(const rlbm_ctx3* c, unsigned mask) {
+  if (!c) return 0;
+  size_t planes = 0;
+  for (unsigned b : {RLBM_M_N, RLBM_M_UX, RLBM_M_UY, RLBM_M_T, RLBM_M_E, RLBM_M_UZ})
+    if (mask & b) ++planes;
+  if (mask & RLBM_M_NVEC) planes += 4;
+  if (mask & RLBM_M_TMN) planes += 10;
+  return planes * (size_t)c->Nx * c->Ny * c->Nz;
+}
+
+rlbm_status rlbm3_moments(rlbm_ctx3* c, double* out, unsigned mask) {
+  if (!c) return RLBM_EINVAL;
+  if (!out) return fail3(c, RLBM_EINVAL, "out is NULL");
+  if (!c->initialised) return fail3(c, RLBM_EINVAL, "rlbm3_init has not been called");
+  if (mask & ~0xFFu) return fail3(c, RLBM_EINVAL, "unknown mask bits");
+  const size_t need = rlbm3_moments_size(c, mask);
+  if (need == 0) return RLBM_OK;
+  if (need > c->out_cap) {
+    if (c->d_out) cudaFree(c->d_out);
+    c->d_out = nullptr;
+    c->out_cap = 0;
+    cudaError_t e = cudaMalloc(&c->d_out, need * sizeof(double));
+    if (e != cudaSuccess) return fail3(c, RLBM_ENOMEM, "read-out buffer");
+    c->out_cap = need;
+  }
+  MomentOut mo{c->d_out, mask};
+  // the pre-collision state at t is the pull of S_{t-1}, the buffer the last step read
+  cudaError_t e = launch_moments3d(c->dtype, c->p, c->buf[1 - c->cur], mo, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, c->d_out, need * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail3(c, e, "read-out");
+  return check_error3(c);
+}
+
+rlbm_status rlbm3_sync(rlbm_ctx3* c) {
+  if (!c) return RLBM_EINVAL;
+  return check_error3(c);
+}
+
+rlbm_status rlbm3_get_info(const rlbm_ctx3* c, rlbm3_info* info) {
+  if (!c || !info) return RLBM_EINVAL;
+  std::memset(info, 0, sizeof(*info));
+  info->Nx = c->Nx;
+  info->Ny = c->Ny;
+  info->Nz = c->Nz;
+  info->Q = c->Q;
+  info->halo = c->sb.halo;
+  info->dtype = c->dtype;
+  info->m = c->m;
+  info->tau = c->tau;
+  info->v0 = c->sb.sb.v0;
+  info->t = c->t;
+  info->bytes_per_site = 2 * (size_t)c->Q * c->elem;
+  info->device_bytes = c->device_bytes + c->out_cap * sizeof(double);
+  return RLBM_OK;
+}
+
+const char* rlbm3_last_error(const rlbm_ctx3* c) {
+  return c ? c->last_error.c_str() : g_create_error3.c_str();
+}
+
+void rlbm3_destroy(rlbm_ctx3* c) {
+  if (!c) return;
+  release3(c);
+  delete c;
+}
+
+}  // extern "C"

@@ -142,6 +142,45 @@ struct MomentOut {
   unsigned mask;
 };
 
+// ------------------------------------------------------------ 3D lattices
+// Unfolded stencil on an Nx x Ny x Nz periodic lattice (rlbm_kernels3d.cu).
+// Per population, kPop3 constants in table rows [k][i] (k < 14: momentum
+// products p0, px, py, pz, p0p0, p0px, p0py, p0pz, pxpx, pxpy, pxpz, pypy,
+// pypz, pzpz; 14 <= k < 28: w_i J of App. A in the order 1, J0, Jx, Jy, Jz,
+// J00, J0x, J0y, J0z, (py^2-pz^2)/2E, (-2px^2+py^2+pz^2)/(2 sqrt3 E), Jxz,
+// Jyz, Jxy; 28..30: p^a/p^0).
+constexpr int kPop3 = 31;
+constexpr int kMaxPop3 = 160;
+
+struct Step3Params {
+  int Nx, Ny, Nz, Q;
+  long long pitch, plane;     // elements: x pitch; plane = pitch * Ny * Nz (one population)
+  double inv_tau;
+  double nref;                // FP32 storage holds d_i = f_i - r_i (see StepParams); 0 for FP64
+  double b0ref;               // nref K1/K2(mbar)/mbar
+  double mref[14];            // moments of r_i (order of the table rows 0..13)
+  SiteConsts sc;
+  const double* rt64;         // FP64 R(zeta) table
+  const int* shift;           // [3][Q]: n_x mod Nx, n_y mod Ny, n_z mod Nz
+  const double* tab64;        // [kPop3][Q]
+  const float* tab32;         // [kPop3][Q] (FP32 storage)
+  unsigned* err;              // sticky device error bits
+};
+
+struct Field3Ptrs {
+  const double* n;
+  const double* ux;
+  const double* uy;
+  const double* uz;
+  const double* T;
+};
+
+cudaError_t launch_step3d(rlbm_dtype dt, const Step3Params& p, const void* fin, void* fout, cudaStream_t s);
+cudaError_t launch_init3d(rlbm_dtype dt, const Step3Params& p, Field3Ptrs f, void* cur, void* prev,
+                          cudaStream_t s);
+cudaError_t launch_moments3d(rlbm_dtype dt, const Step3Params& p, const void* prev, MomentOut o,
+                             cudaStream_t s);
+
 // Kernel launchers (rlbm_kernels_*.cu).
 cudaError_t launch_step_f64(const StepParams<double>& p, const void* fin, void* fout, int qb,
                             cudaStream_t s);

@@ -521,6 +521,76 @@ rlbm_status build_stencil(const rlbm_stencil* st, double m, StencilBuild* out, s
   return RLBM_OK;
 }
 
+rlbm_status build_stencil3d(const rlbm_stencil* st, double m, StencilBuild3* out, std::string* err) {
+  rlbm_status s = build_stencil(st, m, &out->sb, err);
+  if (s != RLBM_OK) return s;
+  const int* g6 = out->sb.groups;        // ascending, as the weights
+  const double v0 = out->sb.v0;
+  qf wq[6];
+  {
+    qf A[6][6], b[6];
+    GroupSums gs[6];
+    for (int k = 0; k < 6; ++k) gs[k] = group_sums(g6[k]);
+    rest_moments_q((qf)m, b);
+    build_system<qf>(gs, (qf)m, (qf)v0, A);
+    solve6<qf>(A, b, wq);
+  }
+  qf cJ1, cJ0, Aq, Bq, Cq, Dq, Eq, k21q, k32q;
+  site_consts(m, &cJ1, &cJ0, &Aq, &Bq, &Cq, &Dq, &Eq, &k21q, &k32q);
+  const qf s3 = q_sqrt((qf)3);
+  const qf mq = (qf)m;
+  const qf b0r = 1 / (k21q * mq);          // K1/K2(mbar)/mbar: J^(0) coefficient of r_i
+  qf mref[14] = {};
+  out->pops.clear();
+  out->halo = 0;
+  for (int k = 0; k < 6; ++k) {
+    const qf len2 = (qf)group_len2(g6[k]);
+    const qf gam = 1 / q_sqrt(1 - (qf)v0 * (qf)v0 * len2);
+    const qf p0 = mq * gam, ps = mq * gam * (qf)v0;
+    for (const auto& v : group_orbit(g6[k])) {
+      Pop3 q;
+      q.group = k;
+      q.nx = v[0];
+      q.ny = v[1];
+      q.nz = v[2];
+      out->halo = std::max(out->halo, std::max(std::abs(v[0]), std::max(std::abs(v[1]), std::abs(v[2]))));
+      const qf px = ps * v[0], py = ps * v[1], pz = ps * v[2];
+      const qf mom[14] = {p0,      px,      py,      pz,      p0 * p0, p0 * px, p0 * py,
+                          p0 * pz, px * px, px * py, px * pz, py * py, py * pz, pz * pz};
+      const qf sh21 = p0 - mq * k21q, sh32 = p0 - mq * k32q;
+      const qf J[14] = {1,
+                        sh21 / Aq,
+                        px / Bq,
+                        py / Bq,
+                        pz / Bq,
+                        (p0 * p0 + cJ1 * p0 + cJ0) / (s3 * Cq),
+                        px * sh32 / Dq,
+                        py * sh32 / Dq,
+                        pz * sh32 / Dq,
+                        (py * py - pz * pz) / (2 * Eq),
+                        (-2 * px * px + py * py + pz * pz) / (2 * s3 * Eq),
+                        px * pz / Eq,
+                        py * pz / Eq,
+                        px * py / Eq};
+      for (int a = 0; a < 14; ++a) {
+        q.c[a] = (double)mom[a];
+        q.c[14 + a] = (double)(wq[k] * J[a]);
+        mref[a] += wq[k] * b0r * mom[a];
+      }
+      q.c[28] = (double)(px / p0);
+      q.c[29] = (double)(py / p0);
+      q.c[30] = (double)(pz / p0);
+      out->pops.push_back(q);
+    }
+  }
+  for (int a = 0; a < 14; ++a) out->mref1[a] = (double)mref[a];
+  if ((int)out->pops.size() > kMaxPop3) {
+    *err = "stencil has more populations than the 3D kernels support (160)";
+    return RLBM_ENOTSUP;
+  }
+  return RLBM_OK;
+}
+
 template <typename CT>
 void fill_pop_table(const StencilBuild& sb, int Nx, int Ny, PopTable<CT>* pt) {
   std::memset(pt, 0, sizeof(*pt));

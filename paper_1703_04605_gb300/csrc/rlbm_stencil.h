@@ -53,6 +53,31 @@ int quadrature_window(const int* groups, double m, double* lo, double* hi);
 // Returns RLBM_OK or an error with a message.
 rlbm_status build_stencil(const rlbm_stencil* st, double m, StencilBuild* out, std::string* err);
 
+// Number of constants per population of an unfolded (3D) stencil: the 14
+// momentum products p0, px, py, pz, p0p0, p0px, p0py, p0pz, pxpx, pxpy,
+// pxpz, pypy, pypz, pzpz; the 14 values w_i J_k(p_i) of App. A in the order
+// 1, J0, Jx, Jy, Jz, J00, J0x, J0y, J0z, (Jyy-Jzz), Jxx, Jxz, Jyz, Jxy; and
+// the velocities p^a/p^0.
+// (kPop3 and kMaxPop3 are defined with the device parameters.)
+
+// One population of the unfolded stencil.
+struct Pop3 {
+  int group;
+  int nx, ny, nz;
+  std::array<double, kPop3> c;   // rounded once from binary128
+};
+
+struct StencilBuild3 {
+  StencilBuild sb;                // validation, v0, weights, site constants
+  std::vector<Pop3> pops;
+  double mref1[14];               // moments of the reference r_i at unit density
+  int halo;                       // largest |n| component
+};
+
+// Unfolded build for 3D lattices (the paper's stencil itself, Table I orbits
+// with signed n_z); same validation and weights as build_stencil.
+rlbm_status build_stencil3d(const rlbm_stencil* st, double m, StencilBuild3* out, std::string* err);
+
 // Per-population constant table for the kernels (CT = float or double).
 template <typename CT>
 void fill_pop_table(const StencilBuild& sb, int Nx, int Ny, PopTable<CT>* pt);

@@ -114,3 +114,73 @@ def batch_tuning(lattices):
     out = [C.c_int(0) for _ in range(2)]
     A.check(L.rlbm_batch_tuning(arr, len(lattices), *[C.byref(o) for o in out]))
     return dict(steps_per_graph=out[0].value, launches_per_step=out[1].value)
+
+
+class Lattice3D:
+    """A periodic Nx x Ny x Nz lattice with the unfolded stencil (the
+    rlbm3_* entry points).  Fields are [Nz, Ny, Nx] arrays; dtype 'f64' or
+    'f32'; v0 = 0 picks the centre of the widest positive-weight window."""
+
+    def __init__(self, groups, m, tau, Nx, Ny, Nz, dtype="f64", v0=0.0, stream=None):
+        L = A.load()
+        self._lib = L
+        self._ctx = C.c_void_p()
+        self._groups = A.int_array(groups)
+        st = A.Stencil(len(groups), self._groups, float(v0))
+        if stream is None:
+            stream = _default_stream()
+        A.check(L.rlbm3_create(C.byref(st), float(m), float(tau), int(Nx), int(Ny), int(Nz), A.DTYPES[dtype],
+                               C.c_void_p(stream) if stream else None, C.byref(self._ctx)), None, True)
+        self.Nx, self.Ny, self.Nz = int(Nx), int(Ny), int(Nz)
+        self.dtype = dtype
+
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            self._lib.rlbm3_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _chk(self, status):
+        A.check(status, self._ctx, True)
+
+    def init(self, n, ux, uy, uz, T):
+        shape = (self.Nz, self.Ny, self.Nx)
+        arrs = [np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), shape))
+                for a in (n, ux, uy, uz, T)]
+        ptrs = [a.ctypes.data_as(C.POINTER(C.c_double)) for a in arrs]
+        self._chk(self._lib.rlbm3_init(self._ctx, *ptrs))
+
+    def step(self, k=1):
+        self._chk(self._lib.rlbm3_step(self._ctx, int(k)))
+
+    def sync(self):
+        self._chk(self._lib.rlbm3_sync(self._ctx))
+
+    def moments(self, mask=A.M_N | A.M_UX | A.M_UY | A.M_UZ | A.M_T | A.M_E):
+        size = self._lib.rlbm3_moments_size(self._ctx, mask)
+        out = np.empty(size, dtype=np.float64)
+        self._chk(self._lib.rlbm3_moments(self._ctx, out.ctypes.data_as(C.POINTER(C.c_double)), mask))
+        res, plane = {}, 0
+        N = self.Nx * self.Ny * self.Nz
+        for bit, names in A.MASK_PLANES3:
+            if mask & bit:
+                for nm in names:
+                    res[nm] = out[plane * N:(plane + 1) * N].reshape(self.Nz, self.Ny, self.Nx)
+                    plane += 1
+        return res
+
+    def info(self):
+        inf = A.Info3()
+        self._chk(self._lib.rlbm3_get_info(self._ctx, C.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in A.Info3._fields_}

@@ -9,6 +9,8 @@ Stencils (six groups of Table I, folded to 2D):
   E5   G1, G14, G49, G51, G60, G70 at m = 0.36 (the stencil of the paper's
        BAMPS comparison), v0 = 0.1488232 (window (0.14882301, 0.14882336)),
        Q = 73, halo 6
+  S2   G3, G9, G10, G14, G17, G21 at m = 3, v0 = 0.227 (window
+       (0.22326, 0.23074)), Q = 49, halo 4
 """
 import math
 
@@ -17,6 +19,7 @@ import numpy as np
 STENCIL_M1 = dict(groups=[5, 12, 14, 17, 21, 26], m=1.0, v0=0.23342)
 STENCIL_G16 = dict(groups=[1, 2, 3, 4, 5, 6], m=5.0, v0=0.398)
 STENCIL_E5 = dict(groups=[1, 14, 49, 51, 60, 70], m=0.36, v0=0.1488232)
+STENCIL_S2 = dict(groups=[3, 9, 10, 14, 17, 21], m=3.0, v0=0.227)
 
 
 def seed(config_index):
@@ -82,6 +85,25 @@ def random_flow(N=4096, sigma=8.0, dn=0.01, dT=0.01, du=0.05, config_index=2):
     rng = np.random.default_rng(seed(config_index))
     g = [_smooth_unit(rng, N, sigma) for _ in range(4)]
     return dict(n=1.0 + dn * g[0], T=1.0 + dT * g[1], ux=du * g[2], uy=du * g[3])
+
+
+def _smooth_unit3(rng, N, sigma):
+    """White N(0,1) on an N^3 periodic grid, Gaussian-smoothed (width sigma
+    cells) by FFT, rescaled to zero mean and unit standard deviation."""
+    g = rng.standard_normal((N, N, N))
+    k = np.fft.fftfreq(N) * 2 * np.pi
+    kz, ky, kx = np.meshgrid(k, k, k, indexing="ij")
+    filt = np.exp(-0.5 * sigma * sigma * (kx * kx + ky * ky + kz * kz))
+    s = np.real(np.fft.ifftn(np.fft.fftn(g) * filt))
+    s -= s.mean()
+    return s / s.std()
+
+
+def random_flow3d(N=256, sigma=8.0, dn=0.01, dT=0.01, du=0.05, config_index=6):
+    """The random-flow recipe on an N^3 periodic lattice ([z, y, x] arrays)."""
+    rng = np.random.default_rng(seed(config_index))
+    g = [_smooth_unit3(rng, N, sigma) for _ in range(5)]
+    return dict(n=1.0 + dn * g[0], T=1.0 + dT * g[1], ux=du * g[2], uy=du * g[3], uz=du * g[4])
 
 
 def random_flow_crop(N_full=4096, crop=1024, **kw):

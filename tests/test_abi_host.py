@@ -28,7 +28,7 @@ def _header_functions():
     with open(os.path.join(ROOT, "include", "rlbm.h")) as fh:
         txt = fh.read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(rlbm_[a-z0-9_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(rlbm3?_[a-z0-9_]+)\s*\(", txt)))
 
 
 def test_exports_every_declared_symbol(lib):
@@ -128,3 +128,19 @@ def test_null_context_calls(lib):
     null2 = (C.c_void_p * 2)(None, None)
     assert lib.rlbm_batch_step(null2, 2, 1) == A.RLBM_EINVAL
     assert lib.rlbm_batch_tuning(null2, 2, None, None) == A.RLBM_EINVAL
+
+
+def test_3d_entry_points_without_device(lib):
+    g = A.int_array([1, 2, 3, 4, 5, 6])
+    st = A.Stencil(6, g, 0.398)
+    ctx = C.c_void_p()
+    assert lib.rlbm3_create(C.byref(st), 5.0, 0.8, 4, 4, 0, 0, None, C.byref(ctx)) == A.RLBM_EINVAL
+    assert lib.rlbm3_create(C.byref(st), 5.0, 0.5, 4, 4, 4, 0, None, C.byref(ctx)) == A.RLBM_EINVAL
+    assert lib.rlbm3_create(C.byref(st), 5.0, 0.8, 4, 4, 4, 2, None, C.byref(ctx)) == A.RLBM_ENOTSUP
+    s = lib.rlbm3_create(C.byref(st), 5.0, 0.8, 4, 4, 4, 0, None, C.byref(ctx))
+    assert s == A.RLBM_ECUDA and not ctx.value
+    assert b"device" in lib.rlbm3_last_error(None)
+    assert lib.rlbm3_step(None, 1) == A.RLBM_EINVAL
+    assert lib.rlbm3_sync(None) == A.RLBM_EINVAL
+    assert lib.rlbm3_moments_size(None, 1) == 0
+    lib.rlbm3_destroy(None)

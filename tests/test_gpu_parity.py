@@ -9,7 +9,7 @@ from paper_1703_04605_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-STENCILS = {"M1": W.STENCIL_M1, "G16": W.STENCIL_G16, "E5": W.STENCIL_E5}
+STENCILS = {"M1": W.STENCIL_M1, "G16": W.STENCIL_G16, "E5": W.STENCIL_E5, "S2": W.STENCIL_S2}
 TOL = {"f64": 1e-12, "f32": 1e-5, "bf16dev": 2e-3}
 
 
@@ -19,7 +19,7 @@ def _built():
     build.build()
 
 
-@pytest.mark.parametrize("name", ["M1", "G16", "E5"])
+@pytest.mark.parametrize("name", ["M1", "G16", "E5", "S2"])
 def test_f64_small_ragged(name):
     # 37 x 29 = 1073 sites: nine blocks of 128 sites and a ragged tail;
     # Q = 58, 39, 73 exercise three population buckets.
@@ -89,12 +89,12 @@ def test_f64_degenerate_shapes(shape):
     assert np.max(np.abs(got["ux"] - ref["ux"])) < 1e-12 * max(umax, 1.0)
 
 
-@pytest.mark.parametrize("name", ["M1", "G16", "E5"])
+@pytest.mark.parametrize("name", ["M1", "G16", "E5", "S2"])
 def test_f32_small_ragged(name):
     st = STENCILS[name]
     f = smooth_fields(45, 31, seed=17)
     got, info = run_gpu(st, 0.8, f, "f32", 50)
-    assert info["kernel"] == {"M1": 1, "G16": 2, "E5": 3}[name]
+    assert info["kernel"] == {"M1": 1, "G16": 2, "E5": 3, "S2": 4}[name]
     ref = run_oracle(st, 0.8, f, 50)
     e = errors(got, ref)
     assert max(e.values()) < TOL["f32"], e
@@ -131,12 +131,12 @@ def test_f32_generic_kernel_tiny_lattice():
     assert e["n"] < 1e-5 and e["T"] < 1e-5, e
 
 
-@pytest.mark.parametrize("name", ["M1", "G16", "E5"])
+@pytest.mark.parametrize("name", ["M1", "G16", "E5", "S2"])
 def test_bf16dev_small_ragged(name):
     st = STENCILS[name]
     f = smooth_fields(45, 31, seed=19)
     got, info = run_gpu(st, 0.8, f, "bf16dev", 50)
-    assert info["kernel"] == {"M1": 1, "G16": 2, "E5": 3}[name]
+    assert info["kernel"] == {"M1": 1, "G16": 2, "E5": 3, "S2": 4}[name]
     assert info["bytes_per_site"] == 2 * info["Q"] * 2
     ref = run_oracle(st, 0.8, f, 50)
     e = errors(got, ref)
