@@ -25,7 +25,9 @@ struct rlbm_ctx3 {
   long long t = 0;
   unsigned* d_err = nullptr;
   double* d_rt64 = nullptr;
+  float* d_rt32 = nullptr;
   int* d_shift = nullptr;
+  long long* d_off = nullptr;
   double* d_tab64 = nullptr;
   float* d_tab32 = nullptr;
   double* d_fields = nullptr;  // 5 planes for rlbm3_init
@@ -53,7 +55,8 @@ rlbm_status cuda_fail3(rlbm_ctx3* c, cudaError_t e, const char* where) {
 
 void release3(rlbm_ctx3* c) {
   if (c->buf[0] || c->buf[1]) cudaStreamSynchronize(c->stream);
-  for (void* p : {c->buf[0], c->buf[1], (void*)c->d_err, (void*)c->d_rt64, (void*)c->d_shift, (void*)c->d_tab64,
+  for (void* p : {c->buf[0], c->buf[1], (void*)c->d_err, (void*)c->d_rt64, (void*)c->d_rt32, (void*)c->d_shift, (void*)c->d_off,
+                  (void*)c->d_tab64,
                   (void*)c->d_tab32, (void*)c->d_fields, (void*)c->d_out})
     if (p) cudaFree(p);
   c->buf[0] = c->buf[1] = nullptr;
@@ -116,28 +119,34 @@ rlbm_status rlbm3_create(const rlbm_stencil* st, double m, double tau, int Nx, i
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess || ndev == 0) return fail3(nullptr, RLBM_ECUDA, "no CUDA device available");
-  // constant table [kPop3][Q] and shifts [3][Q]
+  // constant table [Q][kRow3], shifts [3][Q], interior offsets [Q]
   const int Q = c->Q;
-  std::vector<double> t64((size_t)kPop3 * Q);
-  std::vector<float> t32((size_t)kPop3 * Q);
+  const long long pitch = ((long long)Nx + 31) / 32 * 32;
+  std::vector<double> t64((size_t)kRow3 * Q, 0.0);
+  std::vector<float> t32((size_t)kRow3 * Q, 0.0f);
   std::vector<int> sh((size_t)3 * Q);
+  std::vector<long long> off(Q);
   for (int i = 0; i < Q; ++i) {
     const Pop3& q = c->sb.pops[i];
     for (int k = 0; k < kPop3; ++k) {
-      t64[(size_t)k * Q + i] = q.c[k];
-      t32[(size_t)k * Q + i] = (float)q.c[k];
+      t64[(size_t)i * kRow3 + k] = q.c[k];
+      t32[(size_t)i * kRow3 + k] = (float)q.c[k];
     }
     sh[i] = ((q.nx % Nx) + Nx) % Nx;
     sh[Q + i] = ((q.ny % Ny) + Ny) % Ny;
     sh[2 * Q + i] = ((q.nz % Nz) + Nz) % Nz;
+    off[i] = -(((long long)q.nz * Ny + q.ny) * pitch + q.nx);
   }
   const size_t fbytes = (size_t)Q * (size_t)c->plane * c->elem;
   const size_t nsite = (size_t)Nx * Ny * Nz;
   const auto& r64 = ratio_table64();
+  const auto& r32 = ratio_table32();
   bool ok = cudaMalloc(&c->buf[0], fbytes) == cudaSuccess && cudaMalloc(&c->buf[1], fbytes) == cudaSuccess &&
             cudaMalloc(&c->d_err, sizeof(unsigned)) == cudaSuccess &&
             cudaMalloc(&c->d_rt64, r64.size() * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->d_rt32, r32.size() * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&c->d_shift, sh.size() * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&c->d_off, off.size() * sizeof(long long)) == cudaSuccess &&
             cudaMalloc(&c->d_tab64, t64.size() * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&c->d_tab32, t32.size() * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&c->d_fields, 5 * nsite * sizeof(double)) == cudaSuccess;
@@ -145,9 +154,12 @@ rlbm_status rlbm3_create(const rlbm_stencil* st, double m, double tau, int Nx, i
     release3(c.get());
     return fail3(nullptr, RLBM_ENOMEM, "device allocation failed");
   }
-  c->device_bytes = 2 * fbytes + r64.size() * 8 + sh.size() * 4 + t64.size() * 12 + 5 * nsite * 8 + 4;
+  c->device_bytes = 2 * fbytes + r64.size() * 8 + r32.size() * 4 + sh.size() * 4 + off.size() * 8 + t64.size() * 12 +
+                    5 * nsite * 8 + 4;
   e = cudaMemcpy(c->d_rt64, r64.data(), r64.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_rt32, r32.data(), r32.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_shift, sh.data(), sh.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_off, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_tab64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_tab32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(unsigned));
@@ -165,7 +177,10 @@ rlbm_status rlbm3_create(const rlbm_stencil* st, double m, double tau, int Nx, i
   p.inv_tau = 1.0 / tau;
   p.sc = c->sb.sb.sc;
   p.rt64 = c->d_rt64;
+  p.rt32 = c->d_rt32;
   p.shift = c->d_shift;
+  p.off = c->d_off;
+  p.halo = c->sb.halo;
   p.tab64 = c->d_tab64;
   p.tab32 = c->d_tab32;
   p.err = c->d_err;

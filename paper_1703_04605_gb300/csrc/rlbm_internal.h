@@ -144,12 +144,14 @@ struct MomentOut {
 
 // ------------------------------------------------------------ 3D lattices
 // Unfolded stencil on an Nx x Ny x Nz periodic lattice (rlbm_kernels3d.cu).
-// Per population, kPop3 constants in table rows [k][i] (k < 14: momentum
-// products p0, px, py, pz, p0p0, p0px, p0py, p0pz, pxpx, pxpy, pxpz, pypy,
-// pypz, pzpz; 14 <= k < 28: w_i J of App. A in the order 1, J0, Jx, Jy, Jz,
-// J00, J0x, J0y, J0z, (py^2-pz^2)/2E, (-2px^2+py^2+pz^2)/(2 sqrt3 E), Jxz,
-// Jyz, Jxy; 28..30: p^a/p^0).
+// Per population i, one table row of kRow3 values at [i * kRow3] (16-byte
+// aligned for vector loads): entries 0..13 momentum products p0, px, py, pz,
+// p0p0, p0px, p0py, p0pz, pxpx, pxpy, pxpz, pypy, pypz, pzpz; 14..27 w_i J of
+// App. A in the order 1, J0, Jx, Jy, Jz, J00, J0x, J0y, J0z,
+// (py^2-pz^2)/2E, (-2px^2+py^2+pz^2)/(2 sqrt3 E), Jxz, Jyz, Jxy; 28..30
+// p^a/p^0; 31 zero.
 constexpr int kPop3 = 31;
+constexpr int kRow3 = 32;
 constexpr int kMaxPop3 = 160;
 
 struct Step3Params {
@@ -161,9 +163,14 @@ struct Step3Params {
   double mref[14];            // moments of r_i (order of the table rows 0..13)
   SiteConsts sc;
   const double* rt64;         // FP64 R(zeta) table
+  const float* rt32;          // FP32 R(zeta) table (FP32 storage: solve iterations)
   const int* shift;           // [3][Q]: n_x mod Nx, n_y mod Ny, n_z mod Nz
-  const double* tab64;        // [kPop3][Q]
-  const float* tab32;         // [kPop3][Q] (FP32 storage)
+  const long long* off;       // [Q]: -(n_z Ny pitch + n_y pitch + n_x), the source
+                              // element of population i relative to a site at least
+                              // halo cells from every face
+  int halo;                   // largest |n| component
+  const double* tab64;        // [Q][kRow3]
+  const float* tab32;         // [Q][kRow3] (FP32 storage)
   unsigned* err;              // sticky device error bits
 };
 

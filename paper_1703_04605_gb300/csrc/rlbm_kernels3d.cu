@@ -7,7 +7,8 @@
 // and the Anderson-Witting relaxation with weight p_i.U/(p_i^0 tau).
 //
 // Generic kernels: the population loop runs over a constant table in global
-// memory (every thread of a warp reads the same entry), in two passes: the
+// memory (one 32-entry row per population, read with vector loads; every
+// thread of a warp reads the same row), in two passes: the
 // first pulls and accumulates the moments, the second pulls again (the values
 // are in L1/L2) to relax and store, so no per-thread population array is held
 // in registers whatever Q is.  The site solve is FP64; FP64 storage holds f_i,
@@ -41,6 +42,28 @@ __device__ __forceinline__ void site3(long long s, const Step3Params& p, int& x,
   const long long r = s / p.Nx;
   y = (int)(r % p.Ny);
   z = (int)(r / p.Ny);
+}
+
+// Four consecutive table entries (16-byte aligned) by vector loads.
+__device__ __forceinline__ void ld4(const float* p, float* d) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  d[0] = v.x;
+  d[1] = v.y;
+  d[2] = v.z;
+  d[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double* d) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  d[0] = a.x;
+  d[1] = a.y;
+  d[2] = b.x;
+  d[3] = b.y;
+}
+
+__device__ __forceinline__ bool interior3(const Step3Params& p, int x, int y, int z) {
+  const int h = p.halo;
+  return x >= h && x < p.Nx - h && y >= h && y < p.Ny - h && z >= h && z < p.Nz - h;
 }
 
 // Source element of population i for the site (x, y, z): x - n_i, periodic.
@@ -125,6 +148,108 @@ __device__ __forceinline__ Macro3 solve3(const double* m, const SiteConsts& sc, 
   return o;
 }
 
+// The same solve for FP32 storage: the Landau and EOS Newton iterations in
+// FP32, then one Newton step of each with the residual formed in FP64 (the
+// Landau Jacobian of the last FP32 iterate; the FP64 R(zeta) table), which
+// squares an error already near FP32 rounding.  About a tenth of the FP64
+// operations of solve3, the pipe that bounds the FP32 kernel otherwise.
+__device__ __forceinline__ Macro3 solve3_mixed(const double* m, const SiteConsts& sc,
+                                               const double* __restrict__ rt64, const float* __restrict__ rt32,
+                                               unsigned& fl) {
+  float mf[14];
+#pragma unroll
+  for (int k = 0; k < 14; ++k) mf[k] = (float)m[k];
+  const float T00 = mf[4];
+  const float T0[3] = {mf[5], mf[6], mf[7]};
+  const float Tij[3][3] = {{mf[8], mf[9], mf[10]}, {mf[9], mf[11], mf[12]}, {mf[10], mf[12], mf[13]}};
+  const float den = T00 + (mf[8] + mf[11] + mf[13]) * (1.0f / 3.0f);
+  float v[3] = {T0[0] / den, T0[1] / den, T0[2] / den};
+  float J[3][3];
+#pragma unroll 1
+  for (int it = 0; it < 12; ++it) {
+    const float e = T00 - T0[0] * v[0] - T0[1] * v[1] - T0[2] * v[2];
+    float F[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      F[a] = T0[a] - Tij[a][0] * v[0] - Tij[a][1] * v[1] - Tij[a][2] * v[2] - e * v[a];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) J[a][b] = -Tij[a][b] - (a == b ? e : 0.0f) + v[a] * T0[b];
+    }
+    const float c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    const float c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const float c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    const float id = 1.0f / (J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02);
+    const float d0 = (F[0] * c00 + J[0][1] * (F[2] * J[1][2] - F[1] * J[2][2]) +
+                      J[0][2] * (F[1] * J[2][1] - F[2] * J[1][1])) * id;
+    const float d1 = (J[0][0] * (F[1] * J[2][2] - F[2] * J[1][2]) + F[0] * c01 +
+                      J[0][2] * (F[2] * J[1][0] - F[1] * J[2][0])) * id;
+    const float d2 = (J[0][0] * (F[2] * J[1][1] - F[1] * J[2][1]) + J[0][1] * (F[1] * J[2][0] - F[2] * J[1][0]) +
+                      F[0] * c02) * id;
+    v[0] -= d0;
+    v[1] -= d1;
+    v[2] -= d2;
+    if (fabsf(d0) + fabsf(d1) + fabsf(d2) < 1e-7f) break;
+  }
+  // one Newton step with the FP64 residual
+  double vd[3] = {v[0], v[1], v[2]};
+  {
+    const double e = m[4] - m[5] * vd[0] - m[6] * vd[1] - m[7] * vd[2];
+    const double Td[3][3] = {{m[8], m[9], m[10]}, {m[9], m[11], m[12]}, {m[10], m[12], m[13]}};
+    double F[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      F[a] = m[5 + a] - Td[a][0] * vd[0] - Td[a][1] * vd[1] - Td[a][2] * vd[2] - e * vd[a];
+    const double c00 = (double)J[1][1] * J[2][2] - (double)J[1][2] * J[2][1];
+    const double c01 = (double)J[1][2] * J[2][0] - (double)J[1][0] * J[2][2];
+    const double c02 = (double)J[1][0] * J[2][1] - (double)J[1][1] * J[2][0];
+    const double id = 1.0 / (J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02);
+    vd[0] -= (F[0] * c00 + J[0][1] * (F[2] * J[1][2] - F[1] * J[2][2]) + J[0][2] * (F[1] * J[2][1] - F[2] * J[1][1])) * id;
+    vd[1] -= (J[0][0] * (F[1] * J[2][2] - F[2] * J[1][2]) + F[0] * c01 + J[0][2] * (F[2] * J[1][0] - F[1] * J[2][0])) * id;
+    vd[2] -= (J[0][0] * (F[2] * J[1][1] - F[1] * J[2][1]) + J[0][1] * (F[1] * J[2][0] - F[2] * J[1][0]) + F[0] * c02) * id;
+  }
+  Macro3 o;
+  const double v2 = vd[0] * vd[0] + vd[1] * vd[1] + vd[2] * vd[2];
+  if (!(v2 < 1.0)) fl |= ERR_LANDAU;
+  const double g = 1.0 / sqrt(1.0 - v2);
+  o.U0 = g;
+  o.Ux = g * vd[0];
+  o.Uy = g * vd[1];
+  o.Uz = g * vd[2];
+  o.e = m[4] - m[5] * vd[0] - m[6] * vd[1] - m[7] * vd[2];
+  o.n = g * (m[0] - vd[0] * m[1] - vd[1] * m[2] - vd[2] * m[3]);
+  if (!(o.n > 0.0)) fl |= ERR_DENSITY;
+  // EOS: FP32 Newton with the FP32 table, one FP64 step, R at the final T
+  const double y = o.e / o.n;
+  const double mb = sc.mbar;
+  if (!(y > mb)) fl |= ERR_EOS;
+  float T = (float)((y - mb) / (3.0 - 1.5 * (mb * mb) / (y * y)));
+  const float mbf = (float)mb, yf = (float)y;
+  float slope = 3.0f;
+#pragma unroll 1
+  for (int it = 0; it < 20; ++it) {
+    if (!(T > 0.0f)) {
+      fl |= ERR_EOS;
+      T = 1.0f;
+      break;
+    }
+    const float z = mbf / T;
+    const float R = ratio32(z, rt32, fl);
+    slope = eos_slope<float>(R, z);
+    const float dT = (3.0f * T + mbf * R - yf) / slope;
+    T -= dT;
+    if (fabsf(dT) < 3e-7f * T) break;
+  }
+  double Td = T;
+  Td -= (3.0 * Td + mb * ratio64(mb / Td, rt64, fl) - y) / (double)slope;
+  if (!(Td > 0.0)) {
+    fl |= ERR_EOS;
+    Td = 1.0;
+  }
+  o.T = Td;
+  o.R = ratio64(mb / Td, rt64, fl);
+  return o;
+}
+
 // n b^(k) of App. B (corrected) for the 14 polynomials, table order.
 __device__ __forceinline__ void projections3(const Macro3& o, const SiteConsts& sc, double* bn) {
   const double n = o.n, U0 = o.U0, Ux = o.Ux, Uy = o.Uy, Uz = o.Uz, R = o.R, T = o.T;
@@ -155,11 +280,18 @@ __device__ __forceinline__ void moments3(const Step3Params& p, const S* __restri
   S mm[14];
 #pragma unroll
   for (int k = 0; k < 14; ++k) mm[k] = S(0);
-#pragma unroll 1
+  const bool in = interior3(p, x, y, z);
+  const long long here = at3(p, x, y, z);
+#pragma unroll 4
   for (int i = 0; i < p.Q; ++i) {
-    const S f = __ldg(fin + (long long)i * p.plane + source3(p, i, x, y, z));
+    const long long src = in ? here + __ldg(p.off + i) : source3(p, i, x, y, z);
+    const S f = __ldg(fin + (long long)i * p.plane + src);
+    S c[16];
+    const S* row = tab + (long long)i * kRow3;
 #pragma unroll
-    for (int k = 0; k < 14; ++k) mm[k] = fma_t(f, __ldg(tab + k * p.Q + i), mm[k]);
+    for (int j = 0; j < 4; ++j) ld4(row + 4 * j, c + 4 * j);
+#pragma unroll
+    for (int k = 0; k < 14; ++k) mm[k] = fma_t(f, c[k], mm[k]);
   }
 #pragma unroll
   for (int k = 0; k < 14; ++k) md[k] = (double)mm[k] + p.mref[k];
@@ -176,7 +308,9 @@ __global__ void __launch_bounds__(128) step3d_kernel(const __grid_constant__ Ste
     site3(s, p, x, y, z);
     double md[14];
     moments3<S>(p, fin, x, y, z, md);
-    const Macro3 o = solve3(md, p.sc, p.rt64, fl);
+    Macro3 o;
+    if constexpr (sizeof(S) == 4) o = solve3_mixed(md, p.sc, p.rt64, p.rt32, fl);
+    else o = solve3(md, p.sc, p.rt64, fl);
     double bn[14];
     projections3(o, p.sc, bn);
     bn[0] -= p.b0ref;                                  // f^eq - r_i (r_i = 0 for FP64 storage)
@@ -186,16 +320,22 @@ __global__ void __launch_bounds__(128) step3d_kernel(const __grid_constant__ Ste
     const S a0 = (S)(o.U0 * p.inv_tau), ax = (S)(o.Ux * p.inv_tau), ay = (S)(o.Uy * p.inv_tau),
             az = (S)(o.Uz * p.inv_tau);
     const S* tab = table<S>(p);
-    S* out = fout + at3(p, x, y, z);
-#pragma unroll 1
+    const bool in = interior3(p, x, y, z);
+    const long long here = at3(p, x, y, z);
+    S* out = fout + here;
+#pragma unroll 4
     for (int i = 0; i < p.Q; ++i) {
-      const S f = __ldg(fin + (long long)i * p.plane + source3(p, i, x, y, z));
+      const long long src = in ? here + __ldg(p.off + i) : source3(p, i, x, y, z);
+      const S f = __ldg(fin + (long long)i * p.plane + src);
+      S c[20];                                         // row entries 12..31
+      const S* row = tab + (long long)i * kRow3 + 12;
+#pragma unroll
+      for (int j = 0; j < 5; ++j) ld4(row + 4 * j, c + 4 * j);
       S feq = S(0);
 #pragma unroll
-      for (int k = 0; k < 14; ++k) feq = fma_t(b[k], __ldg(tab + (14 + k) * p.Q + i), feq);
+      for (int k = 0; k < 14; ++k) feq = fma_t(b[k], c[2 + k], feq);
       // weight p_i.U/(p_i^0 tau) = (U0 - v_i . U)/tau
-      const S om = a0 - ax * __ldg(tab + 28 * p.Q + i) - ay * __ldg(tab + 29 * p.Q + i) -
-                   az * __ldg(tab + 30 * p.Q + i);
+      const S om = a0 - ax * c[16] - ay * c[17] - az * c[18];
       __stcs(out + (long long)i * p.plane, fma_t(om, feq - f, f));
     }
   }
@@ -231,7 +371,7 @@ __global__ void __launch_bounds__(128) init3d_kernel(const __grid_constant__ Ste
     for (int i = 0; i < p.Q; ++i) {
       double feq = 0.0;
 #pragma unroll
-      for (int k = 0; k < 14; ++k) feq = fma(bn[k], __ldg(p.tab64 + (14 + k) * p.Q + i), feq);
+      for (int k = 0; k < 14; ++k) feq = fma(bn[k], __ldg(p.tab64 + (long long)i * kRow3 + 14 + k), feq);
       cur[(long long)i * p.plane + here] = (S)feq;
       prev[(long long)i * p.plane + source3(p, i, x, y, z)] = (S)feq;
     }
@@ -259,7 +399,7 @@ __global__ void __launch_bounds__(128) moments3d_kernel(const __grid_constant__ 
     for (int i = 0; i < p.Q; ++i) {
       const double f = (double)prev[(long long)i * p.plane + source3(p, i, x, y, z)];
 #pragma unroll
-      for (int k = 0; k < 14; ++k) md[k] = fma(f, __ldg(tab + k * p.Q + i), md[k]);
+      for (int k = 0; k < 14; ++k) md[k] = fma(f, __ldg(tab + (long long)i * kRow3 + k), md[k]);
     }
 #pragma unroll
     for (int k = 0; k < 14; ++k) md[k] += p.mref[k];
