@@ -133,6 +133,40 @@ def cpu_baseline(seconds=12.0, side=96, procs=None):
                                          max(r["steps"] for r in res), max(r["seconds"] for r in res))}
 
 
+def cpu_baseline3d(seconds=10.0, side=12, procs=None):
+    """The FP64 oracle's 3D lattice on the host cores: one process per core,
+    each advancing its own side^3 lattice of the 3D random-flow recipe (same
+    stencil, m, tau) for about `seconds` of CPU time."""
+    procs = procs or os.cpu_count() or 1
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = (
+        "import sys, time, json; sys.path.insert(0, %r)\n"
+        "from paper_1703_04605_gb300 import workloads as W\n"
+        "from oracle import lattice as L\n"
+        "f = W.random_flow3d(%d)\n"
+        "st = W.STENCIL_M1\n"
+        "lat = L.make_lattice(st['groups'], st['m'], st['v0'], %r, (%d, %d, %d), two_d=False)\n"
+        "lat.init(f['n'], f['ux'], f['uy'], f['T'], uz=f['uz'])\n"
+        "t0 = time.process_time(); w0 = time.time(); k = 0\n"
+        "while time.process_time() - t0 < %r:\n"
+        "    lat.step(1); k += 1\n"
+        "print(json.dumps({'steps': k, 'seconds': time.time() - w0}))\n"
+    ) % (ROOT, side, TAU, side, side, side, seconds)
+    ps = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                           text=True, env=env) for _ in range(procs)]
+    res = []
+    for p in ps:
+        out, _ = p.communicate()
+        if p.returncode == 0:
+            res.append(json.loads(out.strip().splitlines()[-1]))
+    if not res:
+        return {"value": None, "unit": "MLUPS", "cores": procs, "kind": "oracle", "sample": "failed"}
+    return {"value": sum(side ** 3 * r["steps"] / r["seconds"] for r in res) / 1e6, "unit": "MLUPS",
+            "cores": len(res), "kind": "oracle",
+            "sample": "%d processes x one %d^3 lattice of the 3D recipe, %d-%d steps each, 1 thread each" % (
+                len(res), side, min(r["steps"] for r in res), max(r["steps"] for r in res))}
+
+
 def kernel_name(dtype, variant):
     stencil = {1: "5,12,14,17,21,26", 2: "1,2,3,4,5,6", 3: "1,14,49,51,60,70", 4: "3,9,10,14,17,21"}.get(variant)
     if dtype == "f64":
@@ -435,8 +469,9 @@ def run_blast(args):
 def run_random3d(args):
     """Native 3D: the random-flow recipe on a 256^3 periodic lattice with the
     unfolded stencil G5,G12,G14,G17,G21,G26 (Q = 96), m/T = 1, tau = 0.8, FP32
-    storage (generic 3D kernel); FP64 timed on fewer steps; FP32 error against
-    the FP64 path after the same steps."""
+    storage (the compiled 3D kernel); FP64 timed on fewer steps; FP32 error
+    against the FP64 path after the same steps; the oracle's 3D lattice on the
+    host cores."""
     import torch
     from paper_1703_04605_gb300 import Lattice3D, build, workloads as W
     ws, rank, local = dist_env()
@@ -498,10 +533,14 @@ def run_random3d(args):
                        "sites": int(sites), "Q": info["Q"], "l2": "inputs larger than L2"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
-                         "kernel": "step3d_kernel<float>", "bytes_per_site": info["bytes_per_site"]},
+                         "kernel": ("fused3d_kernel<Stencil3Def<5,12,14,17,21,26>>" if info["kernel"] == 1
+                                    else "step3d_kernel<float>"),
+                         "bytes_per_site": info["bytes_per_site"]},
             "f64": {"MLUPS": sites / (ms64 / 1e3) / 1e6, "ms_per_step": ms64, "steps": k64,
                     "frac_hbm": info64["bytes_per_site"] * sites / (ms64 / 1e3) / 1e9 / peak},
             "error_vs_f64": err, "gpu_launches": args.steps, "clocks": clk.summary()}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline3d()
     emit(line, rank)
 
 

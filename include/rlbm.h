@@ -198,6 +198,9 @@ typedef struct {
   long long t;
   size_t bytes_per_site;    /* 2 Q sizeof(storage)                            */
   size_t device_bytes;
+  int kernel;               /* step kernel: 0 generic; 1, 2 compiled for the
+                               stencils {5,12,14,17,21,26}, {1..6} (FP32
+                               storage, lattice at least a halo wide)         */
 } rlbm3_info;
 
 /* As rlbm_create, with Nz >= 1; dtype RLBM_F64 or RLBM_F32 (ENOTSUP for

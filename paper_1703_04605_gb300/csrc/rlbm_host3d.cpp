@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "rlbm_stencil.h"
+#include "rlbm_stencils.h"
 
 using namespace rlbm;
 
@@ -36,6 +37,8 @@ struct rlbm_ctx3 {
   size_t device_bytes = 0;
   bool initialised = false;
   Step3Params p{};
+  int fused = 0;               // 0 generic kernel; 1: {5,12,14,17,21,26}, 2: {1..6} (FP32)
+  Fused3Params fp{};
   std::string last_error;
 };
 
@@ -62,12 +65,77 @@ void release3(rlbm_ctx3* c) {
   c->buf[0] = c->buf[1] = nullptr;
 }
 
+HL split3(double v) {
+  HL h;
+  h.hi = (float)v;
+  h.lo = (float)(v - (double)h.hi);
+  return h;
+}
+
+// The compiled 3D stencil for these groups, when its population order is the
+// host's (the storage planes) and the lattice is at least a halo wide.
+template <class D>
+bool same_order(const rlbm_ctx3* c) {
+  for (int k = 0; k < 6; ++k)
+    if (c->sb.sb.groups[k] != D::groups[k]) return false;
+  if (D::Q != c->Q) return false;
+  for (int i = 0; i < D::Q; ++i) {
+    const Pop3& q = c->sb.pops[i];
+    if (q.group != D::U.grp[i] || q.nx != D::U.nx[i] || q.ny != D::U.ny[i] || q.nz != D::U.nz[i]) return false;
+  }
+  const int h = D::U.halo;
+  return c->Nx >= h && c->Ny >= h && c->Nz >= h;
+}
+
+int fused3_kind(const rlbm_ctx3* c) {
+  if (c->dtype != RLBM_F32) return 0;
+  if (same_order<Stencil3M1>(c)) return 1;
+  if (same_order<Stencil3G16>(c)) return 2;
+  return 0;
+}
+
+// Parameters of the stencil-specialised 3D kernel at reference density nref.
+void fill_fused3(rlbm_ctx3* c, double nref) {
+  Fused3Params& f = c->fp;
+  std::memset(&f, 0, sizeof f);
+  const StencilBuild& sb = c->sb.sb;
+  f.Nx = c->Nx;
+  f.Ny = c->Ny;
+  f.Nz = c->Nz;
+  f.pitch = c->pitch;
+  f.zstride = c->pitch * c->Ny;
+  f.plane = c->plane;
+  f.inv_tau = (float)(1.0 / c->tau);
+  f.v0 = (float)sb.v0;
+  f.mb = (float)sb.mbar;
+  f.k21 = (float)sb.sc.k21;
+  f.cb00_1 = (float)sb.sc.cb00_1;
+  f.mY = (float)sb.sc.mY;
+  f.cv_r = (float)sb.cv_r;
+  f.Rr = split3(sb.sc.Rr);
+  const double N0r = nref * c->sb.mref1[0];
+  const double er = nref * c->sb.mref1[4];
+  f.nr = split3(N0r);
+  f.yr = split3(er / N0r);
+  for (int k = 0; k < 14; ++k) f.mref[k] = split3(nref * c->sb.mref1[k]);
+  f.Rr64 = sb.sc.Rr;
+  f.mb64 = sb.mbar;
+  for (int g = 0; g < 6; ++g) {
+    for (int q = 0; q < 5; ++q) f.gm[g][q] = split3(sb.gm[g][q]);
+    for (int q = 0; q < 10; ++q) f.gf[g][q] = split3(c->sb.gf3[g][q]);
+  }
+  f.rt64 = c->d_rt64;
+  f.rt32 = c->d_rt32;
+  f.err = c->d_err;
+}
+
 // Reference r_i of the FP32 storage at density nref (FP64 storage: none).
 void set_reference3(rlbm_ctx3* c, double nref) {
   if (c->dtype == RLBM_F64) nref = 0.0;
   c->p.nref = nref;
   c->p.b0ref = nref * c->sb.sb.b0ref1;
   for (int k = 0; k < 14; ++k) c->p.mref[k] = nref * c->sb.mref1[k];
+  if (c->fused) fill_fused3(c, nref);
 }
 
 rlbm_status check_error3(rlbm_ctx3* c) {
@@ -184,6 +252,7 @@ rlbm_status rlbm3_create(const rlbm_stencil* st, double m, double tau, int Nx, i
   p.tab64 = c->d_tab64;
   p.tab32 = c->d_tab32;
   p.err = c->d_err;
+  c->fused = fused3_kind(c.get());
   set_reference3(c.get(), 1.0);
   *out = c.release();
   return RLBM_OK;
@@ -226,7 +295,8 @@ rlbm_status rlbm3_step(rlbm_ctx3* c, int nsteps) {
   if (nsteps < 0) return fail3(c, RLBM_EINVAL, "nsteps < 0");
   if (!c->initialised) return fail3(c, RLBM_EINVAL, "rlbm3_init has not been called");
   for (int k = 0; k < nsteps; ++k) {
-    cudaError_t e = launch_step3d(c->dtype, c->p, c->buf[c->cur], c->buf[1 - c->cur], c->stream);
+    cudaError_t e = c->fused ? launch_fused3d(c->fused, c->fp, c->buf[c->cur], c->buf[1 - c->cur], c->stream)
+                             : launch_step3d(c->dtype, c->p, c->buf[c->cur], c->buf[1 - c->cur], c->stream);
     if (e != cudaSuccess) return cuda_fail3(c, e, "step launch");
     c->cur = 1 - c->cur;
     ++c->t;
@@ -288,6 +358,7 @@ rlbm_status rlbm3_get_info(const rlbm_ctx3* c, rlbm3_info* info) {
   info->t = c->t;
   info->bytes_per_site = 2 * (size_t)c->Q * c->elem;
   info->device_bytes = c->device_bytes + c->out_cap * sizeof(double);
+  info->kernel = c->fused;
   return RLBM_OK;
 }
 

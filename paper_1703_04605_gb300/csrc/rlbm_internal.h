@@ -182,6 +182,27 @@ struct Field3Ptrs {
   const double* T;
 };
 
+// Stencil-specialised FP32 3D step (rlbm_fused3d.cu): the split arithmetic of
+// FusedParams for the unfolded stencil.  gm: as FusedParams; gf: the ten
+// per-group constants of StencilBuild3::gf3.
+struct Fused3Params {
+  int Nx, Ny, Nz;
+  long long pitch, zstride, plane;   // elements; zstride = pitch * Ny
+  float inv_tau, v0;
+  float mb, k21, cb00_1, mY, cv_r;
+  HL Rr, nr, yr;
+  HL mref[14];
+  double Rr64, mb64;
+  HL gm[6][5];
+  HL gf[6][10];
+  const double* rt64;
+  const float* rt32;
+  unsigned* err;
+};
+
+// kind 1: groups {5,12,14,17,21,26}, kind 2: {1..6}
+cudaError_t launch_fused3d(int kind, const Fused3Params& p, const void* fin, void* fout, cudaStream_t s);
+
 cudaError_t launch_step3d(rlbm_dtype dt, const Step3Params& p, const void* fin, void* fout, cudaStream_t s);
 cudaError_t launch_init3d(rlbm_dtype dt, const Step3Params& p, Field3Ptrs f, void* cur, void* prev,
                           cudaStream_t s);

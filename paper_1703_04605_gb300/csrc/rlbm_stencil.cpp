@@ -547,7 +547,26 @@ rlbm_status build_stencil3d(const rlbm_stencil* st, double m, StencilBuild3* out
     const qf len2 = (qf)group_len2(g6[k]);
     const qf gam = 1 / q_sqrt(1 - (qf)v0 * (qf)v0 * len2);
     const qf p0 = mq * gam, ps = mq * gam * (qf)v0;
-    for (const auto& v : group_orbit(g6[k])) {
+    {
+      const qf w = wq[k], Pv2 = ps * ps;
+      const qf K9 = w * Pv2 / (4 * Eq * Eq), K10 = w * Pv2 / (12 * Eq * Eq), K13 = w * Pv2 / (Eq * Eq);
+      const qf gf[10] = {w / mq,
+                         w * (p0 - mq * k21q) / (Aq * Aq),
+                         w * (p0 * p0 + cJ1 * p0 + cJ0) / (3 * Cq * Cq),
+                         -len2 * K9,
+                         len2 * K10,
+                         w * ps / (Bq * Bq),
+                         w * ps * (p0 - mq * k32q) / (Dq * Dq),
+                         K9,
+                         K10,
+                         K13};
+      for (int q = 0; q < 10; ++q) out->gf3[k][q] = (double)gf[q];
+    }
+    // lexicographic (n_x, n_y, n_z) inside a group: the order the compiled 3D
+    // stencils use (rlbm_stencils.h, unfold_stencil)
+    std::vector<std::array<int, 3>> orb = group_orbit(g6[k]);
+    std::sort(orb.begin(), orb.end());
+    for (const auto& v : orb) {
       Pop3 q;
       q.group = k;
       q.nx = v[0];

@@ -68,10 +68,16 @@ struct Pop3 {
 };
 
 struct StencilBuild3 {
-  StencilBuild sb;                // validation, v0, weights, site constants
+  StencilBuild sb;                // validation, v0, weights, site constants; sb.gm are the
+                                  // group momenta of the 3D kernels as well
   std::vector<Pop3> pops;
   double mref1[14];               // moments of the reference r_i at unit density
   int halo;                       // largest |n| component
+  // per group constants of the stencil-specialised 3D kernel (rlbm_fused3d.cu):
+  // w/m, w(P0-m k21)/A^2, w(P0^2+cJ1 P0+cJ0)/(3C^2), -|n|^2 K9, |n|^2 K10,
+  // w Pv/B^2, w Pv(P0-m k32)/D^2, K9 = w Pv^2/(4E^2), K10 = w Pv^2/(12E^2),
+  // K13 = w Pv^2/E^2
+  double gf3[6][10];
 };
 
 // Unfolded build for 3D lattices (the paper's stencil itself, Table I orbits

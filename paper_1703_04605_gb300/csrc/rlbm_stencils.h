@@ -113,6 +113,75 @@ constexpr Folded fold_stencil(int g0, int g1, int g2, int g3, int g4, int g5) {
   return F;
 }
 
+// Unfolded six-group stencil for 3D lattices: every vector of the groups'
+// orbits, group by group, inside a group by (n_x, n_y, n_z) lexicographically
+// (the host's 3D builder uses the same order).
+constexpr int kMaxUnfolded = 160;
+struct Unfolded {
+  int Q;
+  int halo;
+  int grp[kMaxUnfolded], nx[kMaxUnfolded], ny[kMaxUnfolded], nz[kMaxUnfolded];
+};
+
+constexpr Unfolded unfold_stencil(int g0, int g1, int g2, int g3, int g4, int g5) {
+  Unfolded U{};
+  const int gs[6] = {g0, g1, g2, g3, g4, g5};
+  int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  U.Q = 0;
+  U.halo = 0;
+  for (int g = 0; g < 6; ++g) {
+    const int* b = kTableI.v[gs[g] - 1];
+    int vec[48][3] = {};
+    int nvec = 0;
+    for (int p = 0; p < 6; ++p)
+      for (int s = 0; s < 8; ++s) {
+        int v[3] = {0, 0, 0};
+        for (int a = 0; a < 3; ++a) v[a] = ((s >> a) & 1 ? -1 : 1) * b[perms[p][a]];
+        bool seen = false;
+        for (int q = 0; q < nvec; ++q)
+          if (vec[q][0] == v[0] && vec[q][1] == v[1] && vec[q][2] == v[2]) seen = true;
+        if (!seen) {
+          for (int a = 0; a < 3; ++a) vec[nvec][a] = v[a];
+          ++nvec;
+        }
+      }
+    for (int i = 0; i < nvec; ++i)
+      for (int j = i + 1; j < nvec; ++j) {
+        const bool less = vec[j][0] < vec[i][0] || (vec[j][0] == vec[i][0] && vec[j][1] < vec[i][1]) ||
+                          (vec[j][0] == vec[i][0] && vec[j][1] == vec[i][1] && vec[j][2] < vec[i][2]);
+        if (less)
+          for (int a = 0; a < 3; ++a) {
+            const int t = vec[i][a];
+            vec[i][a] = vec[j][a];
+            vec[j][a] = t;
+          }
+      }
+    for (int q = 0; q < nvec; ++q) {
+      U.grp[U.Q] = g;
+      U.nx[U.Q] = vec[q][0];
+      U.ny[U.Q] = vec[q][1];
+      U.nz[U.Q] = vec[q][2];
+      for (int a = 0; a < 3; ++a) {
+        const int c = vec[q][a] < 0 ? -vec[q][a] : vec[q][a];
+        if (c > U.halo) U.halo = c;
+      }
+      ++U.Q;
+    }
+  }
+  return U;
+}
+
+// Compiled 3D stencils (group ids ascending).
+template <int G0, int G1, int G2, int G3, int G4, int G5>
+struct Stencil3Def {
+  static constexpr int groups[6] = {G0, G1, G2, G3, G4, G5};
+  static constexpr Unfolded U = unfold_stencil(G0, G1, G2, G3, G4, G5);
+  static constexpr int Q = U.Q;
+};
+
+using Stencil3M1 = Stencil3Def<5, 12, 14, 17, 21, 26>;
+using Stencil3G16 = Stencil3Def<1, 2, 3, 4, 5, 6>;
+
 // Reflection orbits of a folded stencil: the populations of one group with
 // the same |n_x|, |n_y| and n_z^2 under n_x -> -n_x and n_y -> -n_y.  kind 4:
 // quartet, members (+,+), (-,+), (+,-), (-,-); kind 2: (+a_x, 0), (-a_x, 0);

@@ -2,8 +2,9 @@
 lattices against the oracle's 3D lattice (same stencil, same v0), and
 properties that hold at any size.
 
-* FP64 parity with the oracle (1e-12) on ragged lattices, two stencils;
-* FP32 storage (generic kernel, FP32 accumulation) against the oracle;
+* FP64 parity with the oracle (1e-12) on ragged lattices, three stencils;
+* FP32 storage against the oracle: the compiled kernels (1e-5) and the
+  generic one;
 * Nz = 1 with u_z = 0 equals the folded 2D lattice of the same stencil
   (the fold of the 3D stencil is exact while U^z = 0);
 * rotation: a flow along z equals the same flow along x, transposed (the
@@ -71,25 +72,38 @@ def errors3(got, ref):
     return e
 
 
-@pytest.mark.parametrize("name,shape,steps", [("G16", (7, 8, 9), 4), ("M1", (5, 6, 9), 3)])
+@pytest.mark.parametrize("name,shape,steps", [("G16", (7, 8, 9), 4), ("M1", (5, 6, 9), 3), ("E5", (4, 5, 13), 2)])
 def test_f64_against_oracle(name, shape, steps):
-    st = {"G16": W.STENCIL_G16, "M1": W.STENCIL_M1}[name]
+    st = {"G16": W.STENCIL_G16, "M1": W.STENCIL_M1, "E5": W.STENCIL_E5}[name]
     f = smooth3(shape[2], shape[1], shape[0], seed=31)
     got, info = gpu3(st, 0.8, f, steps)
-    assert info["Q"] == {"G16": 57, "M1": 96}[name]
+    assert info["Q"] == {"G16": 57, "M1": 96, "E5": 133}[name]
     ref = oracle3(st, 0.8, f, steps)
     e = errors3(got, ref)
     assert max(e.values()) < 1e-12, e
 
 
-def test_f32_against_oracle():
-    st = W.STENCIL_G16
-    f = smooth3(9, 8, 7, seed=32)
+@pytest.mark.parametrize("name,kernel", [("G16", 2), ("M1", 1)])
+def test_f32_compiled_against_oracle(name, kernel):
+    st = {"G16": W.STENCIL_G16, "M1": W.STENCIL_M1}[name]
+    f = smooth3(11, 9, 8, seed=32)
     got, info = gpu3(st, 0.8, f, 10, dtype="f32")
-    assert info["bytes_per_site"] == 2 * 57 * 4
+    assert info["kernel"] == kernel
+    assert info["bytes_per_site"] == 2 * info["Q"] * 4
     ref = oracle3(st, 0.8, f, 10)
     e = errors3(got, ref)
-    # generic FP32 kernel: per-population FP32 constants (as the 2D generic kernel)
+    assert max(e.values()) < 1e-5, e
+
+
+def test_f32_generic_against_oracle():
+    # narrower than the M1 halo (4) in x: the generic FP32 kernel
+    st = W.STENCIL_M1
+    f = smooth3(3, 9, 8, seed=36)
+    got, info = gpu3(st, 0.8, f, 10, dtype="f32")
+    assert info["kernel"] == 0
+    ref = oracle3(st, 0.8, f, 10)
+    e = errors3(got, ref)
+    # per-population FP32 constants (as the generic 2D FP32 kernel)
     assert e["n"] < 1e-5 and e["T"] < 1e-5 and e["u"] < 1e-4, e
 
 
