@@ -198,8 +198,9 @@ typedef struct {
   long long t;
   size_t bytes_per_site;    /* 2 Q sizeof(storage)                            */
   size_t device_bytes;
-  int kernel;               /* step kernel: 0 generic; 1, 2 compiled for the
-                               stencils {5,12,14,17,21,26}, {1..6} (FP32
+  int kernel;               /* step kernel: 0 generic; 1..4 compiled for the
+                               stencils {5,12,14,17,21,26}, {1..6},
+                               {1,14,49,51,60,70}, {3,9,10,14,17,21} (FP32
                                storage, lattice at least a halo wide)         */
 } rlbm3_info;
 

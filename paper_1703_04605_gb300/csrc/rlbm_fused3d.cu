@@ -266,8 +266,12 @@ cudaError_t launch_fused3d_impl(const Fused3Params& p, const void* fin, void* fo
 }  // namespace
 
 cudaError_t launch_fused3d(int kind, const Fused3Params& p, const void* fin, void* fout, cudaStream_t s) {
-  if (kind == 1) return launch_fused3d_impl<Stencil3M1>(p, fin, fout, s);
-  return launch_fused3d_impl<Stencil3G16>(p, fin, fout, s);
+  switch (kind) {
+    case 1: return launch_fused3d_impl<Stencil3M1>(p, fin, fout, s);
+    case 2: return launch_fused3d_impl<Stencil3G16>(p, fin, fout, s);
+    case 3: return launch_fused3d_impl<Stencil3E5>(p, fin, fout, s);
+    default: return launch_fused3d_impl<Stencil3S2>(p, fin, fout, s);
+  }
 }
 
 }  // namespace rlbm

@@ -37,7 +37,8 @@ struct rlbm_ctx3 {
   size_t device_bytes = 0;
   bool initialised = false;
   Step3Params p{};
-  int fused = 0;               // 0 generic kernel; 1: {5,12,14,17,21,26}, 2: {1..6} (FP32)
+  int fused = 0;               // 0 generic kernel; 1..4: {5,12,14,17,21,26}, {1..6},
+                               // {1,14,49,51,60,70}, {3,9,10,14,17,21} (FP32)
   Fused3Params fp{};
   std::string last_error;
 };
@@ -91,6 +92,8 @@ int fused3_kind(const rlbm_ctx3* c) {
   if (c->dtype != RLBM_F32) return 0;
   if (same_order<Stencil3M1>(c)) return 1;
   if (same_order<Stencil3G16>(c)) return 2;
+  if (same_order<Stencil3E5>(c)) return 3;
+  if (same_order<Stencil3S2>(c)) return 4;
   return 0;
 }
 

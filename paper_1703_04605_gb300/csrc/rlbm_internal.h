@@ -200,7 +200,7 @@ struct Fused3Params {
   unsigned* err;
 };
 
-// kind 1: groups {5,12,14,17,21,26}, kind 2: {1..6}
+// kind 1..4: groups {5,12,14,17,21,26}, {1..6}, {1,14,49,51,60,70}, {3,9,10,14,17,21}
 cudaError_t launch_fused3d(int kind, const Fused3Params& p, const void* fin, void* fout, cudaStream_t s);
 
 cudaError_t launch_step3d(rlbm_dtype dt, const Step3Params& p, const void* fin, void* fout, cudaStream_t s);

@@ -181,6 +181,8 @@ struct Stencil3Def {
 
 using Stencil3M1 = Stencil3Def<5, 12, 14, 17, 21, 26>;
 using Stencil3G16 = Stencil3Def<1, 2, 3, 4, 5, 6>;
+using Stencil3E5 = Stencil3Def<1, 14, 49, 51, 60, 70>;
+using Stencil3S2 = Stencil3Def<3, 9, 10, 14, 17, 21>;
 
 // Reflection orbits of a folded stencil: the populations of one group with
 // the same |n_x|, |n_y| and n_z^2 under n_x -> -n_x and n_y -> -n_y.  kind 4:

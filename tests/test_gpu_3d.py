@@ -83,10 +83,10 @@ def test_f64_against_oracle(name, shape, steps):
     assert max(e.values()) < 1e-12, e
 
 
-@pytest.mark.parametrize("name,kernel", [("G16", 2), ("M1", 1)])
+@pytest.mark.parametrize("name,kernel", [("G16", 2), ("M1", 1), ("E5", 3), ("S2", 4)])
 def test_f32_compiled_against_oracle(name, kernel):
-    st = {"G16": W.STENCIL_G16, "M1": W.STENCIL_M1}[name]
-    f = smooth3(11, 9, 8, seed=32)
+    st = {"G16": W.STENCIL_G16, "M1": W.STENCIL_M1, "E5": W.STENCIL_E5, "S2": W.STENCIL_S2}[name]
+    f = smooth3(13, 13, 13, seed=32) if name == "E5" else smooth3(11, 9, 8, seed=32)
     got, info = gpu3(st, 0.8, f, 10, dtype="f32")
     assert info["kernel"] == kernel
     assert info["bytes_per_site"] == 2 * info["Q"] * 4
