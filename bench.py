@@ -478,7 +478,7 @@ def run_random3d(args):
     torch.cuda.set_device(local)
     build.build()
     st = W.STENCIL_M1
-    N = 256
+    N = 256 if args.side == N_SIDE else args.side
     f = W.random_flow3d(N)
     stream = torch.cuda.Stream()
     sites = float(N) ** 3
@@ -527,7 +527,7 @@ def run_random3d(args):
     line = {"metric": METRIC, "value": sites / (ms / 1e3) / 1e6, "unit": "MLUPS", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "random_flow3d_256: 256^3 periodic random flow (n,T = 1+0.01 g, u = 0.05 g, "
+            "config": {"workload": "random_flow3d_%d: %d^3 periodic random flow (n,T = 1+0.01 g, u = 0.05 g, " % (N, N) +
                                    "g Gaussian-smoothed width 8), m/T=1, tau=0.8, unfolded stencil "
                                    "G5,G12,G14,G17,G21,G26 (Q=96), v0=0.23342",
                        "sites": int(sites), "Q": info["Q"], "l2": "inputs larger than L2"},
@@ -551,7 +551,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64", "bf16dev"])
     ap.add_argument("--side", type=int, default=N_SIDE,
-                    help="random_flow only: time a side x side crop of the 4096^2 field (profiling of small cases)")
+                    help="random_flow: time a side x side crop of the 4096^2 field; random3d: a side^3 lattice "
+                         "instead of 256^3 (profiling of small cases)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the accuracy check and the other dtypes")
