@@ -12,7 +12,8 @@ Per site (Sec. II A, Eq. 16-20, 28-29, 49):
  4. T from the equation of state e/n = 3T + m K1(m/T)/K2(m/T) (Eq. 28) by a
     bracketed Newton iteration to round-off (Sec. II B); e/n is strictly
     increasing in T so the root is unique
- 5. f_i^eq (Eq. 16, route (i) of ``equilibrium``)
+ 5. f_i^eq (Eq. 16): route (i) of ``equilibrium`` on a second-order
+    stencil, ``third_order`` on a third-order one
  6. Anderson-Witting relaxation with weight p_i.U/(p_i^0 tau) (Eq. 49)
  7. exact streaming by the integer displacement n_i (Eq. 49-50).
 
@@ -26,6 +27,7 @@ from . import equilibrium as EQ
 from . import polynomials as P
 from . import quadrature as QD
 from . import special as S
+from . import third_order as TO
 
 
 def landau(Tmn, dim):
@@ -93,6 +95,8 @@ class Lattice:
             assert len(shape) == 3
         self.shape = tuple(shape)
         self.Q = len(self.w)
+        self.order = stencil.order
+        self.eq3 = TO.ThirdOrder(stencil, two_d) if self.order == 3 else None
         self.f = None
         self.t = 0
 
@@ -103,6 +107,8 @@ class Lattice:
         return np.stack([g, g * ux, g * uy, g * uz], axis=-1)
 
     def equilibrium(self, n, U, T):
+        if self.eq3 is not None:
+            return self.eq3.feq(self.w, n, U, T)
         return EQ.feq_route_i(self.w, self.p, n, U, T, self.consts)
 
     def init(self, n, ux, uy, T, uz=None):

@@ -14,7 +14,11 @@ vanish on both sides and p0^2 = mbar^2 + |p|^2 holds at every node, so the
 conditions reduce to the six monomials of ``special.MONOMIALS6`` -- the "6
 linearly independent components" of Sec. III D -- giving the square system
 A(v0) w = b of Eq. 52 with A[phi][k] = sum_{i in G_k} phi(p_{i,k}) and
-b[phi] = <phi> (rest-frame moment of the weight).  It is solved in 60-digit
+b[phi] = <phi> (rest-frame moment of the weight).  A third-order stencil (11
+groups) is exact for every product of two polynomials of degree <= 3, i.e.
+every monomial of degree <= 6, and the eleven monomials of
+``special.MONOMIALS11`` give the square 11 x 11 system (Sec. III D: eleven
+independent components at third order).  It is solved in 60-digit
 decimal arithmetic (the system is ill conditioned for small mbar, Sec. III D)
 and rounded to FP64 at the end.
 """
@@ -30,7 +34,7 @@ def _gamma_dec(v0, len2):
     return Decimal(1) / (Decimal(1) - v0 * v0 * Decimal(len2)).sqrt()
 
 
-def _phi_dec(name, p0, px, py):
+def _phi_dec(name, p0, px, py, pz):
     if name == "1":
         return Decimal(1)
     if name == "p0":
@@ -43,7 +47,31 @@ def _phi_dec(name, p0, px, py):
         return px ** 4
     if name == "px2py2":
         return px * px * py * py
+    if name == "p0px4":
+        return p0 * px ** 4
+    if name == "p0px2py2":
+        return p0 * px * px * py * py
+    if name == "px6":
+        return px ** 6
+    if name == "px4py2":
+        return px ** 4 * py * py
+    if name == "px2py2pz2":
+        return px * px * py * py * pz * pz
     raise KeyError(name)
+
+
+def order_of(group_ids):
+    """Expansion order fixed by the number of groups (Sec. III D): 6 -> 2, 11 -> 3."""
+    n = len(group_ids)
+    if n == 6:
+        return 2
+    if n == 11:
+        return 3
+    raise ValueError("a stencil needs 6 groups (second order) or 11 groups (third order), Sec. III D")
+
+
+def monomials_for(order):
+    return S.MONOMIALS6 if order == 2 else S.MONOMIALS11
 
 
 def _solve_dec(A, b):
@@ -67,21 +95,25 @@ def _solve_dec(A, b):
 
 
 class MomentCache:
-    """Rest-frame moments b[phi] of one mbar (they do not depend on v0)."""
+    """Rest-frame moments b[phi] of one mbar and order (they do not depend on v0)."""
 
-    def __init__(self, mbar):
+    def __init__(self, mbar, order=2):
         self.mbar = S._dec(mbar)
-        self.b = [S.rest_moment_dec(nm, self.mbar) for nm in S.MONOMIALS6]
+        self.order = order
+        self.b = [S.rest_moment_dec(nm, self.mbar) for nm in monomials_for(order)]
 
 
 def system_dec(group_ids, mbar, v0, cache=None):
-    """A(v0) and b of Eq. 52 in decimal arithmetic (rows = MONOMIALS6, cols = groups)."""
-    if len(group_ids) != 6:
-        raise ValueError("a second-order stencil needs exactly 6 groups (Sec. III D)")
-    cache = cache or MomentCache(mbar)
+    """A(v0) and b of Eq. 52 in decimal arithmetic (rows = the order's
+    monomials, cols = groups)."""
+    order = order_of(group_ids)
+    if cache is None or cache.order != order:
+        cache = MomentCache(mbar, order)
+    names = monomials_for(order)
+    K = len(group_ids)
     m = cache.mbar
     v0 = S._dec(v0)
-    A = [[Decimal(0)] * 6 for _ in range(6)]
+    A = [[Decimal(0)] * K for _ in range(K)]
     for k, gid in enumerate(group_ids):
         len2 = G.length2(gid)
         if v0 * v0 * len2 >= 1:
@@ -91,8 +123,9 @@ def system_dec(group_ids, mbar, v0, cache=None):
         for vec in G.orbit(gid):
             px = m * gam * v0 * vec[0]
             py = m * gam * v0 * vec[1]
-            for r, nm in enumerate(S.MONOMIALS6):
-                A[r][k] += _phi_dec(nm, p0, px, py)
+            pz = m * gam * v0 * vec[2]
+            for r, nm in enumerate(names):
+                A[r][k] += _phi_dec(nm, p0, px, py, pz)
     return A, list(cache.b)
 
 
@@ -111,7 +144,8 @@ def positive_window(group_ids, mbar, v_lo, v_hi, samples=4000, cache=None):
     """All maximal v0 intervals inside (v_lo, v_hi) where every w_k > 0
     (Sec. III D), located on a uniform scan and refined by bisection on the
     weight that changes sign; returns a list of (lo, hi) floats."""
-    cache = cache or MomentCache(mbar)
+    if cache is None or cache.order != order_of(group_ids):
+        cache = MomentCache(mbar, order_of(group_ids))
 
     def minw(v):
         return min(weights_dec(group_ids, mbar, Decimal(repr(float(v))), cache))
@@ -147,7 +181,8 @@ def _bisect_edge(minw, bad, good, iters=60):
 def zero_of_weight(group_ids, mbar, k, lo, hi, iters=200, cache=None):
     """v0 in (lo, hi) where the weight of the k-th listed group vanishes, by
     decimal bisection (the pruned quadratures of Sec. III D)."""
-    cache = cache or MomentCache(mbar)
+    if cache is None or cache.order != order_of(group_ids):
+        cache = MomentCache(mbar, order_of(group_ids))
     lo = S._dec(lo)
     hi = S._dec(hi)
     flo = weights_dec(group_ids, mbar, lo, cache)[k]
@@ -162,8 +197,9 @@ def zero_of_weight(group_ids, mbar, k, lo, hi, iters=200, cache=None):
 
 
 class Stencil:
-    """A second-order stencil at (mbar, v0): per-population momenta and
-    weights, unfolded (3D) or folded onto the xy plane.
+    """A stencil at (mbar, v0): per-population momenta and weights, unfolded
+    (3D) or folded onto the xy plane.  Six groups give a second-order
+    stencil, eleven a third-order one (``order``).
 
     Folding (2D lattices): the populations (n_x, n_y, +n_z) and (n_x, n_y, -n_z)
     of one group stream identically on an Nx x Ny lattice (Nz = 1) and stay
@@ -175,6 +211,7 @@ class Stencil:
 
     def __init__(self, group_ids, mbar, v0, w=None):
         self.group_ids = list(group_ids)
+        self.order = order_of(self.group_ids)
         self.mbar = float(mbar)
         self.v0 = float(v0)
         self.w_group = np.asarray(w if w is not None else weights(group_ids, mbar, v0), dtype=np.float64)
@@ -197,6 +234,21 @@ class Stencil:
             d.append(vec)
             gi.append(k)
         return np.array(w), np.array(p), np.array(d, dtype=np.int64), np.array(gi)
+
+    def population_vectors(self, two_d):
+        """(group index, n_x, n_y, n_z or |n_z|, multiplicity) per population,
+        in the order of ``populations2d`` (two_d) or ``populations3d``."""
+        if not two_d:
+            return [(k, vec[0], vec[1], vec[2], 1) for k, gid, vec, gam in self._rows]
+        seen = {}
+        order = []
+        for k, gid, vec, gam in self._rows:
+            key = (k, vec[0], vec[1], abs(vec[2]))
+            if key not in seen:
+                seen[key] = 0
+                order.append(key)
+            seen[key] += 1
+        return [key + (seen[key],) for key in order]
 
     def populations2d(self):
         """Folded populations: (w, p[Q,4] with p[:,3] = |p_z|, d[Q,2], group index, multiplicity)."""

@@ -8,7 +8,8 @@ Extended precision (python ``decimal``, 60 significant digits):
   this entire, even integrand (Trefethen & Weideman, SIAM Rev. 56 (2014)).
 * ``rest_moment_dec(name, mbar)``: <phi> = int omega(p0) phi d^3p / p0 with the
   weight omega = exp(-p0/T_R)/N_R of Eq. 36 (T_R = 1) and N_R of Eq. 41, for
-  the six monomials phi that fix a second-order quadrature (Sec. III D).
+  the six monomials phi that fix a second-order quadrature and the eleven
+  that fix a third-order one (Sec. III D).
 
 FP64: ``kv`` (scipy's Bessel K, a library routine) and the ratio
 R(zeta) = K1(zeta)/K2(zeta) used by the equation of state, Eq. 28.
@@ -91,6 +92,13 @@ def kv_dec(nu, x):
 #   1, p0, p_x^2, p0 p_x^2, p_x^4, p_x^2 p_y^2
 # <n_x^2> = 1/3, <n_x^4> = 1/5, <n_x^2 n_y^2> = 1/15 over the unit sphere.
 MONOMIALS6 = ("1", "p0", "px2", "p0px2", "px4", "px2py2")
+# Third order (Sec. III D: eleven independent conditions): exactness for every
+# product of two polynomials of degree <= 3, i.e. every on-shell monomial of
+# degree <= 6.  With p0^2 = mbar^2 + |p|^2 at every node and odd monomials
+# vanishing on both sides, five more conditions join the six:
+#   p0 p_x^4, p0 p_x^2 p_y^2, p_x^6, p_x^4 p_y^2, p_x^2 p_y^2 p_z^2
+# (<n_x^6> = 1/7, <n_x^4 n_y^2> = 1/35, <n_x^2 n_y^2 n_z^2> = 1/105).
+MONOMIALS11 = MONOMIALS6 + ("p0px4", "p0px2py2", "px6", "px4py2", "px2py2pz2")
 _MONO_SPEC = {
     "1": (0, 0, Decimal(1)),
     "p0": (1, 0, Decimal(1)),
@@ -98,6 +106,11 @@ _MONO_SPEC = {
     "p0px2": (1, 2, Decimal(1) / Decimal(3)),
     "px4": (0, 4, Decimal(1) / Decimal(5)),
     "px2py2": (0, 4, Decimal(1) / Decimal(15)),
+    "p0px4": (1, 4, Decimal(1) / Decimal(5)),
+    "p0px2py2": (1, 4, Decimal(1) / Decimal(15)),
+    "px6": (0, 6, Decimal(1) / Decimal(7)),
+    "px4py2": (0, 6, Decimal(1) / Decimal(35)),
+    "px2py2pz2": (0, 6, Decimal(1) / Decimal(105)),
 }
 
 

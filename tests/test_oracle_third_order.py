@@ -1,0 +1,262 @@
+"""Pins of the oracle's third-order scheme (Sec. III A-D at order 3).
+
+* rest-frame moments of the eleven conditions against closed forms in K_nu
+  (scipy, an independent route from the oracle's rapidity trapezoid);
+* a third-order stencil integrates every monomial of degree <= 6 exactly
+  (brute force over all of them, odd ones included), not only the eleven
+  that fixed its weights;
+* the rank-3 Maxwell-Juttner moment against numerical integration, at rest
+  and in a moving frame;
+* the discrete third-order equilibrium reproduces N^a, T^ab and T^abc of the
+  continuum (Eq. 4-6) for random states, folded and unfolded;
+* special cases: the rest state at T_R gives the weights themselves; the
+  folded equilibrium is the unfolded one summed over +-n_z; the J^(k) are
+  orthonormal; a lattice conserves N^0 and T^{0 nu}.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.integrate as si
+import scipy.special as sps
+
+from conftest import read_golden
+from oracle import groups as G
+from oracle import lattice as OL
+from oracle import quadrature as QD
+from oracle import special as S
+from oracle import third_order as TO
+
+S3 = [1, 2, 5, 6, 7, 9, 10, 11, 12, 13, 15]   # third order, positive at mbar = 5
+M3 = 5.0
+
+
+@pytest.fixture(scope="module")
+def window():
+    win = QD.positive_window(S3, M3, 0.27, 0.2765, samples=200)
+    assert len(win) == 1
+    return win[0]
+
+
+@pytest.fixture(scope="module")
+def stencil(window):
+    return QD.Stencil(S3, M3, 0.5 * (window[0] + window[1]))
+
+
+def _p_moment(a, b, m):
+    """<p0^a |p|^(2b)> of the weight of Eq. 36 (T_R = 1), a in {0, 1}, from
+    int_0^inf e^{-m cosh x} sinh^(2nu) x dx = Gamma(nu + 1/2) (2/m)^nu K_nu(m)/sqrt(pi)
+    and d/dm [m^-nu K_nu(m)] = -m^-nu K_{nu+1}(m) (one more power of cosh)."""
+    base = (2 * m) ** b * math.gamma(b + 1.5) / math.gamma(1.5)
+    if a == 0:
+        return base * sps.kv(b + 1, m) / sps.kv(1, m)
+    return m * base * sps.kv(b + 2, m) / sps.kv(1, m)
+
+
+def _sphere_mean(i, j, l):
+    """<n_x^i n_y^j n_z^l> over the unit sphere."""
+    if i % 2 or j % 2 or l % 2:
+        return 0.0
+
+    def df(k):   # (k - 1)!!
+        return math.prod(range(k - 1, 0, -2)) if k > 1 else 1
+
+    return df(i) * df(j) * df(l) / df(i + j + l + 2)
+
+
+def _monomial_mean(a, i, j, l, m):
+    """<p0^a p_x^i p_y^j p_z^l> for any a, reducing p0^2 = m^2 + |p|^2."""
+    ang = _sphere_mean(i, j, l)
+    if ang == 0.0:
+        return 0.0
+    b0 = (i + j + l) // 2
+    s, odd = divmod(a, 2)
+    tot = 0.0
+    for r in range(s + 1):
+        tot += math.comb(s, r) * m ** (2 * (s - r)) * _p_moment(odd, b0 + r, m)
+    return ang * tot
+
+
+@pytest.mark.parametrize("m", [1.5, 5.0, 10.0])
+def test_rest_moments_closed_form(m):
+    spec = {"1": (0, 0, 0, 0), "p0": (1, 0, 0, 0), "px2": (0, 2, 0, 0), "p0px2": (1, 2, 0, 0),
+            "px4": (0, 4, 0, 0), "px2py2": (0, 2, 2, 0), "p0px4": (1, 4, 0, 0),
+            "p0px2py2": (1, 2, 2, 0), "px6": (0, 6, 0, 0), "px4py2": (0, 4, 2, 0),
+            "px2py2pz2": (0, 2, 2, 2)}
+    assert tuple(spec) == S.MONOMIALS11
+    for name, e in spec.items():
+        got = float(S.rest_moment_dec(name, m))
+        ref = _monomial_mean(*e, m)
+        assert abs(got / ref - 1) < 1e-13, (name, got, ref)
+
+
+def test_window_and_weights(window, stencil):
+    lo, hi = window
+    assert 0.2738 < lo < 0.2740 and 0.2748 < hi < 0.2750
+    assert np.all(stencil.w_group > 0)
+    assert stencil.order == 3
+    w, p, d, gi, mult = stencil.populations2d()
+    assert stencil.Q3 == 159 and len(w) == 100
+
+
+def test_exact_for_every_monomial_up_to_degree_6(stencil):
+    w, p, _, _ = stencil.populations3d()
+    count = 0
+    for a in range(7):
+        for i in range(7 - a):
+            for j in range(7 - a - i):
+                for l in range(7 - a - i - j):
+                    disc = np.sum(w * p[:, 0] ** a * p[:, 1] ** i * p[:, 2] ** j * p[:, 3] ** l)
+                    ref = _monomial_mean(a, i, j, l, M3)
+                    scale = np.sum(w * np.abs(p[:, 0] ** a * p[:, 1] ** i * p[:, 2] ** j * p[:, 3] ** l))
+                    assert abs(disc - ref) < 1e-12 * scale, ((a, i, j, l), disc, ref)
+                    count += 1
+    assert count == 210
+    # degree 7 is not integrated exactly (the stencil is third order, not higher)
+    disc = np.sum(w * p[:, 0] * p[:, 1] ** 6)
+    assert abs(disc / _monomial_mean(1, 6, 0, 0, M3) - 1) > 1e-8
+
+
+def test_printed_third_order_quadratures_have_negative_weights():
+    gold = read_golden("quadratures_third_order_m5.txt")
+    m = float(gold["mbar"])
+    for q in "CD":
+        gids = [int(g) for g in gold[q + "_groups"].split(",")]
+        w = QD.weights(gids, m, gold[q + "_v0"])
+        assert np.min(w) < 0, q
+        # the eleven conditions themselves are met
+        st = QD.Stencil(gids, m, gold[q + "_v0"], w=w)
+        wp, p, _, _ = st.populations3d()
+        for e in [(0, 0, 0, 0), (1, 2, 0, 0), (0, 6, 0, 0), (0, 2, 2, 2)]:
+            disc = np.sum(wp * p[:, 0] ** e[0] * p[:, 1] ** e[1] * p[:, 2] ** e[2] * p[:, 3] ** e[3])
+            assert abs(disc / _monomial_mean(*e, m) - 1) < 1e-10
+
+
+def _mj_numeric(idx, U, T, m):
+    """int f p^idx d^3p/p0 per unit density for f ~ exp(-p.U/T), by nested
+    quadrature in the lab frame (|p|, cos theta); U along x."""
+    g, ux = U[0], U[1]
+
+    def integrand(c, q, poly):
+        E = math.sqrt(m * m + q * q)
+        px = q * c
+        s = math.sqrt(max(0.0, 1 - c * c))
+        comps = {0: E, 1: px, 2: q * s / math.sqrt(2), 3: q * s / math.sqrt(2)}
+        val = 1.0
+        for k in poly:
+            val *= comps[k]
+        return val * math.exp(-(E * g - px * ux) / T) * q * q / E
+
+    def moment(poly):
+        # the azimuthal average of py^2 (or pz^2) is q^2 s^2 / 2, of py or py pz zero
+        return si.dblquad(lambda c, q: integrand(c, q, poly), 0, 60 * T + 10, -1, 1,
+                          epsabs=0, epsrel=1e-12)[0]
+
+    return moment(idx) / moment((0,)) * g   # N^0 = n U^0
+
+
+@pytest.mark.filterwarnings("ignore::scipy.integrate.IntegrationWarning")
+@pytest.mark.parametrize("T,u", [(1.0, 0.0), (0.7, 0.0), (1.3, 0.3)])
+def test_rank3_moment_against_integration(T, u):
+    g = 1 / math.sqrt(1 - u * u)
+    U = np.array([g, g * u, 0.0, 0.0])
+    for idx in [(0, 0, 0), (0, 1, 1), (1, 1, 1), (0, 0, 1), (0, 2, 2), (1, 2, 2), (0, 1), (1, 1), (2, 2), ()]:
+        got = float(TO.mj_moment(idx, U, np.array(T), M3))
+        ref = _mj_numeric(idx, U, T, M3)
+        assert abs(got - ref) < 1e-9 * max(1.0, abs(ref)), (idx, got, ref)
+
+
+def _random_states(rng, k, uz=False):
+    u = rng.uniform(-0.3, 0.3, (k, 3))
+    if not uz:
+        u[:, 2] = 0
+    g = 1 / np.sqrt(1 - np.sum(u * u, axis=1))
+    U = np.concatenate([g[:, None], g[:, None] * u], axis=1)
+    return rng.uniform(0.5, 2.0, k), U, rng.uniform(0.6, 1.6, k)
+
+
+@pytest.mark.parametrize("two_d", [True, False])
+def test_feq_reproduces_moments_to_rank_3(stencil, two_d):
+    to = TO.ThirdOrder(stencil, two_d)
+    if two_d:
+        w, p, _, _, _ = stencil.populations2d()
+    else:
+        w, p, _, _ = stencil.populations3d()
+    rng = np.random.default_rng(3)
+    n, U, T = _random_states(rng, 6, uz=not two_d)
+    f = to.feq(w, n, U, T)                     # [Q, 6]
+    idxs = [()]
+    for r in (1, 2, 3):
+        for idx in np.ndindex(*(4,) * r):
+            if list(idx) == sorted(idx):
+                if two_d and sum(1 for c in idx if c == 3) % 2:
+                    continue
+                idxs.append(tuple(idx))
+    assert len(idxs) == (1 + 4 + 10 + 20 if not two_d else 1 + 3 + 7 + 13)
+    for idx in idxs:
+        phi = np.prod([p[:, c] for c in idx], axis=0) if idx else np.ones(len(w))
+        disc = phi @ f
+        ref = n * TO.mj_moment(idx, U, T, M3)
+        scale = n * (np.abs(phi) @ np.abs(f / n))
+        assert np.all(np.abs(disc - ref) < 1e-13 * scale), (idx, disc, ref)
+
+
+def test_rest_state_is_the_weight(stencil):
+    # At rest and T = T_R, f^eq = n omega K1/(mbar K2)(mbar): Eq. 3 normalised
+    # by Eq. 44 against the weight normalised by Eq. 41.
+    to = TO.ThirdOrder(stencil, True)
+    w, _, _, _, _ = stencil.populations2d()
+    f = to.feq(w, np.array(1.0), np.array([1.0, 0, 0, 0]), np.array(1.0))
+    scale = sps.kv(1, M3) / (M3 * sps.kv(2, M3))
+    err = np.abs(f - w * scale)
+    # relative 1e-13 except where w_i is tiny (G13 has w ~ 1e-9 here): there
+    # the bound is absolute, |J^(k)(p_i)| <= 1/sqrt(w_i) amplifying round-off
+    assert np.all(err < 1e-13 * w * scale + 1e-18), np.max(err / (w * scale))
+
+
+def test_fold_equals_unfolded(stencil):
+    to2 = TO.ThirdOrder(stencil, True)
+    to3 = TO.ThirdOrder(stencil, False)
+    w2, _, _, _, _ = stencil.populations2d()
+    w3, _, _, _ = stencil.populations3d()
+    rng = np.random.default_rng(4)
+    n, U, T = _random_states(rng, 3)
+    f2 = to2.feq(w2, n, U, T)
+    f3 = to3.feq(w3, n, U, T)
+    rows2 = stencil.population_vectors(True)
+    rows3 = stencil.population_vectors(False)
+    pos = {r[:4]: q for q, r in enumerate(rows2)}
+    acc = np.zeros_like(f2)
+    for q, (k, nx, ny, nz, _) in enumerate(rows3):
+        acc[pos[(k, nx, ny, abs(nz))]] += f3[q]
+    assert np.max(np.abs(acc - f2)) < 1e-15 * np.max(np.abs(f2)) * 50
+
+
+def test_polynomials_orthonormal(stencil):
+    for two_d in (True, False):
+        to = TO.ThirdOrder(stencil, two_d)
+        w = stencil.populations2d()[0] if two_d else stencil.populations3d()[0]
+        assert to.K == (20 if two_d else 30)
+        gram = np.einsum("i,ik,il->kl", w, to.J, to.J)
+        assert np.max(np.abs(gram - np.eye(to.K))) < 1e-12
+        assert np.allclose(to.J[:, 0], 1.0, atol=1e-14)
+
+
+def test_lattice_conserves_and_rest_is_stationary(stencil):
+    lat = OL.Lattice(stencil, 0.8, (6, 7))
+    rng = np.random.default_rng(5)
+    shp = (6, 7)
+    lat.init(1 + 0.05 * rng.standard_normal(shp), 0.05 * rng.standard_normal(shp),
+             0.05 * rng.standard_normal(shp), 1 + 0.05 * rng.standard_normal(shp))
+    N0, T0 = lat.moments()
+    lat.step(3)
+    N1, T1 = lat.moments()
+    assert abs(N1[..., 0].sum() / N0[..., 0].sum() - 1) < 1e-13
+    for a in range(3):
+        assert abs(T1[..., 0, a].sum() - T0[..., 0, a].sum()) < 1e-13 * T0[..., 0, 0].sum()
+    rest = OL.Lattice(stencil, 0.8, (3, 4))
+    ones = np.ones((3, 4))
+    rest.init(ones, 0 * ones, 0 * ones, ones)
+    f0 = rest.f.copy()
+    rest.step(2)
+    assert np.max(np.abs(rest.f - f0)) < 1e-15
