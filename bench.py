@@ -167,6 +167,41 @@ def cpu_baseline3d(seconds=10.0, side=12, procs=None):
                 len(res), side, min(r["steps"] for r in res), max(r["steps"] for r in res))}
 
 
+def cpu_baseline_o3(seconds=10.0, side=24, procs=None):
+    """The FP64 oracle's third-order lattice on the host cores: one process
+    per core, each advancing its own side^2 lattice of the random-flow recipe
+    with the third-order stencil (same m, tau) for about `seconds` of CPU time."""
+    procs = procs or os.cpu_count() or 1
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = (
+        "import sys, time, json; sys.path.insert(0, %r)\n"
+        "from paper_1703_04605_gb300 import workloads as W\n"
+        "from oracle import lattice as L\n"
+        "f = W.random_flow(%d)\n"
+        "st = W.STENCIL_O3\n"
+        "lat = L.make_lattice(st['groups'], st['m'], st['v0'], %r, (%d, %d))\n"
+        "lat.init(f['n'], f['ux'], f['uy'], f['T'])\n"
+        "t0 = time.process_time(); w0 = time.time(); k = 0\n"
+        "while time.process_time() - t0 < %r:\n"
+        "    lat.step(1); k += 1\n"
+        "print(json.dumps({'steps': k, 'seconds': time.time() - w0}))\n"
+    ) % (ROOT, side, TAU, side, side, seconds)
+    ps = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                           text=True, env=env) for _ in range(procs)]
+    res = []
+    for p in ps:
+        out, _ = p.communicate()
+        if p.returncode == 0:
+            res.append(json.loads(out.strip().splitlines()[-1]))
+    if not res:
+        return {"value": None, "unit": "MLUPS", "cores": procs, "kind": "oracle", "sample": "failed"}
+    return {"value": sum(side ** 2 * r["steps"] / r["seconds"] for r in res) / 1e6, "unit": "MLUPS",
+            "cores": len(res), "kind": "oracle",
+            "sample": "%d processes x one %d^2 lattice of the random-flow recipe, third-order stencil, "
+                      "%d-%d steps each, 1 thread each" % (
+                          len(res), side, min(r["steps"] for r in res), max(r["steps"] for r in res))}
+
+
 def kernel_name(dtype, variant):
     stencil = {1: "5,12,14,17,21,26", 2: "1,2,3,4,5,6", 3: "1,14,49,51,60,70", 4: "3,9,10,14,17,21"}.get(variant)
     if dtype == "f64":
@@ -544,6 +579,93 @@ def run_random3d(args):
     emit(line, rank)
 
 
+def run_third_order(args):
+    """Third order: the random-flow recipe on a 4096^2 lattice (--side for a
+    smaller one) at m/T_R = 5 with the eleven-group stencil
+    G1,G2,G5,G6,G7,G9,G10,G11,G12,G13,G15 (Q = 100 folded), tau = 0.8, FP32
+    storage; FP64 timed on fewer steps; FP32 error against the FP64 path after
+    the same steps; the oracle's third-order lattice on the host cores."""
+    import torch
+    from paper_1703_04605_gb300 import Lattice, build, workloads as W
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    build.build()
+
+    def barrier():
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    st = W.STENCIL_O3
+    N = args.side
+    f = W.random_flow(N)
+    stream = torch.cuda.Stream()
+    sites = float(N) ** 2
+    peak, peak_kind = _peaks()
+
+    def run(dtype, steps, clk=None):
+        lat = Lattice(st["groups"], st["m"], TAU, N, N, dtype=dtype, v0=st["v0"], stream=stream.cuda_stream)
+        lat.init(f["n"], f["ux"], f["uy"], f["T"])
+        lat.step(args.warmup)
+        lat.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        barrier()
+        if clk:
+            clk.__enter__()
+        e0.record(stream)
+        lat.step(steps)
+        e1.record(stream)
+        stream.synchronize()
+        if clk:
+            clk.__exit__(None, None, None)
+        barrier()
+        lat.sync()
+        info = lat.info()
+        mom = lat.moments()
+        lat.close()
+        return reduce_max(e0.elapsed_time(e1) / steps, pg, "cuda:%d" % local), info, mom
+
+    clk = ClockSampler(local)
+    ms, info, m32 = run("f32", args.steps, clk)
+    k64 = max(5, args.steps // 10)
+    ms64, info64, _ = run("f64", k64)
+    err = None
+    if not args.no_extra:
+        with Lattice(st["groups"], st["m"], TAU, N, N, dtype="f64", v0=st["v0"], stream=stream.cuda_stream) as ref:
+            ref.init(f["n"], f["ux"], f["uy"], f["T"])
+            ref.step(args.warmup + args.steps)
+            m64 = ref.moments()
+        umax = max(np.abs(m64[k]).max() for k in ("ux", "uy"))
+        err = {"n": float(np.max(np.abs(m32["n"] / m64["n"] - 1))),
+               "T": float(np.max(np.abs(m32["T"] / m64["T"] - 1))),
+               "u": float(max(np.abs(m32[k] - m64[k]).max() for k in ("ux", "uy")) / umax),
+               "steps": args.warmup + args.steps, "against": "FP64 third-order path (parity-tested vs the oracle)"}
+    achieved = info["bytes_per_site"] * sites / (ms / 1e3) / 1e9
+    line = {"metric": METRIC, "value": ws * sites / (ms / 1e3) / 1e6, "unit": "MLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "random_flow_o3_%d: %d^2 periodic random flow (n,T = 1+0.01 g, u = 0.05 g, " % (N, N) +
+                                   "g Gaussian-smoothed width 8), m/T_R=5, tau=0.8, third-order stencil "
+                                   "G1,G2,G5,G6,G7,G9,G10,G11,G12,G13,G15 (Q=100 folded), v0=0.27438",
+                       "sites": int(sites), "Q": info["Q"], "order": info["order"], "l2": "inputs larger than L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                         "kernel": "step_o3_kernel<float>", "bytes_per_site": info["bytes_per_site"]},
+            "f64": {"MLUPS": sites / (ms64 / 1e3) / 1e6, "ms_per_step": ms64, "steps": k64,
+                    "frac_hbm": info64["bytes_per_site"] * sites / (ms64 / 1e3) / 1e9 / peak},
+            "error_vs_f64": err, "gpu_launches": args.steps, "clocks": clk.summary()}
+    if not args.no_cpu_baseline and rank == 0:
+        line["cpu_baseline"] = cpu_baseline_o3()
+    emit(line, rank)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -558,7 +680,7 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the accuracy check and the other dtypes")
     ap.add_argument("--check-f64", action="store_true",
                     help="batch only: compare every lattice with the FP64 path after the run (untimed, minutes)")
-    ap.add_argument("--workload", default="random_flow", choices=["random_flow", "batch", "blast", "random3d"],
+    ap.add_argument("--workload", default="random_flow", choices=["random_flow", "batch", "blast", "random3d", "third_order"],
                     help="random_flow: the headline 4096^2 lattice; batch: 256 independent lattices; "
                          "blast: the 8192^2 near-massless blast in BF16-deviation storage; "
                          "random3d: a 256^3 lattice with the unfolded stencil")
@@ -571,6 +693,8 @@ def main():
         return run_batch(args)
     if args.workload == "blast":
         return run_blast(args)
+    if args.workload == "third_order":
+        return run_third_order(args)
     if args.workload == "random3d":
         return run_random3d(args)
 

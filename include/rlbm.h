@@ -13,11 +13,13 @@
  * (Eq. 4-5, 18), e and U solve the Landau-frame eigenproblem T^ab U_b = e U^a
  * (Eq. 20), n = U_a N^a (Eq. 19), T solves e/n = 3T + m K1(m/T)/K2(m/T)
  * (Eq. 28), and f_i^eq = n w_i sum_k b^(k)(U, T) J^(k)(p_i) is the
- * second-order expansion (Eq. 16, App. A and B).
+ * second-order expansion (Eq. 16, App. A and B) -- or, on an eleven-group
+ * stencil, the third-order one (polynomials of degree <= 3, Sec. III A-D).
  *
  * Units: c = k_B = T_R = 1 (so mbar = m), lattice spacing 1, one time step 1.
  * Metric diag(1,-1,-1,-1).  The velocity set is a second-order stencil of six
- * groups of Table I (App. C) with common velocity parameter v0 (Eq. 48),
+ * groups (or a third-order one of eleven) of Table I (App. C) with common
+ * velocity parameter v0 (Eq. 48),
  * folded onto the xy plane: the +-n_z members of a group merge into one
  * population of doubled weight, which reproduces the 3D model on an
  * Nx x Ny x 1 lattice exactly while U^z = 0.
@@ -63,10 +65,15 @@ typedef enum {
  * per-site FP32 macroscopic fields used to rebuild f_i^eq. */
 typedef enum { RLBM_F64 = 0, RLBM_F32 = 1, RLBM_BF16_DEV = 2 } rlbm_dtype;
 
-/* A second-order stencil (Sec. III C-D): exactly six distinct groups of
- * Table I (ids 1..84) and v0.  v0 > 0 is used as given (it must make every
- * weight positive and v0 ||n_k|| < 1); v0 == 0 selects the centre of the
- * widest interval of v0 where all six weights are positive (Sec. III D). */
+/* A stencil (Sec. III C-D): six distinct groups of Table I (ids 1..84) for
+ * the second-order scheme, or eleven for the third-order one, and v0.  v0 > 0
+ * is used as given (it must make every weight positive and v0 ||n_k|| < 1);
+ * v0 == 0 selects the centre of the widest interval of v0 where all weights
+ * are positive (Sec. III D).  Third-order contexts take FP64 or FP32 storage
+ * (ENOTSUP for BF16_DEV), are not accepted by rlbm_batch_step, and their
+ * equilibrium is the unique w_i times a polynomial of degree <= 3 in p_i
+ * whose moments up to rank 3 (N^a, T^ab, T^abc, Eq. 4-6) equal those of the
+ * Maxwell-Juttner distribution. */
 typedef struct {
   int ngroups;
   const int* groups;
@@ -80,7 +87,8 @@ typedef struct {
   int halo;         /* largest |n_x| or |n_y| of the stencil                */
   rlbm_dtype dtype;
   double m, tau, v0;
-  double w_group[6];        /* weights of the six groups (Eq. 47/52)         */
+  double w_group[11];       /* weights of the groups (Eq. 47/52): six, or
+                               eleven for a third-order stencil             */
   long long t;              /* current time step                             */
   size_t bytes_per_site;    /* populations read + written per site update:
                                2 Q sizeof(storage)                           */
@@ -90,6 +98,7 @@ typedef struct {
                                from the parameter block), 1..3 compiled for the
                                stencils {5,12,14,17,21,26}, {1..6},
                                {1,14,49,51,60,70} (FP32 storage)              */
+  int order;                /* expansion order of f^eq: 2 or 3               */
 } rlbm_info;
 
 /* Create a lattice context.
@@ -261,14 +270,16 @@ rlbm_status rlbm_moments_noalloc(const int* groups, int ngroups, double m, doubl
 
 /* ---- host-only helpers (no device needed) ---------------------------- */
 
-/* Weights of the six groups at (m, v0) from Eq. 52, solved in binary128 and
- * rounded to FP64.  Returns ENOQUAD if the system is singular; the weights
- * are returned whatever their sign. */
+/* Weights of the groups at (m, v0) from Eq. 52 (ngroups = 6: the six
+ * second-order conditions; 11: the eleven third-order ones), solved in
+ * binary128 and rounded to FP64 into w_out[ngroups].  Returns ENOQUAD if the
+ * system is singular; the weights are returned whatever their sign. */
 rlbm_status rlbm_quadrature_weights(const int* groups, int ngroups, double m, double v0,
                                     double* w_out);
 
-/* The widest v0 interval (lo, hi) in which all six weights are positive, and
- * its count of disjoint positive intervals; ENOQUAD if there is none. */
+/* The widest v0 interval (lo, hi) in which all weights (6 or 11 groups) are
+ * positive, and the count of disjoint positive intervals; ENOQUAD if there is
+ * none. */
 rlbm_status rlbm_quadrature_window(const int* groups, int ngroups, double m, double* lo,
                                    double* hi, int* nwindows);
 

@@ -35,8 +35,9 @@ class Stencil(C.Structure):
 class Info(C.Structure):
     _fields_ = [("Nx", C.c_int), ("Ny", C.c_int), ("Q", C.c_int), ("halo", C.c_int),
                 ("dtype", C.c_int), ("m", C.c_double), ("tau", C.c_double), ("v0", C.c_double),
-                ("w_group", C.c_double * 6), ("t", C.c_longlong), ("bytes_per_site", C.c_size_t),
-                ("extra_bytes_per_site", C.c_size_t), ("device_bytes", C.c_size_t), ("kernel", C.c_int)]
+                ("w_group", C.c_double * 11), ("t", C.c_longlong), ("bytes_per_site", C.c_size_t),
+                ("extra_bytes_per_site", C.c_size_t), ("device_bytes", C.c_size_t), ("kernel", C.c_int),
+                ("order", C.c_int)]
 
 
 class Info3(C.Structure):
@@ -124,7 +125,7 @@ def int_array(values):
 
 
 def quadrature_weights(groups, m, v0):
-    out = (C.c_double * 6)()
+    out = (C.c_double * len(groups))()
     g = int_array(groups)
     check(load().rlbm_quadrature_weights(g, len(groups), float(m), float(v0), out))
     return list(out)

@@ -42,6 +42,14 @@ struct rlbm_ctx {
   std::unique_ptr<StepParams<float>> p32;
   int fused = 0;                 // 1: M1, 2: G1..G6, 3: E5, 4: S2; 0: generic kernel
   std::unique_ptr<FusedParams> fp;
+  // third-order stencils (eleven groups)
+  int order = 2;
+  std::unique_ptr<StencilBuildO3> sb3;
+  std::unique_ptr<O3Params> o3;
+  int* d_shift = nullptr;
+  long long* d_off = nullptr;
+  double* d_tab64 = nullptr;
+  float* d_tab32 = nullptr;
   std::string last_error;
 };
 
@@ -64,7 +72,8 @@ static void release(rlbm_ctx* c) {
   if (!c) return;
   if (c->buf[0]) cudaStreamSynchronize(c->stream);
   for (void* p : {c->buf[0], c->buf[1], c->coef[0], c->coef[1], (void*)c->d_err, (void*)c->d_rt64, (void*)c->d_rt32,
-                  (void*)c->d_fields, (void*)c->d_out})
+                  (void*)c->d_fields, (void*)c->d_out, (void*)c->d_shift, (void*)c->d_off, (void*)c->d_tab64,
+                  (void*)c->d_tab32})
     if (p) cudaFree(p);
 }
 
@@ -158,6 +167,11 @@ static void fill_fused(rlbm_ctx* c, double nref) {
 // Reference density of the FP32 deviation storage (see StepParams).
 static void set_reference(rlbm_ctx* c, double nref) {
   if (c->dtype == RLBM_F64) return;
+  if (c->order == 3) {
+    c->o3->nref = nref;
+    for (int k = 0; k < 9; ++k) c->o3->mref[k] = nref * c->sb3->mref1[k];
+    return;
+  }
   for (StepParams<double>* p : {c->p64.get()}) {
     p->nref = nref;
     p->b0ref = nref * c->sb.b0ref1;
@@ -188,6 +202,109 @@ static rlbm_status check_device_error(rlbm_ctx* c) {
   return RLBM_OK;
 }
 
+// Context of a third-order (eleven-group) stencil: FP64 or FP32 storage,
+// generic kernels over a device table (rlbm_kernels_o3.cu).
+static rlbm_status create_o3(const rlbm_stencil* st, double m, double tau, int Nx, int Ny, rlbm_dtype dtype,
+                             void* cuda_stream, rlbm_ctx** out) {
+  if (dtype == RLBM_BF16_DEV)
+    return fail(nullptr, RLBM_ENOTSUP, "third-order stencils support FP64 and FP32 storage only");
+  std::unique_ptr<rlbm_ctx> c(new (std::nothrow) rlbm_ctx);
+  if (!c) return fail(nullptr, RLBM_ENOMEM, "host allocation failed");
+  c->sb3.reset(new StencilBuildO3);
+  std::string err;
+  rlbm_status s = build_stencil_o3(st, m, c->sb3.get(), &err);
+  if (s != RLBM_OK) return fail(nullptr, s, err);
+  const StencilBuildO3& sb = *c->sb3;
+  c->order = 3;
+  c->Nx = Nx;
+  c->Ny = Ny;
+  c->dtype = dtype;
+  c->m = m;
+  c->tau = tau;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->Q = (int)sb.pops.size();
+  c->elem = (dtype == RLBM_F64) ? sizeof(double) : sizeof(float);
+  c->pitch = ((long long)Nx + 31) / 32 * 32;
+  c->plane = c->pitch * Ny;
+  c->sb.halo = sb.halo;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) return fail(nullptr, RLBM_ECUDA, "no CUDA device available");
+  const int Q = c->Q;
+  const size_t fbytes = (size_t)Q * (size_t)c->plane * c->elem;
+  for (int b = 0; b < 2; ++b) {
+    e = cudaMalloc(&c->buf[b], fbytes);
+    if (e != cudaSuccess) {
+      release(c.get());
+      return fail(nullptr, RLBM_ENOMEM, "population buffers: " + std::string(cudaGetErrorString(e)));
+    }
+  }
+  const auto& t64 = ratio_table64();
+  const auto& t32 = ratio_table32();
+  const size_t nsite = (size_t)Nx * Ny;
+  const size_t tbytes = (size_t)Q * kRowO3;
+  bool ok = cudaMalloc(&c->d_err, sizeof(unsigned)) == cudaSuccess &&
+            cudaMalloc(&c->d_rt64, t64.size() * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->d_rt32, t32.size() * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&c->d_fields, 4 * nsite * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->d_shift, 2 * Q * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&c->d_off, Q * sizeof(long long)) == cudaSuccess &&
+            cudaMalloc(&c->d_tab64, tbytes * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->d_tab32, tbytes * sizeof(float)) == cudaSuccess;
+  if (!ok) {
+    release(c.get());
+    return fail(nullptr, RLBM_ENOMEM, "device allocation failed");
+  }
+  c->device_bytes = 2 * fbytes + sizeof(unsigned) + t64.size() * 8 + t32.size() * 4 + 4 * nsite * 8 +
+                    2 * Q * sizeof(int) + Q * sizeof(long long) + tbytes * 12;
+  std::vector<int> shift(2 * Q);
+  std::vector<long long> off(Q);
+  std::vector<double> tab64(tbytes);
+  std::vector<float> tab32(tbytes);
+  for (int i = 0; i < Q; ++i) {
+    const FoldedPop& fp = sb.pops[i];
+    shift[i] = ((fp.nx % Nx) + Nx) % Nx;
+    shift[Q + i] = ((fp.ny % Ny) + Ny) % Ny;
+    off[i] = -((long long)fp.ny * c->pitch + fp.nx);
+    for (int k = 0; k < kRowO3; ++k) {
+      tab64[(size_t)i * kRowO3 + k] = sb.rows[i][k];
+      tab32[(size_t)i * kRowO3 + k] = (float)sb.rows[i][k];
+    }
+  }
+  e = cudaMemcpy(c->d_rt64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_rt32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_shift, shift.data(), shift.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_off, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_tab64, tab64.data(), tbytes * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_tab32, tab32.data(), tbytes * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(unsigned));
+  if (e != cudaSuccess) {
+    release(c.get());
+    return fail(nullptr, RLBM_ECUDA, std::string("upload: ") + cudaGetErrorString(e));
+  }
+  c->o3.reset(new O3Params);
+  O3Params& p = *c->o3;
+  std::memset(&p, 0, sizeof p);
+  p.Nx = Nx;
+  p.Ny = Ny;
+  p.Q = Q;
+  p.halo = sb.halo;
+  p.pitch = c->pitch;
+  p.plane = c->plane;
+  p.inv_tau = 1.0 / tau;
+  p.c = sb.c;
+  p.sc = sb.sc;
+  p.rt64 = c->d_rt64;
+  p.rt32 = c->d_rt32;
+  p.shift = c->d_shift;
+  p.off = c->d_off;
+  p.tab64 = c->d_tab64;
+  p.tab32 = c->d_tab32;
+  p.err = c->d_err;
+  *out = c.release();
+  return RLBM_OK;
+}
+
 extern "C" {
 
 const char* rlbm_version(void) { return "rlbm-gb300 0.1 (sm_103a)"; }
@@ -200,6 +317,7 @@ rlbm_status rlbm_create(const rlbm_stencil* st, double m, double tau, int Nx, in
   if (!(tau > 0.5) || !std::isfinite(tau)) return fail(nullptr, RLBM_EINVAL, "tau must exceed 1/2");
   if (dtype != RLBM_F64 && dtype != RLBM_F32 && dtype != RLBM_BF16_DEV)
     return fail(nullptr, RLBM_EINVAL, "unknown dtype");
+  if (st && st->ngroups == 11) return create_o3(st, m, tau, Nx, Ny, dtype, cuda_stream, out);
   std::unique_ptr<rlbm_ctx> c(new (std::nothrow) rlbm_ctx);
   if (!c) return fail(nullptr, RLBM_ENOMEM, "host allocation failed");
   std::string err;
@@ -292,7 +410,9 @@ rlbm_status rlbm_init_device(rlbm_ctx* c, const double* n, const double* ux, con
   batch_forget(c);   // its parameters change below
   if (!c->host_init) set_reference(c, 1.0);
   cudaError_t e;
-  if (c->dtype == RLBM_BF16_DEV) {
+  if (c->order == 3) {
+    e = launch_init_o3(c->dtype, *c->o3, fp, c->buf[0], c->buf[1], c->stream);
+  } else if (c->dtype == RLBM_BF16_DEV) {
     MomentOut none{nullptr, 0};
     if (c->fused == 1) e = launch_bf16_io<StencilM1>(0, *c->fp, *c->p64, fp, c->buf[0], c->buf[1], c->coef[0], c->coef[1], none, c->stream);
     else if (c->fused == 2) e = launch_bf16_io<StencilG16>(0, *c->fp, *c->p64, fp, c->buf[0], c->buf[1], c->coef[0], c->coef[1], none, c->stream);
@@ -347,7 +467,8 @@ rlbm_status rlbm_step(rlbm_ctx* c, int nsteps) {
     const void* fin = c->buf[c->cur];
     void* fout = c->buf[1 - c->cur];
     cudaError_t e;
-    if (c->dtype == RLBM_F64) e = launch_step_f64(*c->p64, fin, fout, c->qb, c->stream);
+    if (c->order == 3) e = launch_step_o3(c->dtype, *c->o3, fin, fout, c->stream);
+    else if (c->dtype == RLBM_F64) e = launch_step_f64(*c->p64, fin, fout, c->qb, c->stream);
     else if (c->fused) {
       const bool bf = c->dtype == RLBM_BF16_DEV;
       c->fp->cin = c->coef[c->cur];
@@ -392,7 +513,9 @@ rlbm_status rlbm_moments(rlbm_ctx* c, double* out, unsigned mask) {
   }
   MomentOut mo{c->d_out, mask};
   cudaError_t e;
-  if (c->dtype == RLBM_BF16_DEV) {
+  if (c->order == 3) {
+    e = launch_moments_o3(c->dtype, *c->o3, c->buf[1 - c->cur], mo, c->stream);
+  } else if (c->dtype == RLBM_BF16_DEV) {
     FieldPtrs none{nullptr, nullptr, nullptr, nullptr};
     void* pv = c->buf[1 - c->cur];
     void* cp = c->coef[1 - c->cur];
@@ -424,8 +547,14 @@ rlbm_status rlbm_get_info(const rlbm_ctx* c, rlbm_info* info) {
   info->dtype = c->dtype;
   info->m = c->m;
   info->tau = c->tau;
-  info->v0 = c->sb.v0;
-  for (int k = 0; k < 6; ++k) info->w_group[k] = c->sb.w_group[k];
+  info->order = c->order;
+  if (c->order == 3) {
+    info->v0 = c->sb3->v0;
+    for (int k = 0; k < 11; ++k) info->w_group[k] = c->sb3->w_group[k];
+  } else {
+    info->v0 = c->sb.v0;
+    for (int k = 0; k < 6; ++k) info->w_group[k] = c->sb.w_group[k];
+  }
   info->t = c->t;
   info->bytes_per_site = 2 * (size_t)c->Q * c->elem;
   info->extra_bytes_per_site = (c->dtype == RLBM_BF16_DEV) ? 2 * 6 * 8 : 0;   // coefficients read + written
@@ -447,18 +576,18 @@ void rlbm_destroy(rlbm_ctx* c) {
 
 rlbm_status rlbm_quadrature_weights(const int* groups, int ngroups, double m, double v0,
                                     double* w_out) {
-  if (!groups || ngroups != 6 || !w_out || !(m > 0) || !(v0 > 0)) return RLBM_EINVAL;
-  for (int k = 0; k < 6; ++k)
+  if (!groups || (ngroups != 6 && ngroups != 11) || !w_out || !(m > 0) || !(v0 > 0)) return RLBM_EINVAL;
+  for (int k = 0; k < ngroups; ++k)
     if (groups[k] < 1 || groups[k] > 84) return RLBM_EINVAL;
-  return quadrature_weights(groups, m, v0, w_out) ? RLBM_OK : RLBM_ENOQUAD;
+  return quadrature_weights(groups, ngroups, m, v0, w_out) ? RLBM_OK : RLBM_ENOQUAD;
 }
 
 rlbm_status rlbm_quadrature_window(const int* groups, int ngroups, double m, double* lo, double* hi,
                                    int* nwindows) {
-  if (!groups || ngroups != 6 || !lo || !hi || !(m > 0)) return RLBM_EINVAL;
-  for (int k = 0; k < 6; ++k)
+  if (!groups || (ngroups != 6 && ngroups != 11) || !lo || !hi || !(m > 0)) return RLBM_EINVAL;
+  for (int k = 0; k < ngroups; ++k)
     if (groups[k] < 1 || groups[k] > 84) return RLBM_EINVAL;
-  const int n = quadrature_window(groups, m, lo, hi);
+  const int n = quadrature_window(groups, ngroups, m, lo, hi);
   if (nwindows) *nwindows = n;
   return n > 0 ? RLBM_OK : RLBM_ENOQUAD;
 }

@@ -142,6 +142,37 @@ struct MomentOut {
   unsigned mask;
 };
 
+// ------------------------------------------------- third-order 2D lattices
+// Eleven-group stencils folded onto the xy plane (rlbm_kernels_o3.cu); the
+// table layout is described with StencilBuildO3 (rlbm_stencil.h).  Centred
+// monomials of the equilibrium polynomial, t = p0 - c:
+//   1, t, px, py, t px, t py, px^2, py^2, px py, pz^2, t px^2, t py^2,
+//   t px py, px^3, px^2 py, px py^2, py^3, t pz^2, px pz^2, py pz^2
+constexpr int kO3Mono = 20;
+constexpr int kRowO3 = 32;
+constexpr int kMaxPopO3 = 256;
+
+struct O3Params {
+  int Nx, Ny, Q, halo;
+  long long pitch, plane;     // elements
+  double inv_tau;
+  double nref;                // FP32 storage holds d_i = f_i - nref wr_i; 0 for FP64
+  double mref[9];             // moments of nref wr_i
+  double c;                   // centring shift of t
+  SiteConsts sc;
+  const double* rt64;
+  const float* rt32;
+  const int* shift;           // [2][Q]: n_x mod Nx, n_y mod Ny
+  const long long* off;       // [Q]: -(n_y pitch + n_x), source offset of an interior site
+  const double* tab64;        // [Q][kRowO3]
+  const float* tab32;         // [Q][kRowO3] (FP32 storage)
+  unsigned* err;
+};
+
+cudaError_t launch_step_o3(rlbm_dtype dt, const O3Params& p, const void* fin, void* fout, cudaStream_t s);
+cudaError_t launch_init_o3(rlbm_dtype dt, const O3Params& p, FieldPtrs f, void* cur, void* prev, cudaStream_t s);
+cudaError_t launch_moments_o3(rlbm_dtype dt, const O3Params& p, const void* prev, MomentOut o, cudaStream_t s);
+
 // ------------------------------------------------------------ 3D lattices
 // Unfolded stencil on an Nx x Ny x Nz periodic lattice (rlbm_kernels3d.cu).
 // Per population i, one table row of kRow3 values at [i * kRow3] (16-byte

@@ -112,37 +112,41 @@ static qf bessel_ratio_q(qf x, double digits = 36.0) {
 }
 
 // Rest-frame moments <phi> = int omega phi d^3p/p0 (Eq. 36, 40-41, T_R = 1)
-// of the six monomials 1, p0, px^2, p0 px^2, px^4, px^2 py^2 (Sec. III D).
+// of the eleven monomials that fix a quadrature (Sec. III D): the first six
+// (1, p0, px^2, p0 px^2, px^4, px^2 py^2) for second order, all eleven (plus
+// p0 px^4, p0 px^2 py^2, px^6, px^4 py^2, px^2 py^2 pz^2) for third order.
 // In rapidity chi: d^3p/p0 = m^2 sinh^2 chi dchi dOmega and N_R = 4 pi m K1(m):
 //   <p0^a |p|^b * ang> = ang int e^{-m cosh} (m cosh)^a (m sinh)^(b+2) dchi / (m K1(m)),
-// with angular means 1, 1, 1/3, 1/3, 1/5, 1/15.
-static void rest_moments_q_uncached(qf m, qf out[6]);
+// with angular means 1, 1, 1/3, 1/3, 1/5, 1/15, 1/5, 1/15, 1/7, 1/35, 1/105.
+constexpr int kMom = 11;
+static void rest_moments_q_uncached(qf m, qf out[kMom]);
 
 // The moments depend on m only; the last few are kept (window searches and
 // stencil builds ask for the same m many times).
-static void rest_moments_q(qf m, qf out[6]) {
+static void rest_moments_q(qf m, qf* out, int K) {
   struct Entry {
     qf m;
-    qf v[6];
+    qf v[kMom];
   };
   static thread_local Entry cache[8];
   static thread_local int used = 0, next = 0;
   for (int i = 0; i < used; ++i)
     if (cache[i].m == m) {
-      for (int k = 0; k < 6; ++k) out[k] = cache[i].v[k];
+      for (int k = 0; k < K; ++k) out[k] = cache[i].v[k];
       return;
     }
-  rest_moments_q_uncached(m, out);
   Entry& e = cache[next];
+  rest_moments_q_uncached(m, e.v);
   e.m = m;
-  for (int k = 0; k < 6; ++k) e.v[k] = out[k];
+  for (int k = 0; k < K; ++k) out[k] = e.v[k];
   next = (next + 1) % 8;
   if (used < 8) ++used;
 }
 
-static void rest_moments_q_uncached(qf m, qf out[6]) {
+static void rest_moments_q_uncached(qf m, qf out[kMom]) {
   const qf h = trap_step<qf>((double)m, 36.0);
-  qf s[6] = {0, 0, 0, 0, 0, 0};
+  // radial integrals of (m cosh)^a (m sinh)^b: (a,b) = (0,0) (1,0) (0,2) (1,2) (0,4) (1,4) (0,6)
+  qf s[7] = {0, 0, 0, 0, 0, 0, 0};
   const qf tiny = (qf)1e-38;
   for (long j = 0;; ++j) {
     const qf t = h * (qf)j;
@@ -156,90 +160,104 @@ static void rest_moments_q_uncached(qf m, qf out[6]) {
     s[2] += base * p2;
     s[3] += base * p0 * p2;
     s[4] += base * p2 * p2;
-    s[5] += base * p2 * p2;
-    if (j > 4 && base * p2 * p2 * p0 < tiny * s[4] && m * (ch - 1) > (qf)5) break;
+    s[5] += base * p0 * p2 * p2;
+    s[6] += base * p2 * p2 * p2;
+    if (j > 4 && base * p2 * p2 * p2 * p0 < tiny * s[6] && m * (ch - 1) > (qf)5) break;
     if (j > 2000000) break;
   }
   qf k1, k2, k3;
   bessel_k123_scaled(m, &k1, &k2, &k3);   // same e^{m} scaling as the integrals
   const qf norm = h / (m * k1);
-  const qf ang[6] = {1, 1, (qf)1 / 3, (qf)1 / 3, (qf)1 / 5, (qf)1 / 15};
-  for (int k = 0; k < 6; ++k) out[k] = s[k] * norm * ang[k];
+  const int src[kMom] = {0, 1, 2, 3, 4, 4, 5, 5, 6, 6, 6};
+  const qf ang[kMom] = {1, 1, (qf)1 / 3, (qf)1 / 3, (qf)1 / 5, (qf)1 / 15,
+                        (qf)1 / 5, (qf)1 / 15, (qf)1 / 7, (qf)1 / 35, (qf)1 / 105};
+  for (int k = 0; k < kMom; ++k) out[k] = s[src[k]] * norm * ang[k];
 }
 
 // ------------------------------------------------------------ Eq. 52 solve
-// Column k of A(v0): sums over group k of the six monomials at the momenta
-// p = m gamma_k (1, v0 n) of Eq. 48.
-// Integer sums over the vectors of one group: count, sum n_x^2, sum n_x^4,
-// sum n_x^2 n_y^2 (the orbit is symmetric, so these fix all six monomials).
+// Integer sums over the vectors of one group: count and the sums of n_x^2,
+// n_x^4, n_x^2 n_y^2, n_x^6, n_x^4 n_y^2, n_x^2 n_y^2 n_z^2 (the orbit is
+// symmetric, so these fix all eleven monomials).
 struct GroupSums {
-  int cnt, sx2, sx4, sx2y2, len2;
+  int cnt, sx2, sx4, sx2y2, sx6, sx4y2, sx2y2z2, len2;
 };
 
 static GroupSums group_sums(int gid) {
-  GroupSums g{0, 0, 0, 0, group_len2(gid)};
+  GroupSums g{0, 0, 0, 0, 0, 0, 0, group_len2(gid)};
   for (const auto& v : group_orbit(gid)) {
+    const int x2 = v[0] * v[0], y2 = v[1] * v[1], z2 = v[2] * v[2];
     g.cnt += 1;
-    g.sx2 += v[0] * v[0];
-    g.sx4 += v[0] * v[0] * v[0] * v[0];
-    g.sx2y2 += v[0] * v[0] * v[1] * v[1];
+    g.sx2 += x2;
+    g.sx4 += x2 * x2;
+    g.sx2y2 += x2 * y2;
+    g.sx6 += x2 * x2 * x2;
+    g.sx4y2 += x2 * x2 * y2;
+    g.sx2y2z2 += x2 * y2 * z2;
   }
   return g;
 }
 
-// Column k of A(v0): sums over group k of the six monomials at the momenta
-// p = m gamma_k (1, v0 n) of Eq. 48.
-template <typename F>
-static bool build_system(const GroupSums* gs, F m, F v0, F A[6][6]) {
-  for (int k = 0; k < 6; ++k) {
+// Column k of A(v0) (K = 6 or 11 rows): sums over group k of the monomials at
+// the momenta p = m gamma_k (1, v0 n) of Eq. 48.
+template <typename F, int K>
+static bool build_system(const GroupSums* gs, F m, F v0, F A[K][K]) {
+  for (int k = 0; k < K; ++k) {
     const F s = 1 - v0 * v0 * (F)gs[k].len2;
     if (!(s > 0)) return false;
     F gam;
     if constexpr (std::is_same<F, double>::value) gam = 1 / std::sqrt(s);
     else gam = 1 / q_sqrt(s);
-    const F p0 = m * gam, ps = m * gam * v0, ps2 = ps * ps;
+    const F p0 = m * gam, ps = m * gam * v0, ps2 = ps * ps, ps4 = ps2 * ps2;
     A[0][k] = (F)gs[k].cnt;
     A[1][k] = (F)gs[k].cnt * p0;
     A[2][k] = ps2 * (F)gs[k].sx2;
     A[3][k] = p0 * ps2 * (F)gs[k].sx2;
-    A[4][k] = ps2 * ps2 * (F)gs[k].sx4;
-    A[5][k] = ps2 * ps2 * (F)gs[k].sx2y2;
+    A[4][k] = ps4 * (F)gs[k].sx4;
+    A[5][k] = ps4 * (F)gs[k].sx2y2;
+    if constexpr (K == 11) {
+      A[6][k] = p0 * ps4 * (F)gs[k].sx4;
+      A[7][k] = p0 * ps4 * (F)gs[k].sx2y2;
+      A[8][k] = ps4 * ps2 * (F)gs[k].sx6;
+      A[9][k] = ps4 * ps2 * (F)gs[k].sx4y2;
+      A[10][k] = ps4 * ps2 * (F)gs[k].sx2y2z2;
+    }
   }
   return true;
 }
 
-template <typename F>
-static bool solve6(F A[6][6], F b[6], F x[6]) {
-  F M[6][7];
-  for (int r = 0; r < 6; ++r) {
-    for (int c = 0; c < 6; ++c) M[r][c] = A[r][c];
-    M[r][6] = b[r];
+// Gaussian elimination with partial pivoting; false if singular or NaN.
+template <typename F, int K>
+static bool solve_k(F A[K][K], const F* b, F* x) {
+  F M[K][K + 1];
+  for (int r = 0; r < K; ++r) {
+    for (int c = 0; c < K; ++c) M[r][c] = A[r][c];
+    M[r][K] = b[r];
   }
-  for (int c = 0; c < 6; ++c) {
+  for (int c = 0; c < K; ++c) {
     int piv = c;
-    for (int r = c + 1; r < 6; ++r)
+    for (int r = c + 1; r < K; ++r)
       if ((M[r][c] < 0 ? -M[r][c] : M[r][c]) > (M[piv][c] < 0 ? -M[piv][c] : M[piv][c])) piv = r;
     if (M[piv][c] == 0) return false;
     if (piv != c)
-      for (int k = 0; k < 7; ++k) std::swap(M[c][k], M[piv][k]);
-    for (int r = c + 1; r < 6; ++r) {
+      for (int k = 0; k <= K; ++k) std::swap(M[c][k], M[piv][k]);
+    for (int r = c + 1; r < K; ++r) {
       const F f = M[r][c] / M[c][c];
-      for (int k = c; k < 7; ++k) M[r][k] -= f * M[c][k];
+      for (int k = c; k <= K; ++k) M[r][k] -= f * M[c][k];
     }
   }
-  for (int r = 5; r >= 0; --r) {
-    F s = M[r][6];
-    for (int k = r + 1; k < 6; ++k) s -= M[r][k] * x[k];
+  for (int r = K - 1; r >= 0; --r) {
+    F s = M[r][K];
+    for (int k = r + 1; k < K; ++k) s -= M[r][k] * x[k];
     x[r] = s / M[r][r];
   }
-  for (int r = 0; r < 6; ++r)
+  for (int r = 0; r < K; ++r)
     if (!(x[r] == x[r])) return false;
   return true;
 }
 
 static bool valid_groups(const int* groups, int ngroups) {
-  if (ngroups != 6 || !groups) return false;
-  for (int k = 0; k < 6; ++k) {
+  if ((ngroups != 6 && ngroups != 11) || !groups) return false;
+  for (int k = 0; k < ngroups; ++k) {
     if (groups[k] < 1 || groups[k] > 84) return false;
     for (int j = 0; j < k; ++j)
       if (groups[j] == groups[k]) return false;
@@ -247,58 +265,67 @@ static bool valid_groups(const int* groups, int ngroups) {
   return true;
 }
 
-bool quadrature_weights(const int* groups, double m, double v0, double* w) {
-  qf A[6][6], b[6], x[6];
-  GroupSums gs[6];
-  for (int k = 0; k < 6; ++k) gs[k] = group_sums(groups[k]);
-  rest_moments_q((qf)m, b);
-  if (!build_system<qf>(gs, (qf)m, (qf)v0, A)) return false;
-  if (!solve6<qf>(A, b, x)) return false;
-  for (int k = 0; k < 6; ++k) w[k] = (double)x[k];
+template <int K>
+static bool weights_q(const int* groups, double m, double v0, qf* x) {
+  qf A[K][K], b[K];
+  GroupSums gs[K];
+  for (int k = 0; k < K; ++k) gs[k] = group_sums(groups[k]);
+  rest_moments_q((qf)m, b, K);
+  if (!build_system<qf, K>(gs, (qf)m, (qf)v0, A)) return false;
+  return solve_k<qf, K>(A, b, x);
+}
+
+bool quadrature_weights(const int* groups, int ngroups, double m, double v0, double* w) {
+  qf x[kMom];
+  bool ok = false;
+  if (ngroups == 6) ok = weights_q<6>(groups, m, v0, x);
+  else if (ngroups == 11) ok = weights_q<11>(groups, m, v0, x);
+  if (!ok) return false;
+  for (int k = 0; k < ngroups; ++k) w[k] = (double)x[k];
   return true;
 }
 
 // Positive-weight windows (Sec. III D).  Each weight w_k(v0) is scanned on a
 // uniform grid; every sign change is refined by bisection; the sorted set of
 // crossings splits (0, v_max) into intervals of constant sign pattern, and
-// those whose midpoint has all six weights positive are the windows.
-int quadrature_window(const int* groups, double m, double* lo, double* hi) {
+// those whose midpoint has all weights positive are the windows.
+template <int K>
+static int window_k(const int* groups, double m, double* lo, double* hi) {
   double vmax = 1e300;
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < K; ++k) {
     const int l2 = group_len2(groups[k]);
     if (l2 > 0) vmax = std::min(vmax, 1.0 / std::sqrt((double)l2));
   }
   if (vmax > 1.0) vmax = 1.0;
-  qf bq[6];
-  rest_moments_q((qf)m, bq);
-  double b[6];
-  for (int k = 0; k < 6; ++k) b[k] = (double)bq[k];
-  GroupSums gs[6];
-  for (int k = 0; k < 6; ++k) gs[k] = group_sums(groups[k]);
+  qf bq[K];
+  rest_moments_q((qf)m, bq, K);
+  double b[K];
+  for (int k = 0; k < K; ++k) b[k] = (double)bq[k];
+  GroupSums gs[K];
+  for (int k = 0; k < K; ++k) gs[k] = group_sums(groups[k]);
   auto weights_d = [&](double v, double* w) -> bool {
-    double A[6][6], bb[6];
-    for (int k = 0; k < 6; ++k) bb[k] = b[k];
-    if (!build_system<double>(gs, m, v, A)) return false;
-    return solve6<double>(A, bb, w);
+    double A[K][K];
+    if (!build_system<double, K>(gs, m, v, A)) return false;
+    return solve_k<double, K>(A, b, w);
   };
   const int N = 20000;
   const double v_a = vmax * 1e-4, v_b = vmax * (1 - 1e-9);
   std::vector<double> cross;
-  double wprev[6];
+  double wprev[K];
   bool okprev = weights_d(v_a, wprev);
   double vprev = v_a;
   for (int i = 1; i <= N; ++i) {
     const double v = v_a + (v_b - v_a) * i / N;
-    double w[6];
+    double w[K];
     const bool ok = weights_d(v, w);
     if (ok && okprev) {
-      for (int k = 0; k < 6; ++k) {
+      for (int k = 0; k < K; ++k) {
         if ((w[k] > 0) != (wprev[k] > 0)) {
           double a = vprev, c = v;
           const bool sa = wprev[k] > 0;
           for (int it = 0; it < 80; ++it) {
             const double mid = 0.5 * (a + c);
-            double wm[6];
+            double wm[K];
             if (!weights_d(mid, wm)) break;
             if ((wm[k] > 0) == sa) a = mid;
             else c = mid;
@@ -321,10 +348,10 @@ int quadrature_window(const int* groups, double m, double* lo, double* hi) {
   for (size_t i = 0; i + 1 < cross.size(); ++i) {
     const double a = cross[i], c = cross[i + 1];
     if (!(c > a)) continue;
-    double w[6];
-    if (!quadrature_weights(groups, m, 0.5 * (a + c), w)) continue;
+    double w[K];
+    if (!quadrature_weights(groups, K, m, 0.5 * (a + c), w)) continue;
     bool pos = true;
-    for (int k = 0; k < 6; ++k) pos = pos && (w[k] > 0);
+    for (int k = 0; k < K; ++k) pos = pos && (w[k] > 0);
     if (!pos) continue;
     ++count;
     if (c - a > best) {
@@ -336,6 +363,11 @@ int quadrature_window(const int* groups, double m, double* lo, double* hi) {
   return count;
 }
 
+int quadrature_window(const int* groups, int ngroups, double m, double* lo, double* hi) {
+  if (ngroups == 6) return window_k<6>(groups, m, lo, hi);
+  if (ngroups == 11) return window_k<11>(groups, m, lo, hi);
+  return 0;
+}
 // ------------------------------------------------------- App. A constants
 static SiteConsts site_consts(double mbar, qf* cJ00_1, qf* cJ00_0, qf* Aq, qf* Bq, qf* Cq,
                               qf* Dq, qf* Eq, qf* k21q, qf* k32q) {
@@ -379,7 +411,7 @@ struct PopConstsQ {
 };
 
 rlbm_status build_stencil(const rlbm_stencil* st, double m, StencilBuild* out, std::string* err) {
-  if (!st || !valid_groups(st->groups, st->ngroups)) {
+  if (!st || !valid_groups(st->groups, st->ngroups) || st->ngroups != 6) {
     *err = "stencil must list 6 distinct group ids in 1..84 (second order, Sec. III D)";
     return RLBM_EINVAL;
   }
@@ -400,7 +432,7 @@ rlbm_status build_stencil(const rlbm_stencil* st, double m, StencilBuild* out, s
   }
   if (v0 == 0) {
     double lo, hi;
-    if (quadrature_window(sorted, m, &lo, &hi) == 0) {
+    if (quadrature_window(sorted, 6, m, &lo, &hi) == 0) {
       *err = "no v0 gives positive weights for these groups at this m";
       return RLBM_ENOQUAD;
     }
@@ -413,7 +445,7 @@ rlbm_status build_stencil(const rlbm_stencil* st, double m, StencilBuild* out, s
       return RLBM_EINVAL;
     }
   }
-  if (!quadrature_weights(sorted, m, v0, out->w_group)) {
+  if (!quadrature_weights(sorted, 6, m, v0, out->w_group)) {
     *err = "singular quadrature system at this v0";
     return RLBM_ENOQUAD;
   }
@@ -425,14 +457,7 @@ rlbm_status build_stencil(const rlbm_stencil* st, double m, StencilBuild* out, s
   }
   // weights again in binary128 for the per-population constants
   qf wq[6];
-  {
-    qf A[6][6], b[6];
-    GroupSums gs[6];
-    for (int k = 0; k < 6; ++k) gs[k] = group_sums(sorted[k]);
-    rest_moments_q((qf)m, b);
-    build_system<qf>(gs, (qf)m, (qf)v0, A);
-    solve6<qf>(A, b, wq);
-  }
+  weights_q<6>(sorted, m, v0, wq);
   qf cJ1, cJ0, Aq, Bq, Cq, Dq, Eq, k21q, k32q;
   out->sc = site_consts(m, &cJ1, &cJ0, &Aq, &Bq, &Cq, &Dq, &Eq, &k21q, &k32q);
   const qf s3 = q_sqrt((qf)3);
@@ -521,20 +546,195 @@ rlbm_status build_stencil(const rlbm_stencil* st, double m, StencilBuild* out, s
   return RLBM_OK;
 }
 
+// ------------------------------------------------------- third order
+// Inverse of a K x K binary128 matrix by Gauss-Jordan elimination with
+// partial pivoting (K = 20: the Gram matrix of the centred monomials).
+static bool invert_q(std::vector<qf>& M, int K) {
+  std::vector<qf> I((size_t)K * K, (qf)0);
+  for (int i = 0; i < K; ++i) I[(size_t)i * K + i] = 1;
+  for (int c = 0; c < K; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < K; ++r)
+      if (q_abs(M[(size_t)r * K + c]) > q_abs(M[(size_t)piv * K + c])) piv = r;
+    if (M[(size_t)piv * K + c] == 0) return false;
+    if (piv != c)
+      for (int k = 0; k < K; ++k) {
+        std::swap(M[(size_t)c * K + k], M[(size_t)piv * K + k]);
+        std::swap(I[(size_t)c * K + k], I[(size_t)piv * K + k]);
+      }
+    const qf d = 1 / M[(size_t)c * K + c];
+    for (int k = 0; k < K; ++k) {
+      M[(size_t)c * K + k] *= d;
+      I[(size_t)c * K + k] *= d;
+    }
+    for (int r = 0; r < K; ++r) {
+      if (r == c) continue;
+      const qf f = M[(size_t)r * K + c];
+      if (f == 0) continue;
+      for (int k = 0; k < K; ++k) {
+        M[(size_t)r * K + k] -= f * M[(size_t)c * K + k];
+        I[(size_t)r * K + k] -= f * I[(size_t)c * K + k];
+      }
+    }
+  }
+  M.swap(I);
+  return true;
+}
+
+// The twenty centred monomials (kO3Mono order) at one folded population.
+static void o3_monomials(qf t, qf px, qf py, qf pz2, qf* phi) {
+  phi[0] = 1;
+  phi[1] = t;
+  phi[2] = px;
+  phi[3] = py;
+  phi[4] = t * px;
+  phi[5] = t * py;
+  phi[6] = px * px;
+  phi[7] = py * py;
+  phi[8] = px * py;
+  phi[9] = pz2;
+  phi[10] = t * px * px;
+  phi[11] = t * py * py;
+  phi[12] = t * px * py;
+  phi[13] = px * px * px;
+  phi[14] = px * px * py;
+  phi[15] = px * py * py;
+  phi[16] = py * py * py;
+  phi[17] = t * pz2;
+  phi[18] = px * pz2;
+  phi[19] = py * pz2;
+}
+
+rlbm_status build_stencil_o3(const rlbm_stencil* st, double m, StencilBuildO3* out, std::string* err) {
+  if (!st || !valid_groups(st->groups, st->ngroups) || st->ngroups != 11) {
+    *err = "a third-order stencil lists 11 distinct group ids in 1..84 (Sec. III D)";
+    return RLBM_EINVAL;
+  }
+  if (!(m > 0) || !std::isfinite(m)) {
+    *err = "m must be positive and finite";
+    return RLBM_EINVAL;
+  }
+  int sorted[11];
+  for (int k = 0; k < 11; ++k) sorted[k] = st->groups[k];
+  std::sort(sorted, sorted + 11);
+  for (int k = 0; k < 11; ++k) out->groups[k] = sorted[k];
+  out->mbar = m;
+  double v0 = st->v0;
+  if (!(v0 >= 0) || !std::isfinite(v0)) {
+    *err = "v0 must be >= 0";
+    return RLBM_EINVAL;
+  }
+  if (v0 == 0) {
+    double lo, hi;
+    if (quadrature_window(sorted, 11, m, &lo, &hi) == 0) {
+      *err = "no v0 gives positive weights for these groups at this m";
+      return RLBM_ENOQUAD;
+    }
+    v0 = 0.5 * (lo + hi);
+  }
+  out->v0 = v0;
+  for (int k = 0; k < 11; ++k)
+    if (!(v0 * v0 * group_len2(sorted[k]) < 1)) {
+      *err = "v0 ||n_k|| must stay below the speed of light (Sec. III C)";
+      return RLBM_EINVAL;
+    }
+  qf wq[11];
+  if (!weights_q<11>(sorted, m, v0, wq)) {
+    *err = "singular quadrature system at this v0";
+    return RLBM_ENOQUAD;
+  }
+  for (int k = 0; k < 11; ++k) {
+    out->w_group[k] = (double)wq[k];
+    if (!(wq[k] > 0)) {
+      *err = "a quadrature weight is not positive at this v0 (Sec. III D requires w > 0)";
+      return RLBM_ENOQUAD;
+    }
+  }
+  qf cJ1, cJ0, Aq, Bq, Cq, Dq, Eq, k21q, k32q;
+  out->sc = site_consts(m, &cJ1, &cJ0, &Aq, &Bq, &Cq, &Dq, &Eq, &k21q, &k32q);
+  const qf mq = (qf)m;
+  const qf c = mq * k21q;                  // <p0>_omega = mbar K2/K1(mbar)
+  const qf wr1 = 1 / (k21q * mq);          // K1/K2(mbar)/mbar
+  out->c = (double)c;
+  // fold (as build_stencil): per group, the orbit with +-n_z merged
+  struct PopQ {
+    qf p0, px, py, pz2, w;
+  };
+  std::vector<PopQ> pq;
+  out->pops.clear();
+  out->halo = 0;
+  for (int k = 0; k < 11; ++k) {
+    const qf len2 = (qf)group_len2(sorted[k]);
+    const qf gam = 1 / q_sqrt(1 - (qf)v0 * (qf)v0 * len2);
+    const qf p0 = mq * gam, ps = mq * gam * (qf)v0;
+    std::vector<std::array<int, 3>> seen;
+    std::vector<int> mult;
+    for (const auto& v : group_orbit(sorted[k])) {
+      std::array<int, 3> key{v[0], v[1], std::abs(v[2])};
+      auto it = std::find(seen.begin(), seen.end(), key);
+      if (it == seen.end()) {
+        seen.push_back(key);
+        mult.push_back(1);
+      } else {
+        mult[it - seen.begin()] += 1;
+      }
+    }
+    for (size_t a = 0; a < seen.size(); ++a) {
+      FoldedPop fp{k, seen[a][0], seen[a][1], seen[a][2] * seen[a][2], mult[a]};
+      out->pops.push_back(fp);
+      out->halo = std::max(out->halo, std::max(std::abs(fp.nx), std::abs(fp.ny)));
+      pq.push_back(PopQ{p0, ps * fp.nx, ps * fp.ny, ps * ps * fp.nz2, wq[k] * (qf)fp.mult});
+    }
+  }
+  const int Q = (int)pq.size();
+  if (Q > kMaxPopO3) {
+    *err = "folded stencil has more populations than the compiled maximum (256)";
+    return RLBM_ENOTSUP;
+  }
+  // Gram matrix of the centred monomials under the stencil's weights; the
+  // quadrature is exact for their products, so this is the continuum one
+  const int K = kO3Mono;
+  std::vector<qf> phi((size_t)Q * K), G((size_t)K * K, (qf)0);
+  for (int i = 0; i < Q; ++i) {
+    o3_monomials(pq[i].p0 - c, pq[i].px, pq[i].py, pq[i].pz2, &phi[(size_t)i * K]);
+    for (int a = 0; a < K; ++a)
+      for (int b = 0; b < K; ++b) G[(size_t)a * K + b] += pq[i].w * phi[(size_t)i * K + a] * phi[(size_t)i * K + b];
+  }
+  if (!invert_q(G, K)) {
+    *err = "singular third-order Gram matrix (the stencil is not third order)";
+    return RLBM_ENOQUAD;
+  }
+  qf mref[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  out->rows.assign(Q, {});
+  for (int i = 0; i < Q; ++i) {
+    const PopQ& P = pq[i];
+    const qf mom[9] = {P.p0, P.px, P.py, P.p0 * P.p0, P.p0 * P.px, P.p0 * P.py,
+                       P.px * P.px, P.px * P.py, P.py * P.py};
+    auto& row = out->rows[i];
+    for (int q = 0; q < 9; ++q) {
+      row[q] = (double)mom[q];
+      mref[q] += P.w * wr1 * mom[q];
+    }
+    row[9] = (double)(P.w * wr1);
+    for (int l = 0; l < K; ++l) {
+      qf acc = 0;
+      for (int b = 0; b < K; ++b) acc += G[(size_t)l * K + b] * phi[(size_t)i * K + b];
+      row[10 + l] = (double)(P.w * acc);
+    }
+    row[30] = (double)(P.px / P.p0);
+    row[31] = (double)(P.py / P.p0);
+  }
+  for (int q = 0; q < 9; ++q) out->mref1[q] = (double)mref[q];
+  return RLBM_OK;
+}
+
 rlbm_status build_stencil3d(const rlbm_stencil* st, double m, StencilBuild3* out, std::string* err) {
   rlbm_status s = build_stencil(st, m, &out->sb, err);
   if (s != RLBM_OK) return s;
   const int* g6 = out->sb.groups;        // ascending, as the weights
   const double v0 = out->sb.v0;
   qf wq[6];
-  {
-    qf A[6][6], b[6];
-    GroupSums gs[6];
-    for (int k = 0; k < 6; ++k) gs[k] = group_sums(g6[k]);
-    rest_moments_q((qf)m, b);
-    build_system<qf>(gs, (qf)m, (qf)v0, A);
-    solve6<qf>(A, b, wq);
-  }
+  weights_q<6>(g6, m, v0, wq);
   qf cJ1, cJ0, Aq, Bq, Cq, Dq, Eq, k21q, k32q;
   site_consts(m, &cJ1, &cJ0, &Aq, &Bq, &Cq, &Dq, &Eq, &k21q, &k32q);
   const qf s3 = q_sqrt((qf)3);

@@ -43,11 +43,12 @@ struct StencilBuild {
 // Vectors of group gid of Table I (full-symmetric orbit of its generator).
 std::vector<std::array<int, 3>> group_orbit(int gid);
 
-// Weights of Eq. 52 at (m, v0) in extended precision; false if singular.
-bool quadrature_weights(const int* groups, double m, double v0, double* w);
+// Weights of Eq. 52 at (m, v0) in extended precision for 6 (second order) or
+// 11 (third order) groups; false if singular.
+bool quadrature_weights(const int* groups, int ngroups, double m, double v0, double* w);
 
 // Widest positive-weight interval; returns number of disjoint windows (0: none).
-int quadrature_window(const int* groups, double m, double* lo, double* hi);
+int quadrature_window(const int* groups, int ngroups, double m, double* lo, double* hi);
 
 // Full build: validates, solves weights, folds, App. A constants.
 // Returns RLBM_OK or an error with a message.
@@ -83,6 +84,33 @@ struct StencilBuild3 {
 // Unfolded build for 3D lattices (the paper's stencil itself, Table I orbits
 // with signed n_z); same validation and weights as build_stencil.
 rlbm_status build_stencil3d(const rlbm_stencil* st, double m, StencilBuild3* out, std::string* err);
+
+// Third-order stencil folded onto the xy plane (eleven groups, Sec. III D).
+// The equilibrium is f_i^eq = n w_i P(p_i) with P the polynomial of degree
+// <= 3 whose moments against every monomial of degree <= 3 are those of the
+// Maxwell-Juttner distribution (the third-order truncation of Eq. 14-16).
+// Per population i the table row (kRowO3 entries) holds:
+//   0..8   p0, px, py, p0p0, p0px, p0py, pxpx, pxpy, pypy
+//   9      wr_i = w_i K1/K2(mbar)/mbar  (f^eq of the rest state at T_R, n = 1)
+//   10..29 W_il = w_i (G^-1 phi(p_i))_l: the dual basis of the 20 centred
+//          monomials phi_l (kO3Mono order, t = p0 - c, c = mbar K2/K1(mbar)),
+//          G_lk = sum_i w_i phi_l(p_i) phi_k(p_i)
+//   30, 31 px/p0, py/p0
+// so that f^eq_i = n wr_i + n sum_l dmu_l W_il, dmu_l the deviation of the
+// l-th centred moment (per unit density) from its value at rest and T_R.
+struct StencilBuildO3 {
+  int groups[11];
+  double mbar, v0;
+  double w_group[11];
+  std::vector<FoldedPop> pops;
+  std::vector<std::array<double, kRowO3>> rows;
+  double mref1[9];       // moments of the reference wr_i (unit density)
+  double c;              // centring shift mbar K2/K1(mbar) = <p0>_omega
+  int halo;
+  SiteConsts sc;         // mbar, R(mbar) and the constants of the site solve
+};
+
+rlbm_status build_stencil_o3(const rlbm_stencil* st, double m, StencilBuildO3* out, std::string* err);
 
 // Per-population constant table for the kernels (CT = float or double).
 template <typename CT>

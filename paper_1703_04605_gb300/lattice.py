@@ -19,7 +19,8 @@ def _default_stream():
 class Lattice:
     """A periodic Nx x Ny lattice advanced by the library's CUDA kernels.
 
-    groups  six group ids of Table I; m = m/T_R; tau in lattice steps;
+    groups  six group ids of Table I (second-order equilibrium) or eleven
+    (third order); m = m/T_R; tau in lattice steps;
     dtype   'f64' | 'f32' | 'bf16dev';  v0 = 0 picks the centre of the widest
     positive-weight window.  stream: a cudaStream_t as int (default: torch's
     current stream when torch sees a GPU, else the legacy default stream)."""
@@ -96,7 +97,9 @@ class Lattice:
     def info(self):
         inf = A.Info()
         self._chk(self._lib.rlbm_get_info(self._ctx, C.byref(inf)))
-        return {k: (list(getattr(inf, k)) if k == "w_group" else getattr(inf, k)) for k, _ in A.Info._fields_}
+        out = {k: (list(getattr(inf, k)) if k == "w_group" else getattr(inf, k)) for k, _ in A.Info._fields_}
+        out["w_group"] = out["w_group"][: 11 if out["order"] == 3 else 6]
+        return out
 
 
 def batch_step(lattices, k=1):

@@ -20,6 +20,11 @@ STENCIL_M1 = dict(groups=[5, 12, 14, 17, 21, 26], m=1.0, v0=0.23342)
 STENCIL_G16 = dict(groups=[1, 2, 3, 4, 5, 6], m=5.0, v0=0.398)
 STENCIL_E5 = dict(groups=[1, 14, 49, 51, 60, 70], m=0.36, v0=0.1488232)
 STENCIL_S2 = dict(groups=[3, 9, 10, 14, 17, 21], m=3.0, v0=0.227)
+# Third order (eleven groups, Sec. III D) at m/T_R = 5: positive for v0 in
+# (0.273903, 0.274861); 159 populations, 100 after the fold, halo 3.  The
+# paper's own third-order quadratures C and D have negative weights at their
+# printed v0 under the eleven conditions (read as misprints).
+STENCIL_O3 = dict(groups=[1, 2, 5, 6, 7, 9, 10, 11, 12, 13, 15], m=5.0, v0=0.27438)
 
 
 def seed(config_index):

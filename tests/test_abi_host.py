@@ -73,6 +73,29 @@ def test_window_matches_oracle_m1(lib):
     assert abs(lo - olo) < 1e-9 and abs(hi - ohi) < 1e-9
 
 
+O3 = [1, 2, 5, 6, 7, 9, 10, 11, 12, 13, 15]
+
+
+def test_third_order_weights_and_window_match_oracle(lib):
+    # eleven groups: the 11 x 11 system of the third-order conditions
+    w = A.quadrature_weights(O3, 5.0, 0.27438)
+    wo = QD.weights_dec(O3, 5.0, Decimal(0.27438))
+    assert len(w) == 11
+    for a, b in zip(w, wo):
+        assert abs(a / float(b) - 1) < 1e-12
+    lo, hi, nwin = A.quadrature_window(O3, 5.0)
+    (olo, ohi), = QD.positive_window(O3, 5.0, 0.2730, 0.2755, samples=26)
+    assert nwin == 1
+    assert abs(lo - olo) < 1e-9 and abs(hi - ohi) < 1e-9
+
+
+def test_third_order_create_validates_before_device(lib):
+    assert _create(lib, groups=O3[:10] + [1], m=5.0, v0=0.27438)[0] == A.RLBM_EINVAL
+    assert _create(lib, groups=O3, m=5.0, v0=0.26)[0] == A.RLBM_ENOQUAD
+    assert b"weight" in lib.rlbm_last_error(None)
+    assert _create(lib, groups=O3, m=5.0, v0=0.27438, dtype=2)[0] == A.RLBM_ENOTSUP
+
+
 def test_ratio_tables_against_oracle_bessel(lib):
     rng = np.random.default_rng(3)
     z = np.exp(rng.uniform(np.log(2.0 ** -18), np.log(2.0 ** 18), 60))
