@@ -657,7 +657,9 @@ def run_third_order(args):
                        "sites": int(sites), "Q": info["Q"], "order": info["order"], "l2": "inputs larger than L2"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
-                         "kernel": "step_o3_kernel<float>", "bytes_per_site": info["bytes_per_site"]},
+                         "kernel": ("fused_o3_kernel<StencilO3Def<1,2,5,6,7,9,10,11,12,13,15>>"
+                                    if info["kernel"] == 5 else "step_o3_kernel<float>"),
+                         "bytes_per_site": info["bytes_per_site"]},
             "f64": {"MLUPS": sites / (ms64 / 1e3) / 1e6, "ms_per_step": ms64, "steps": k64,
                     "frac_hbm": info64["bytes_per_site"] * sites / (ms64 / 1e3) / 1e9 / peak},
             "error_vs_f64": err, "gpu_launches": args.steps, "clocks": clk.summary()}

@@ -94,10 +94,12 @@ typedef struct {
                                2 Q sizeof(storage)                           */
   size_t extra_bytes_per_site; /* other per-site traffic of one step (macros) */
   size_t device_bytes;      /* device memory owned by the context            */
-  int kernel;               /* step kernel: 0 generic (per-population constants
-                               from the parameter block), 1..3 compiled for the
+  int kernel;               /* step kernel: 0 generic; 1..4 compiled for the
                                stencils {5,12,14,17,21,26}, {1..6},
-                               {1,14,49,51,60,70} (FP32 storage)              */
+                               {1,14,49,51,60,70}, {3,9,10,14,17,21}; 5 the
+                               compiled third-order stencil
+                               {1,2,5,6,7,9,10,11,12,13,15} (FP32 storage,
+                               lattice at least a halo wide)                   */
   int order;                /* expansion order of f^eq: 2 or 3               */
 } rlbm_info;
 

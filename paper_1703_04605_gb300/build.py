@@ -14,7 +14,7 @@ LIB = os.path.join(PKG, "librlbm.so")
 
 CUDA_SOURCES = ["rlbm_kernels_f64.cu", "rlbm_kernels_f32.cu", "rlbm_kernels_io.cu",
                 "rlbm_fused_m1.cu", "rlbm_fused_g16.cu", "rlbm_fused_e5.cu", "rlbm_fused_s2.cu", "rlbm_noalloc.cu",
-                "rlbm_kernels3d.cu", "rlbm_fused3d.cu", "rlbm_kernels_o3.cu"]
+                "rlbm_kernels3d.cu", "rlbm_fused3d.cu", "rlbm_kernels_o3.cu", "rlbm_fused_o3.cu"]
 CXX_SOURCES = ["rlbm_stencil.cpp", "rlbm_host.cpp", "rlbm_host3d.cpp"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

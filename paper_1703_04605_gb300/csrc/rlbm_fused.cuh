@@ -248,6 +248,101 @@ __device__ __forceinline__ void fused_collide_pop_all(std::integer_sequence<int,
   (fused_collide_pop<Def, BF, Is>(d, c, cq, a0, ax, ay, out, plane), ...);
 }
 
+// Site solve of the split arithmetic (see the header comment): from the
+// deviation moments M (reference excluded) to U, n = n_r + n_d and
+// T = 1 + T_d, R = R(mbar) + dR.  Landau frame by FP32 Newton on the full
+// moments; EOS by FP32 Newton on the deviations and one FP64 Newton step with
+// the FP64 R(zeta) table.
+struct SplitSite {
+  float dg, U0, Ux, Uy, n, nd, Td, dR, R, T;
+};
+
+// P: FusedParams or FusedO3Params (fields mref, nr, yr, Rr, mb, cv_r, mb64,
+// Rr64, rt64, rt32).
+template <class P>
+__device__ __forceinline__ SplitSite split_solve(const P& p, const float (&M)[9], unsigned& fl) {
+  // Landau frame: FP32 Newton on the full moments.  v = T^0i/(...) is well
+  // conditioned (relative error ~ FP32 rounding); the cancelling parts of the
+  // energy and density are formed below from the deviation moments.
+  float Mf[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Mf[k] = p.mref[k].hi + (p.mref[k].lo + M[k]);
+  float vx, vy, dvx, dvy;
+  {
+    const float iden = __fdividef(1.0f, Mf[3] + 0.5f * (Mf[6] + Mf[8]));
+    vx = Mf[4] * iden;
+    vy = Mf[5] * iden;
+#pragma unroll 1
+    for (int it = 0; it < 8; ++it) {
+      landau_newton_step_fast(Mf, vx, vy, dvx, dvy);
+      if (fabsf(dvx) + fabsf(dvy) < 1e-7f) break;
+    }
+  }
+  const float v2 = vx * vx + vy * vy;
+  if (!(v2 < 1.0f)) fl |= ERR_LANDAU;
+  const float sq = sqrtf(1.0f - v2);
+  const float dg = __fdividef(v2, sq * (1.0f + sq));  // gamma - 1
+  const float U0 = 1.0f + dg, Ux = U0 * vx, Uy = U0 * vy;
+  // n = U.N = n_r + n_d
+  const float Xi = M[0] - vx * M[1] - vy * M[2];
+  const float nd = fmaf(dg, p.nr.lo, fmaf(dg, Xi + p.nr.hi, Xi));
+  const float n = p.nr.hi + (p.nr.lo + nd);
+  if (!(n > 0.0f)) fl |= ERR_DENSITY;
+  // e/n = y_r + y_d
+  const float ed = M[3] - M[4] * vx - M[5] * vy;
+  const float yd = __fdividef(ed - fmaf(p.yr.hi, nd, p.yr.lo * nd), n);
+  if (!(p.yr.hi + yd > p.mb)) fl |= ERR_EOS;
+  // EOS: T = 1 + T_d solves 3 T_d + m (R(m/T) - R_r) = y_d.  FP32 Newton ...
+  float Td = yd / p.cv_r, slope = p.cv_r, R32 = p.Rr.hi;
+#pragma unroll 1
+  for (int it = 0; it < 12; ++it) {
+    const float T = 1.0f + Td;
+    if (!(T > 0.0f)) {
+      fl |= ERR_EOS;
+      Td = 0.0f;
+      break;
+    }
+    const float z = __fdividef(p.mb, T);
+    R32 = ratio32(z, p.rt32, fl);
+    const float dR = (R32 - p.Rr.hi) - p.Rr.lo;
+    slope = eos_slope<float>(R32, z);
+    const float step = __fdividef(3.0f * Td + p.mb * dR - yd, slope);
+    Td -= step;
+    if (fabsf(step) < 3e-8f) break;
+  }
+  // ... and one FP64 Newton step with the FP64 R(zeta) table
+  float dR;
+  {
+    const float Tf = 1.0f + Td;
+    const double T64 = 1.0 + (double)Td;
+    double iT = (double)__fdividef(1.0f, Tf);
+    iT = fma(iT, fma(-T64, iT, 1.0), iT);
+    const double z64 = p.mb64 * iT;
+    const double dR64 = ratio64(z64, p.rt64, fl) - p.Rr64;
+    const double g64 = fma(3.0, (double)Td, fma(p.mb64, dR64, -(double)yd));
+    const float step = __fdividef((float)g64, slope);
+    Td -= step;
+    const float R = p.Rr.hi + (p.Rr.lo + (float)dR64);
+    const float z = (float)z64;
+    const float dRdz = R * R + 3.0f * __fdividef(R, z) - 1.0f;
+    dR = fmaf(dRdz, z * step / Tf, (float)dR64);     // R at the corrected T (first order)
+  }
+  const float R = p.Rr.hi + (p.Rr.lo + dR);
+  const float T = 1.0f + Td;
+  SplitSite o;
+  o.dg = dg;
+  o.U0 = U0;
+  o.Ux = Ux;
+  o.Uy = Uy;
+  o.n = n;
+  o.nd = nd;
+  o.Td = Td;
+  o.dR = dR;
+  o.R = R;
+  o.T = T;
+  return o;
+}
+
 // One site update (see the header comment); p describes the lattice.
 template <class Def, bool BF>
 __device__ __forceinline__ void fused_site(const FusedParams& p, const void* __restrict__ fin,
@@ -286,74 +381,9 @@ __device__ __forceinline__ void fused_site(const FusedParams& p, const void* __r
       M[8] = hl_fma(p.gm[g][4], s[g][5], M[8]);
     }
 
-    // Landau frame: FP32 Newton on the full moments.  v = T^0i/(...) is well
-    // conditioned (relative error ~ FP32 rounding); the cancelling parts of the
-    // energy and density are formed below from the deviation moments.
-    float Mf[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) Mf[k] = p.mref[k].hi + (p.mref[k].lo + M[k]);
-    float vx, vy, dvx, dvy;
-    {
-      const float iden = __fdividef(1.0f, Mf[3] + 0.5f * (Mf[6] + Mf[8]));
-      vx = Mf[4] * iden;
-      vy = Mf[5] * iden;
-#pragma unroll 1
-      for (int it = 0; it < 8; ++it) {
-        landau_newton_step_fast(Mf, vx, vy, dvx, dvy);
-        if (fabsf(dvx) + fabsf(dvy) < 1e-7f) break;
-      }
-    }
-    const float v2 = vx * vx + vy * vy;
-    if (!(v2 < 1.0f)) fl |= ERR_LANDAU;
-    const float sq = sqrtf(1.0f - v2);
-    const float dg = __fdividef(v2, sq * (1.0f + sq));  // gamma - 1
-    const float U0 = 1.0f + dg, Ux = U0 * vx, Uy = U0 * vy;
-    // n = U.N = n_r + n_d
-    const float Xi = M[0] - vx * M[1] - vy * M[2];
-    const float nd = fmaf(dg, p.nr.lo, fmaf(dg, Xi + p.nr.hi, Xi));
-    const float n = p.nr.hi + (p.nr.lo + nd);
-    if (!(n > 0.0f)) fl |= ERR_DENSITY;
-    // e/n = y_r + y_d
-    const float ed = M[3] - M[4] * vx - M[5] * vy;
-    const float yd = __fdividef(ed - fmaf(p.yr.hi, nd, p.yr.lo * nd), n);
-    if (!(p.yr.hi + yd > p.mb)) fl |= ERR_EOS;
-    // EOS: T = 1 + T_d solves 3 T_d + m (R(m/T) - R_r) = y_d.  FP32 Newton ...
-    float Td = yd / p.cv_r, slope = p.cv_r, R32 = p.Rr.hi;
-#pragma unroll 1
-    for (int it = 0; it < 12; ++it) {
-      const float T = 1.0f + Td;
-      if (!(T > 0.0f)) {
-        fl |= ERR_EOS;
-        Td = 0.0f;
-        break;
-      }
-      const float z = __fdividef(p.mb, T);
-      R32 = ratio32(z, p.rt32, fl);
-      const float dR = (R32 - p.Rr.hi) - p.Rr.lo;
-      slope = eos_slope<float>(R32, z);
-      const float step = __fdividef(3.0f * Td + p.mb * dR - yd, slope);
-      Td -= step;
-      if (fabsf(step) < 3e-8f) break;
-    }
-    // ... and one FP64 Newton step with the FP64 R(zeta) table
-    float dR;
-    {
-      const float Tf = 1.0f + Td;
-      const double T64 = 1.0 + (double)Td;
-      double iT = (double)__fdividef(1.0f, Tf);
-      iT = fma(iT, fma(-T64, iT, 1.0), iT);
-      const double z64 = p.mb64 * iT;
-      const double dR64 = ratio64(z64, p.rt64, fl) - p.Rr64;
-      const double g64 = fma(3.0, (double)Td, fma(p.mb64, dR64, -(double)yd));
-      const float step = __fdividef((float)g64, slope);
-      Td -= step;
-      const float R = p.Rr.hi + (p.Rr.lo + (float)dR64);
-      const float z = (float)z64;
-      const float dRdz = R * R + 3.0f * __fdividef(R, z) - 1.0f;
-      dR = fmaf(dRdz, z * step / Tf, (float)dR64);     // R at the corrected T (first order)
-    }
-    const float R = p.Rr.hi + (p.Rr.lo + dR);
-    const float T = 1.0f + Td;
+    const SplitSite ss = split_solve(p, M, fl);
+    const float dg = ss.dg, U0 = ss.U0, Ux = ss.Ux, Uy = ss.Uy, n = ss.n, nd = ss.nd;
+    const float Td = ss.Td, dR = ss.dR, R = ss.R, T = ss.T;
     // projections without their normalisations (those live in p.gf)
     const float mr32 = fmaf(p.mb, R, 4.0f * T);          // mbar K3/K2(zeta)
     const float r0 = fmaf(p.nr.hi, dR, fmaf(p.nr.lo, dR, nd * R));   // n R - n_r R_r

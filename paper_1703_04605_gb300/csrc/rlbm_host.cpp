@@ -46,6 +46,7 @@ struct rlbm_ctx {
   int order = 2;
   std::unique_ptr<StencilBuildO3> sb3;
   std::unique_ptr<O3Params> o3;
+  std::unique_ptr<FusedO3Params> fo3;   // compiled third-order kernel (fused == 5)
   int* d_shift = nullptr;
   long long* d_off = nullptr;
   double* d_tab64 = nullptr;
@@ -164,12 +165,61 @@ static void fill_fused(rlbm_ctx* c, double nref) {
   f.err = c->d_err;
 }
 
+// Does the compiled third-order kernel serve this context (FP32, the
+// compiled groups in the host's population order, Nx, Ny >= halo)?
+static bool fused_o3_matches(const rlbm_ctx* c) {
+  using D = StencilO3M5;
+  if (c->dtype != RLBM_F32 || c->Q != D::Q || c->sb3->halo != D::halo) return false;
+  for (int k = 0; k < 11; ++k)
+    if (c->sb3->groups[k] != D::groups[k]) return false;
+  for (int i = 0; i < D::Q; ++i) {
+    const FoldedPop& fp = c->sb3->pops[i];
+    if (fp.nx != D::F.nx[i] || fp.ny != D::F.ny[i] || fp.group != D::F.grp[i] || fp.mult != D::F.mult[i])
+      return false;
+  }
+  return c->Nx >= D::halo && c->Ny >= D::halo;
+}
+
+static void fill_fused_o3(rlbm_ctx* c, double nref) {
+  using D = StencilO3M5;
+  FusedO3Params& f = *c->fo3;
+  std::memset(&f, 0, sizeof f);
+  const StencilBuildO3& sb = *c->sb3;
+  f.Nx = c->Nx;
+  f.Ny = c->Ny;
+  f.pitch = c->pitch;
+  f.plane = c->plane;
+  f.inv_tau = (float)(1.0 / c->tau);
+  f.v0 = (float)sb.v0;
+  f.mb = (float)sb.mbar;
+  f.cv_r = (float)sb.cv_r;
+  f.c = (float)sb.c;
+  f.Rr = split(sb.sc.Rr);
+  const double N0r = nref * sb.mref1[0];
+  const double er = nref * sb.mref1[3];
+  f.nr = split(N0r);
+  f.yr = split(er / N0r);
+  for (int k = 0; k < 9; ++k) f.mref[k] = split(nref * sb.mref1[k]);
+  f.Rr64 = sb.sc.Rr;
+  f.mb64 = sb.mbar;
+  for (int g = 0; g < 11; ++g)
+    for (int q = 0; q < 5; ++q) f.gm[g][q] = split(sb.gm[g][q]);
+  for (int k = 0; k < D::O.K; ++k) {
+    const auto& row = sb.rows[D::O.idx[k][0]];
+    for (int l = 0; l <= kO3Mono; ++l) f.ow[k][l] = split(row[9 + l]);
+  }
+  f.rt64 = c->d_rt64;
+  f.rt32 = c->d_rt32;
+  f.err = c->d_err;
+}
+
 // Reference density of the FP32 deviation storage (see StepParams).
 static void set_reference(rlbm_ctx* c, double nref) {
   if (c->dtype == RLBM_F64) return;
   if (c->order == 3) {
     c->o3->nref = nref;
     for (int k = 0; k < 9; ++k) c->o3->mref[k] = nref * c->sb3->mref1[k];
+    if (c->fo3) fill_fused_o3(c, nref);
     return;
   }
   for (StepParams<double>* p : {c->p64.get()}) {
@@ -301,6 +351,11 @@ static rlbm_status create_o3(const rlbm_stencil* st, double m, double tau, int N
   p.tab64 = c->d_tab64;
   p.tab32 = c->d_tab32;
   p.err = c->d_err;
+  if (fused_o3_matches(c.get())) {
+    c->fused = 5;
+    c->fo3.reset(new FusedO3Params);
+    fill_fused_o3(c.get(), 1.0);
+  }
   *out = c.release();
   return RLBM_OK;
 }
@@ -467,7 +522,8 @@ rlbm_status rlbm_step(rlbm_ctx* c, int nsteps) {
     const void* fin = c->buf[c->cur];
     void* fout = c->buf[1 - c->cur];
     cudaError_t e;
-    if (c->order == 3) e = launch_step_o3(c->dtype, *c->o3, fin, fout, c->stream);
+    if (c->order == 3)
+      e = c->fo3 ? launch_fused_o3(*c->fo3, fin, fout, c->stream) : launch_step_o3(c->dtype, *c->o3, fin, fout, c->stream);
     else if (c->dtype == RLBM_F64) e = launch_step_f64(*c->p64, fin, fout, c->qb, c->stream);
     else if (c->fused) {
       const bool bf = c->dtype == RLBM_BF16_DEV;
@@ -753,6 +809,8 @@ extern "C" rlbm_status rlbm_batch_step(rlbm_ctx* const* ctxs, int count, int nst
   for (int i = 0; i < count; ++i) {
     rlbm_ctx* c = ctxs[i];
     if (!c || !c->initialised) return fail(nullptr, RLBM_EINVAL, "batch: a context is missing or not initialised");
+    if (c->order != 2)
+      return fail(nullptr, RLBM_ENOTSUP, "batch: third-order contexts are stepped one at a time (rlbm_step)");
     if ((c->dtype != RLBM_F32 && c->dtype != RLBM_BF16_DEV) || !c->fused)
       return fail(nullptr, RLBM_ENOTSUP, "batch: every context needs FP32 or BF16 storage and a compiled stencil");
     if (c->stream != ctxs[0]->stream) return fail(nullptr, RLBM_EINVAL, "batch: contexts on different streams");

@@ -169,6 +169,29 @@ struct O3Params {
   unsigned* err;
 };
 
+// Stencil-specialised FP32 third-order step (rlbm_fused_o3.cu): the split
+// arithmetic of FusedParams with eleven groups.  Per reflection orbit K of
+// the compiled stencil, ow[K] holds the representative (+n_x, +n_y)
+// population's wr_i and its twenty dual-basis values W_il (host table row
+// entries 9..29, multiplicity included) as hi/lo pairs.
+constexpr int kMaxOrbO3 = 40;
+struct FusedO3Params {
+  int Nx, Ny;
+  long long pitch, plane;
+  float inv_tau, v0;
+  float mb, cv_r, c;
+  HL Rr, nr, yr;
+  HL mref[9];
+  double Rr64, mb64;
+  HL gm[11][5];        // per group: P0, P0^2, Pv, P0 Pv, Pv^2
+  HL ow[kMaxOrbO3][21];
+  const double* rt64;
+  const float* rt32;
+  unsigned* err;
+};
+
+cudaError_t launch_fused_o3(const FusedO3Params& p, const void* fin, void* fout, cudaStream_t s);
+
 cudaError_t launch_step_o3(rlbm_dtype dt, const O3Params& p, const void* fin, void* fout, cudaStream_t s);
 cudaError_t launch_init_o3(rlbm_dtype dt, const O3Params& p, FieldPtrs f, void* cur, void* prev, cudaStream_t s);
 cudaError_t launch_moments_o3(rlbm_dtype dt, const O3Params& p, const void* prev, MomentOut o, cudaStream_t s);

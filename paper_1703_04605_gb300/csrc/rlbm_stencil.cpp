@@ -656,6 +656,10 @@ rlbm_status build_stencil_o3(const rlbm_stencil* st, double m, StencilBuildO3* o
   const qf c = mq * k21q;                  // <p0>_omega = mbar K2/K1(mbar)
   const qf wr1 = 1 / (k21q * mq);          // K1/K2(mbar)/mbar
   out->c = (double)c;
+  {
+    const qf Rr = 1 / k21q;
+    out->cv_r = (double)(3 - mq * mq * (Rr * Rr + 3 * Rr / mq - 1));
+  }
   // fold (as build_stencil): per group, the orbit with +-n_z merged
   struct PopQ {
     qf p0, px, py, pz2, w;
@@ -667,6 +671,8 @@ rlbm_status build_stencil_o3(const rlbm_stencil* st, double m, StencilBuildO3* o
     const qf len2 = (qf)group_len2(sorted[k]);
     const qf gam = 1 / q_sqrt(1 - (qf)v0 * (qf)v0 * len2);
     const qf p0 = mq * gam, ps = mq * gam * (qf)v0;
+    const qf gm[5] = {p0, p0 * p0, ps, p0 * ps, ps * ps};
+    for (int q = 0; q < 5; ++q) out->gm[k][q] = (double)gm[q];
     std::vector<std::array<int, 3>> seen;
     std::vector<int> mult;
     for (const auto& v : group_orbit(sorted[k])) {

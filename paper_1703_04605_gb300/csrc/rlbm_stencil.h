@@ -106,6 +106,8 @@ struct StencilBuildO3 {
   std::vector<std::array<double, kRowO3>> rows;
   double mref1[9];       // moments of the reference wr_i (unit density)
   double c;              // centring shift mbar K2/K1(mbar) = <p0>_omega
+  double gm[11][5];      // per group: P0, P0^2, Pv, P0 Pv, Pv^2 (P0 = m gamma, Pv = m gamma v0)
+  double cv_r;           // 3 - mbar^2 R'(mbar): specific heat per particle at T_R
   int halo;
   SiteConsts sc;         // mbar, R(mbar) and the constants of the site solve
 };

@@ -37,13 +37,13 @@ struct Folded {
   int nx[kMaxFolded], ny[kMaxFolded], nz2[kMaxFolded], mult[kMaxFolded];
 };
 
-constexpr Folded fold_stencil(int g0, int g1, int g2, int g3, int g4, int g5) {
+template <int NG>
+constexpr Folded fold_groups(const int (&gs)[NG]) {
   Folded F{};
-  const int gs[6] = {g0, g1, g2, g3, g4, g5};
   int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
   F.Q = 0;
   F.halo = 0;
-  for (int g = 0; g < 6; ++g) {
+  for (int g = 0; g < NG; ++g) {
     const int* b = kTableI.v[gs[g] - 1];
     // collect distinct (nx, ny, |nz|) with multiplicity = number of distinct
     // 3D vectors mapping to it
@@ -111,6 +111,11 @@ constexpr Folded fold_stencil(int g0, int g1, int g2, int g3, int g4, int g5) {
     }
   }
   return F;
+}
+
+constexpr Folded fold_stencil(int g0, int g1, int g2, int g3, int g4, int g5) {
+  const int gs[6] = {g0, g1, g2, g3, g4, g5};
+  return fold_groups<6>(gs);
 }
 
 // Unfolded six-group stencil for 3D lattices: every vector of the groups'
@@ -252,5 +257,19 @@ using StencilM1 = StencilDef<5, 12, 14, 17, 21, 26>;    // m/T_R ~ 1
 using StencilG16 = StencilDef<1, 2, 3, 4, 5, 6>;        // m/T_R >~ 5 (Sec. III D example)
 using StencilE5 = StencilDef<1, 14, 49, 51, 60, 70>;    // m/T_R in [0.36, 0.58] (Sec. IV, Fig. 5)
 using StencilS2 = StencilDef<3, 9, 10, 14, 17, 21>;     // m/T_R in [1.1, 8.4]
+
+// Third-order stencils (eleven groups, ascending) with a compiled FP32 kernel.
+template <int... G>
+struct StencilO3Def {
+  static_assert(sizeof...(G) == 11, "a third-order stencil has eleven groups");
+  static constexpr int groups[11] = {G...};
+  static constexpr Folded F = fold_groups<11>({G...});
+  static constexpr int Q = F.Q;
+  static constexpr int halo = F.halo;
+  static constexpr Orbits O = make_orbits(F);
+  static_assert(orbits_cover(F, O), "reflection orbits must partition the folded stencil");
+};
+
+using StencilO3M5 = StencilO3Def<1, 2, 5, 6, 7, 9, 10, 11, 12, 13, 15>;   // m/T_R = 5
 
 }  // namespace rlbm

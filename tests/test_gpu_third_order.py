@@ -5,7 +5,8 @@ m/T_R = 5 (Q = 100 folded, halo 3).
 
 * FP64 against the oracle (1e-12) on ragged lattices that span several
   thread blocks and the halo-wide boundary band;
-* FP32 storage against the oracle (1e-5);
+* FP32 storage against the oracle (1e-5): the compiled kernel and the
+  generic one (a lattice narrower than the halo);
 * global N^0 and T^{0 nu} conserved over many steps; moments at t = 0 are the
   input fields; a uniform rest state at T_R is stationary;
 * the library's own positive-weight window and weights agree with the
@@ -44,10 +45,21 @@ def test_f64_against_oracle(shape, steps, seed):
     assert max(e.values()) < 1e-12, e
 
 
-def test_f32_against_oracle():
+def test_f32_compiled_against_oracle():
     f = smooth_fields(29, 22, seed=64, dn=0.05, dT=0.05, du=0.08)
     got, info = run_gpu(ST, 0.9, f, "f32", 10)
     assert info["bytes_per_site"] == 2 * 100 * 4
+    assert info["kernel"] == 5
+    ref = _oracle(f, 0.9, 10)
+    e = errors(got, ref)
+    assert max(e.values()) < 1e-5, e
+
+
+def test_f32_generic_against_oracle():
+    # narrower than the halo (3) in x: the generic FP32 kernel
+    f = smooth_fields(2, 17, seed=66, dn=0.05, dT=0.05, du=0.08)
+    got, info = run_gpu(ST, 0.9, f, "f32", 10)
+    assert info["kernel"] == 0
     ref = _oracle(f, 0.9, 10)
     e = errors(got, ref)
     assert max(e.values()) < 1e-5, e
