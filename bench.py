@@ -249,6 +249,9 @@ def _source_hash(files):
     return h.hexdigest()[:16]
 
 
+O3_SOURCES = ["paper_1703_04605_gb300/csrc/rlbm_fused_o3.cu", "paper_1703_04605_gb300/csrc/rlbm_fused.cuh",
+              "paper_1703_04605_gb300/csrc/rlbm_internal.h", "paper_1703_04605_gb300/csrc/rlbm_stencils.h",
+              "paper_1703_04605_gb300/csrc/rlbm_kernels.cuh"]
 FUSED_SOURCES = ["paper_1703_04605_gb300/csrc/rlbm_fused.cuh", "paper_1703_04605_gb300/csrc/rlbm_internal.h",
                  "paper_1703_04605_gb300/csrc/rlbm_stencils.h", "paper_1703_04605_gb300/csrc/rlbm_kernels.cuh",
                  "paper_1703_04605_gb300/csrc/rlbm_fused_m1.cu"]
@@ -656,7 +659,9 @@ def run_third_order(args):
                                    "G1,G2,G5,G6,G7,G9,G10,G11,G12,G13,G15 (Q=100 folded), v0=0.27438",
                        "sites": int(sites), "Q": info["Q"], "order": info["order"], "l2": "inputs larger than L2"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": (profiled_traffic("fused_o3_kernel_random_flow_o3_4096.md", O3_SOURCES)
+                                     if info["kernel"] == 5 and N == N_SIDE else None),
                          "kernel": ("fused_o3_kernel<StencilO3Def<1,2,5,6,7,9,10,11,12,13,15>>"
                                     if info["kernel"] == 5 else "step_o3_kernel<float>"),
                          "bytes_per_site": info["bytes_per_site"]},

@@ -55,6 +55,16 @@ def test_f32_compiled_against_oracle():
     assert max(e.values()) < 1e-5, e
 
 
+def test_f32_compiled_without_interior():
+    # a lattice narrower than two halos: every site wraps in x and y
+    f = smooth_fields(5, 6, seed=67, dn=0.05, dT=0.05, du=0.08)
+    got, info = run_gpu(ST, 0.9, f, "f32", 10)
+    assert info["kernel"] == 5
+    ref = _oracle(f, 0.9, 10)
+    e = errors(got, ref)
+    assert max(e.values()) < 1e-5, e
+
+
 def test_f32_generic_against_oracle():
     # narrower than the halo (3) in x: the generic FP32 kernel
     f = smooth_fields(2, 17, seed=66, dn=0.05, dT=0.05, du=0.08)
