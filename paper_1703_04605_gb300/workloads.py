@@ -78,6 +78,62 @@ def sod_tau(eta_over_s=0.1, v0=STENCIL_M1["v0"], n=1.0, T=1.0, d_g=16.0, dxT=DX_
     return 0.5 + 1.5 * eta_over_s * (s / P) * v0 / dxT
 
 
+# ---------------------------------------------------------------- demonstrations
+# The paper's Riemann problem in lattice units (Sec. IV): T_0 = 1, T_1 = 0.5,
+# n_0 = 1, n_1 = 0.124; Sec. V sweeps it over m/T_R at fixed eta/s.  The
+# sweep's values are those where the library stencil keeps this strong
+# problem physical (S2 at m/T_R = 2 and 3 does not, within ~100 steps).
+RIEMANN_STATES = dict(n=(1.0, 0.124), T=(1.0, 0.5))
+RIEMANN_SWEEP_M = (0.36, 1.0, 4.0, 5.0)
+DISC_TAU = 1.5
+
+
+def riemann(Nx=2000, Ny=1, x0=None):
+    """The Riemann problem of Sec. IV on a periodic tube (left state for
+    x < x0, so a second interface sits at x = 0)."""
+    return sod(Nx, Ny, n=RIEMANN_STATES["n"], T=RIEMANN_STATES["T"], x0=x0)
+
+
+def sound_pulse(Nx=1024, Ny=1, amp=1e-3, sigma=20.0, x0=None):
+    """A small Gaussian density bump at uniform T = T_R and rest: it splits into
+    two acoustic pulses moving at -+c_s and an entropy mode at rest."""
+    x0 = Nx / 2 if x0 is None else x0
+    xc = np.arange(Nx) + 0.5
+    bump = np.exp(-0.5 * ((xc - x0) / sigma) ** 2)
+    n = np.broadcast_to((1.0 + amp * bump)[None, :], (Ny, Nx))
+    z = np.zeros((Ny, Nx))
+    return dict(n=np.ascontiguousarray(n), ux=z, uy=z.copy(), T=np.ones((Ny, Nx)))
+
+
+def discs(N=256, R=48, v=0.5, n0=1.0, nb=0.1, T=1.0, centres=((0.5, 0.5, 1.0),)):
+    """Discs of radius R with n(r) = n0 (1 - r/R) on a background nb at rest
+    (Sec. V), moving along x with speed v times the sign in `centres`
+    ((cx, cy, sign) in units of N).  Reading: the velocity tapers with the
+    density, u(r) = v (1 - r/R) x_hat, because a uniform c/2 ending in a sharp
+    edge is not representable by the second-order equilibrium on any stencil
+    here (the lattice leaves the physical domain within a few steps)."""
+    y, x = np.mgrid[0:N, 0:N].astype(np.float64)
+    n = np.full((N, N), float(nb))
+    ux = np.zeros((N, N))
+    for cx, cy, sign in centres:
+        r = np.hypot(x - cx * N, y - cy * N)
+        prof = np.clip(1.0 - r / R, 0.0, None)
+        n = np.maximum(n, n0 * prof)
+        ux = ux + sign * v * prof
+    return dict(n=n, ux=ux, uy=np.zeros((N, N)), T=np.full((N, N), float(T)))
+
+
+def taylor_dispersion(N=256, R=48, v=0.5, **kw):
+    """Relativistic Taylor dispersion (Sec. V): one disc moving at v."""
+    return discs(N, R, v, centres=((0.5, 0.5, 1.0),), **kw)
+
+
+def colliding_discs(N=256, R=48, v=0.5, **kw):
+    """Two discs moving towards each other at -+v (Sec. V), mirror images of
+    each other under x -> N - x."""
+    return discs(N, R, v, centres=((0.25, 0.5, 1.0), (0.75, 0.5, -1.0)), **kw)
+
+
 def taylor_green(N=512, u0=0.05, n0=1.0, T0=1.0):
     k = 2 * np.pi / N
     x = np.arange(N)
