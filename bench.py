@@ -249,7 +249,8 @@ def _source_hash(files):
     return h.hexdigest()[:16]
 
 
-O3_SOURCES = ["paper_1703_04605_gb300/csrc/rlbm_fused_o3.cu", "paper_1703_04605_gb300/csrc/rlbm_fused.cuh",
+O3_SOURCES = ["paper_1703_04605_gb300/csrc/rlbm_fused_o3.cu", "paper_1703_04605_gb300/csrc/rlbm_o3.cuh",
+              "paper_1703_04605_gb300/csrc/rlbm_fused.cuh",
               "paper_1703_04605_gb300/csrc/rlbm_internal.h", "paper_1703_04605_gb300/csrc/rlbm_stencils.h",
               "paper_1703_04605_gb300/csrc/rlbm_kernels.cuh"]
 FUSED_SOURCES = ["paper_1703_04605_gb300/csrc/rlbm_fused.cuh", "paper_1703_04605_gb300/csrc/rlbm_internal.h",

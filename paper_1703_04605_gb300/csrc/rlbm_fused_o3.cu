@@ -12,7 +12,7 @@
 //    T = 1 + T_d, R = R(mbar) + dR, one FP64 EOS step) of split_solve;
 //  * the equilibrium f_i^eq - nref wr_i = n_d wr_i + sum_l e_l W_il, with
 //    e_l = n dmu_l (the deviations of the centred Maxwell-Juttner moments,
-//    rlbm_kernels_o3.cu), is evaluated once per reflection orbit: the twenty
+//    rlbm_o3.cuh), is evaluated once per reflection orbit: the twenty
 //    centred monomials split into classes even/odd in p_x and p_y (8 even in
 //    both, 5 odd in p_x only, 5 odd in p_y only, 2 odd in both), the dual
 //    basis W inherits the parities, and the members (+-n_x, +-n_y) of an
@@ -22,6 +22,7 @@
 #include <utility>
 
 #include "rlbm_fused.cuh"
+#include "rlbm_o3.cuh"
 
 namespace rlbm {
 namespace {
@@ -174,38 +175,9 @@ __global__ void __launch_bounds__(128, 3) fused_o3_kernel(const __grid_constant_
     o3_acc_all<Def>(Orb{}, d, s, M, p);
     const SplitSite ss = split_solve(p, M, fl);
     // e_l = n dmu_l in the small quantities dU, dT, dR, U_x, U_y (no cancellation)
-    const float m = p.mb, c = p.c, n = ss.n, Ux = ss.Ux, Uy = ss.Uy, dU = ss.dg, dR = ss.dR, dT = ss.Td;
-    const float T = ss.T;
-    const float h = fmaf(m, ss.R, 4.0f * T);
-    const float dh = fmaf(m, dR, 4.0f * dT);
-    const float Th = T * h;
-    const float Am = fmaf(6.0f, Th, m * m);
-    const float hU = fmaf(h, ss.U0, -c);
-    const float sdev = fmaf(dT, hU, fmaf(h, dU, dh));
-    const float q = fmaf(Am, ss.U0, -c * h);
-    const float dRm = dR * __fdividef(1.0f, m);
-    const float Ux2 = Ux * Ux, Uy2 = Uy * Uy, Uxy = Ux * Uy;
     float e[kO3Mono];
-    e[0] = n * dRm;
-    e[1] = n * fmaf(-c, dRm, dU);
-    e[2] = n * Ux;
-    e[3] = n * Uy;
-    e[4] = e[2] * hU;
-    e[5] = e[3] * hU;
-    e[6] = n * fmaf(h, Ux2, dT);
-    e[7] = n * fmaf(h, Uy2, dT);
-    e[8] = n * h * Uxy;
-    e[9] = n * dT;
-    e[10] = n * fmaf(q, Ux2, sdev);
-    e[11] = n * fmaf(q, Uy2, sdev);
-    e[12] = n * q * Uxy;
-    e[13] = e[2] * fmaf(Am, Ux2, 3.0f * Th);
-    e[14] = e[3] * fmaf(Am, Ux2, Th);
-    e[15] = e[2] * fmaf(Am, Uy2, Th);
-    e[16] = e[3] * fmaf(Am, Uy2, 3.0f * Th);
-    e[17] = n * sdev;
-    e[18] = e[2] * Th;
-    e[19] = e[3] * Th;
+    o3_deviations<float>(p.mb, p.c, ss.n, ss.U0, ss.Ux, ss.Uy, ss.dg, ss.dR, ss.Td, ss.T, ss.R, e);
+    const float Ux = ss.Ux, Uy = ss.Uy;
     const float a0 = ss.U0 * p.inv_tau, ax = p.v0 * Ux * p.inv_tau, ay = p.v0 * Uy * p.inv_tau;
     float* out = fout + (long long)y * p.pitch + x;
     o3_collide_all<Def>(Orb{}, d, e, ss.nd, a0, ax, ay, out, p.plane, p);

@@ -11,20 +11,14 @@
 // where W_il is the dual basis of twenty centred monomials phi_l (host table,
 // rlbm_stencil.h) and dmu_l the deviation, per unit density, of the moment
 // of phi_l under the Maxwell-Juttner distribution (Eq. 4-6, 43-44) from its
-// value at rest and T = T_R.  (*) is the unique w_i times a polynomial of
-// degree <= 3 whose moments against every such polynomial equal the
-// continuum ones, i.e. the third-order truncation.  The moments are, with
-// h = (e + P)/n = m R + 4T, R = K1/K2(m/T), U_z = 0 and t = p0 - c:
-//   <1> = R/m, <p^a> = U^a, <p^a p^b> = h U^a U^b - T eta^ab,
-//   <p^a p^b p^c> = A3 U^a U^b U^c + B3 (eta^ab U^c + eta^ac U^b + eta^bc U^a),
-//   A3 = m^2 + 6 T h, B3 = -T h.
-// dmu is written out in the small quantities dU = U0 - 1, dT = T - 1,
-// dR = R - R(m), U_x, U_y, so the FP32 path evaluates it without
-// cancellation (every term is a deviation times an O(1) factor).
+// value at rest and T = T_R (o3_deviations, rlbm_o3.cuh).  (*) is the unique
+// w_i times a polynomial of degree <= 3 whose moments against every such
+// polynomial equal the continuum ones, i.e. the third-order truncation.
 //
 // Kernels: two passes over the populations per site (moments, then relax and
 // store), table rows read with vector loads, as the generic 3D kernels.
 #include "rlbm_kernels.cuh"
+#include "rlbm_o3.cuh"
 
 namespace rlbm {
 namespace {
@@ -66,38 +60,9 @@ __device__ __forceinline__ long long source_o3(const O3Params& p, int i, int x, 
 
 // n dmu_l (kO3Mono order) from the FP64 site macros; R_t = double or float.
 template <typename R_t>
-__device__ __forceinline__ void dmu_o3(const Macro<double>& md, const O3Params& p, R_t* e) {
-  const R_t m = (R_t)p.sc.mbar, c = (R_t)p.c;
-  const R_t n = (R_t)md.n, U0 = (R_t)md.U0, Ux = (R_t)md.Ux, Uy = (R_t)md.Uy;
-  const R_t dU = (R_t)md.dU, dR = (R_t)md.dR, dT = (R_t)(md.T - 1.0), T = (R_t)md.T;
-  const R_t h = m * (R_t)md.R + R_t(4) * T;
-  const R_t dh = m * dR + R_t(4) * dT;
-  const R_t Th = T * h;
-  const R_t Am = m * m + R_t(6) * Th;          // A3
-  const R_t hU = h * U0 - c;
-  const R_t s = dT * hU + h * dU + dh;          // T (h U0 - c) - (h_r - c)
-  const R_t q = Am * U0 - c * h;
-  const R_t im = R_t(1) / m;
-  e[0] = n * dR * im;                           // 1
-  e[1] = n * (dU - c * dR * im);                // t
-  e[2] = n * Ux;                                // px
-  e[3] = n * Uy;                                // py
-  e[4] = n * Ux * hU;                           // t px
-  e[5] = n * Uy * hU;                           // t py
-  e[6] = n * (h * Ux * Ux + dT);                // px^2
-  e[7] = n * (h * Uy * Uy + dT);                // py^2
-  e[8] = n * h * Ux * Uy;                       // px py
-  e[9] = n * dT;                                // pz^2
-  e[10] = n * (q * Ux * Ux + s);                // t px^2
-  e[11] = n * (q * Uy * Uy + s);                // t py^2
-  e[12] = n * q * Ux * Uy;                      // t px py
-  e[13] = n * Ux * (Am * Ux * Ux + R_t(3) * Th);   // px^3
-  e[14] = n * Uy * (Am * Ux * Ux + Th);         // px^2 py
-  e[15] = n * Ux * (Am * Uy * Uy + Th);         // px py^2
-  e[16] = n * Uy * (Am * Uy * Uy + R_t(3) * Th);   // py^3
-  e[17] = n * s;                                // t pz^2
-  e[18] = n * Th * Ux;                          // px pz^2
-  e[19] = n * Th * Uy;                          // py pz^2
+__device__ __forceinline__ void dmu_o3(const Macro<double>& md, const O3Params& p, R_t (&e)[kO3Mono]) {
+  o3_deviations<R_t>((R_t)p.sc.mbar, (R_t)p.c, (R_t)md.n, (R_t)md.U0, (R_t)md.Ux, (R_t)md.Uy, (R_t)md.dU,
+                     (R_t)md.dR, (R_t)(md.T - 1.0), (R_t)md.T, (R_t)md.R, e);
 }
 
 // Macros of an init field (n, u, T) in the form the site solve returns.
