@@ -138,3 +138,22 @@ def test_quadratures_agree_at_third_order():
     # measured with the oracle on the same setup: 4.4e-5 and 2.0e-3
     assert d3 < 1e-4, d3
     assert d2 > 20 * d3, (d2, d3)
+
+
+@pytest.mark.parametrize("name,m,dtype,tol", [("O3_B", 2.5, "f64", 1e-12), ("O3_C", 4.0, "f64", 1e-12),
+                                              ("O3_A", 2.0, "f32", 1e-5)])
+def test_library_stencils_against_oracle(name, m, dtype, tol):
+    # the third-order stencil library (halo 4-5, 133-149 folded populations)
+    # on the generic kernels
+    from paper_1703_04605_gb300 import quadrature_window, stencils
+    groups = list(getattr(stencils, name))
+    lo, hi, _ = quadrature_window(groups, m)
+    st = dict(groups=groups, m=m, v0=0.5 * (lo + hi))
+    f = smooth_fields(13, 11, seed=68, dn=0.05, dT=0.05, du=0.08)
+    got, info = run_gpu(st, 0.8, f, dtype, 3)
+    assert info["order"] == 3 and info["kernel"] == 0
+    lat = oracle_lattice(st, 0.8, f["n"].shape)
+    lat.init(f["n"], f["ux"], f["uy"], f["T"])
+    lat.step(3)
+    e = errors(got, lat.macros())
+    assert max(e.values()) < tol, e
