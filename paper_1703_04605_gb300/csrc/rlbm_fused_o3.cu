@@ -187,9 +187,13 @@ __global__ void __launch_bounds__(128, 3) fused_o3_kernel(const __grid_constant_
 
 }  // namespace
 
-cudaError_t launch_fused_o3(const FusedO3Params& p, const void* fin, void* fout, cudaStream_t s) {
+cudaError_t launch_fused_o3(int kind, const FusedO3Params& p, const void* fin, void* fout, cudaStream_t s) {
   const unsigned grid = (unsigned)(((long long)p.Nx * p.Ny + 127) / 128);
-  fused_o3_kernel<StencilO3M5><<<grid, 128, 0, s>>>(p, static_cast<const float*>(fin), static_cast<float*>(fout));
+  const float* f = static_cast<const float*>(fin);
+  float* g = static_cast<float*>(fout);
+  if (kind == 5) fused_o3_kernel<StencilO3M5><<<grid, 128, 0, s>>>(p, f, g);
+  else if (kind == 6) fused_o3_kernel<StencilO3D><<<grid, 128, 0, s>>>(p, f, g);
+  else fused_o3_kernel<StencilO3E><<<grid, 128, 0, s>>>(p, f, g);
   return cudaGetLastError();
 }
 

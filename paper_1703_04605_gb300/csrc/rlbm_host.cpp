@@ -165,11 +165,11 @@ static void fill_fused(rlbm_ctx* c, double nref) {
   f.err = c->d_err;
 }
 
-// Does the compiled third-order kernel serve this context (FP32, the
-// compiled groups in the host's population order, Nx, Ny >= halo)?
-static bool fused_o3_matches(const rlbm_ctx* c) {
-  using D = StencilO3M5;
-  if (c->dtype != RLBM_F32 || c->Q != D::Q || c->sb3->halo != D::halo) return false;
+// Compiled third-order kernels (rlbm_fused_o3.cu): kind 5, 6, 7 for the
+// groups of StencilO3M5, StencilO3D, StencilO3E.
+template <class D>
+static bool fused_o3_is(const rlbm_ctx* c) {
+  if (c->Q != D::Q || c->sb3->halo != D::halo) return false;
   for (int k = 0; k < 11; ++k)
     if (c->sb3->groups[k] != D::groups[k]) return false;
   for (int i = 0; i < D::Q; ++i) {
@@ -177,11 +177,28 @@ static bool fused_o3_matches(const rlbm_ctx* c) {
     if (fp.nx != D::F.nx[i] || fp.ny != D::F.ny[i] || fp.group != D::F.grp[i] || fp.mult != D::F.mult[i])
       return false;
   }
-  return c->Nx >= D::halo && c->Ny >= D::halo;
+  return true;
+}
+
+// Which compiled third-order kernel serves this context (0: none): FP32,
+// compiled groups in the host's population order, Nx, Ny >= halo.
+static int fused_o3_kind(const rlbm_ctx* c) {
+  if (c->dtype != RLBM_F32 || c->Nx < c->sb3->halo || c->Ny < c->sb3->halo) return 0;
+  if (fused_o3_is<StencilO3M5>(c)) return 5;
+  if (fused_o3_is<StencilO3D>(c)) return 6;
+  if (fused_o3_is<StencilO3E>(c)) return 7;
+  return 0;
+}
+
+template <class D>
+static void fill_orbits_o3(const StencilBuildO3& sb, FusedO3Params& f) {
+  for (int k = 0; k < D::O.K; ++k) {
+    const auto& row = sb.rows[D::O.idx[k][0]];
+    for (int l = 0; l <= kO3Mono; ++l) f.ow[k][l] = split(row[9 + l]);
+  }
 }
 
 static void fill_fused_o3(rlbm_ctx* c, double nref) {
-  using D = StencilO3M5;
   FusedO3Params& f = *c->fo3;
   std::memset(&f, 0, sizeof f);
   const StencilBuildO3& sb = *c->sb3;
@@ -204,10 +221,9 @@ static void fill_fused_o3(rlbm_ctx* c, double nref) {
   f.mb64 = sb.mbar;
   for (int g = 0; g < 11; ++g)
     for (int q = 0; q < 5; ++q) f.gm[g][q] = split(sb.gm[g][q]);
-  for (int k = 0; k < D::O.K; ++k) {
-    const auto& row = sb.rows[D::O.idx[k][0]];
-    for (int l = 0; l <= kO3Mono; ++l) f.ow[k][l] = split(row[9 + l]);
-  }
+  if (c->fused == 5) fill_orbits_o3<StencilO3M5>(sb, f);
+  else if (c->fused == 6) fill_orbits_o3<StencilO3D>(sb, f);
+  else fill_orbits_o3<StencilO3E>(sb, f);
   f.rt64 = c->d_rt64;
   f.rt32 = c->d_rt32;
   f.err = c->d_err;
@@ -351,8 +367,8 @@ static rlbm_status create_o3(const rlbm_stencil* st, double m, double tau, int N
   p.tab64 = c->d_tab64;
   p.tab32 = c->d_tab32;
   p.err = c->d_err;
-  if (fused_o3_matches(c.get())) {
-    c->fused = 5;
+  c->fused = fused_o3_kind(c.get());
+  if (c->fused) {
     c->fo3.reset(new FusedO3Params);
     fill_fused_o3(c.get(), 1.0);
   }
@@ -523,7 +539,8 @@ rlbm_status rlbm_step(rlbm_ctx* c, int nsteps) {
     void* fout = c->buf[1 - c->cur];
     cudaError_t e;
     if (c->order == 3)
-      e = c->fo3 ? launch_fused_o3(*c->fo3, fin, fout, c->stream) : launch_step_o3(c->dtype, *c->o3, fin, fout, c->stream);
+      e = c->fo3 ? launch_fused_o3(c->fused, *c->fo3, fin, fout, c->stream)
+                 : launch_step_o3(c->dtype, *c->o3, fin, fout, c->stream);
     else if (c->dtype == RLBM_F64) e = launch_step_f64(*c->p64, fin, fout, c->qb, c->stream);
     else if (c->fused) {
       const bool bf = c->dtype == RLBM_BF16_DEV;

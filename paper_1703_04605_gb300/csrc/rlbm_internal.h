@@ -190,7 +190,9 @@ struct FusedO3Params {
   unsigned* err;
 };
 
-cudaError_t launch_fused_o3(const FusedO3Params& p, const void* fin, void* fout, cudaStream_t s);
+// kind 5, 6, 7: groups {1,2,5,6,7,9,10,11,12,13,15}, {2,3,5,6,7,8,9,10,11,13,15},
+// {1,2,3,6,7,8,9,10,11,13,15}
+cudaError_t launch_fused_o3(int kind, const FusedO3Params& p, const void* fin, void* fout, cudaStream_t s);
 
 cudaError_t launch_step_o3(rlbm_dtype dt, const O3Params& p, const void* fin, void* fout, cudaStream_t s);
 cudaError_t launch_init_o3(rlbm_dtype dt, const O3Params& p, FieldPtrs f, void* cur, void* prev, cudaStream_t s);

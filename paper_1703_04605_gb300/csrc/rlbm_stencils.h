@@ -270,6 +270,8 @@ struct StencilO3Def {
   static_assert(orbits_cover(F, O), "reflection orbits must partition the folded stencil");
 };
 
-using StencilO3M5 = StencilO3Def<1, 2, 5, 6, 7, 9, 10, 11, 12, 13, 15>;   // m/T_R = 5
+using StencilO3M5 = StencilO3Def<1, 2, 5, 6, 7, 9, 10, 11, 12, 13, 15>;   // m/T_R in [4.75, 5.19]
+using StencilO3D = StencilO3Def<2, 3, 5, 6, 7, 8, 9, 10, 11, 13, 15>;    // m/T_R in [4.75, 8]
+using StencilO3E = StencilO3Def<1, 2, 3, 6, 7, 8, 9, 10, 11, 13, 15>;    // m/T_R in [6.25, 14]
 
 }  // namespace rlbm

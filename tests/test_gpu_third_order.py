@@ -140,18 +140,20 @@ def test_quadratures_agree_at_third_order():
     assert d2 > 20 * d3, (d2, d3)
 
 
-@pytest.mark.parametrize("name,m,dtype,tol", [("O3_B", 2.5, "f64", 1e-12), ("O3_C", 4.0, "f64", 1e-12),
-                                              ("O3_A", 2.0, "f32", 1e-5)])
-def test_library_stencils_against_oracle(name, m, dtype, tol):
-    # the third-order stencil library (halo 4-5, 133-149 folded populations)
-    # on the generic kernels
+@pytest.mark.parametrize("name,m,dtype,tol,kernel", [("O3_B", 2.5, "f64", 1e-12, 0), ("O3_C", 4.0, "f64", 1e-12, 0),
+                                                     ("O3_A", 2.0, "f32", 1e-5, 0), ("O3_D", 6.0, "f32", 1e-5, 6),
+                                                     ("O3_E", 8.0, "f32", 1e-5, 7)])
+def test_library_stencils_against_oracle(name, m, dtype, tol, kernel):
+    # the third-order stencil library: halo 4-5 sets (133-149 folded
+    # populations) on the generic kernels, the halo-3 sets D and E on their
+    # compiled FP32 kernels
     from paper_1703_04605_gb300 import quadrature_window, stencils
     groups = list(getattr(stencils, name))
     lo, hi, _ = quadrature_window(groups, m)
     st = dict(groups=groups, m=m, v0=0.5 * (lo + hi))
     f = smooth_fields(13, 11, seed=68, dn=0.05, dT=0.05, du=0.08)
     got, info = run_gpu(st, 0.8, f, dtype, 3)
-    assert info["order"] == 3 and info["kernel"] == 0
+    assert info["order"] == 3 and info["kernel"] == kernel
     lat = oracle_lattice(st, 0.8, f["n"].shape)
     lat.init(f["n"], f["ux"], f["uy"], f["T"])
     lat.step(3)
