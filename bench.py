@@ -605,7 +605,13 @@ def run_third_order(args):
             pg.barrier()
         torch.cuda.synchronize()
 
-    st = W.STENCIL_O3
+    if args.mass is None:
+        st = W.STENCIL_O3
+    else:
+        from paper_1703_04605_gb300 import quadrature_window, stencils
+        groups, mb = stencils.choose(args.mass, order=3)
+        lo, hi, _ = quadrature_window(groups, mb)
+        st = dict(groups=groups, m=mb, v0=0.5 * (lo + hi))
     N = args.side
     f = W.random_flow(N)
     stream = torch.cuda.Stream()
@@ -656,15 +662,16 @@ def run_third_order(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "random_flow_o3_%d: %d^2 periodic random flow (n,T = 1+0.01 g, u = 0.05 g, " % (N, N) +
-                                   "g Gaussian-smoothed width 8), m/T_R=5, tau=0.8, third-order stencil "
-                                   "G1,G2,G5,G6,G7,G9,G10,G11,G12,G13,G15 (Q=100 folded), v0=0.27438",
+                                   "g Gaussian-smoothed width 8), m/T_R=%g, tau=0.8, third-order stencil " % st["m"] +
+                                   "G" + ",G".join(str(g) for g in st["groups"]) +
+                                   " (Q=%d folded), v0=%.6g" % (info["Q"], st["v0"]),
                        "sites": int(sites), "Q": info["Q"], "order": info["order"], "l2": "inputs larger than L2"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": (profiled_traffic("fused_o3_kernel_random_flow_o3_4096.md", O3_SOURCES)
-                                     if info["kernel"] == 5 and N == N_SIDE else None),
-                         "kernel": ("fused_o3_kernel<StencilO3Def<1,2,5,6,7,9,10,11,12,13,15>>"
-                                    if info["kernel"] == 5 else "step_o3_kernel<float>"),
+                                     if info["kernel"] == 5 and N == N_SIDE and args.mass is None else None),
+                         "kernel": ("fused_o3_kernel<StencilO3Def<%s>>" % ",".join(str(g) for g in sorted(st["groups"]))
+                                    if info["kernel"] >= 5 else "step_o3_kernel<float>"),
                          "bytes_per_site": info["bytes_per_site"]},
             "f64": {"MLUPS": sites / (ms64 / 1e3) / 1e6, "ms_per_step": ms64, "steps": k64,
                     "frac_hbm": info64["bytes_per_site"] * sites / (ms64 / 1e3) / 1e9 / peak},
@@ -683,6 +690,8 @@ def main():
     ap.add_argument("--side", type=int, default=N_SIDE,
                     help="random_flow: time a side x side crop of the 4096^2 field; random3d: a side^3 lattice "
                          "instead of 256^3 (profiling of small cases)")
+    ap.add_argument("--mass", type=float, default=None,
+                    help="third_order only: m/T_R of the stencil library's set to time (default: the m/T_R = 5 set)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the accuracy check and the other dtypes")

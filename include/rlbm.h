@@ -96,12 +96,15 @@ typedef struct {
   size_t device_bytes;      /* device memory owned by the context            */
   int kernel;               /* step kernel: 0 generic; 1..4 compiled for the
                                stencils {5,12,14,17,21,26}, {1..6},
-                               {1,14,49,51,60,70}, {3,9,10,14,17,21}; 5..7
+                               {1,14,49,51,60,70}, {3,9,10,14,17,21}; 5..10
                                the compiled third-order stencils
                                {1,2,5,6,7,9,10,11,12,13,15},
                                {2,3,5,6,7,8,9,10,11,13,15},
-                               {1,2,3,6,7,8,9,10,11,13,15} (FP32 storage,
-                               lattice at least a halo wide)                   */
+                               {1,2,3,6,7,8,9,10,11,13,15},
+                               {8,15,20,24,26,27,28,30,36,37,42},
+                               {4,10,15,20,24,26,27,28,30,36,37},
+                               {4,8,14,15,16,17,18,21,22,23,26} (FP32
+                               storage, lattice at least a halo wide)          */
   int order;                /* expansion order of f^eq: 2 or 3               */
 } rlbm_info;
 

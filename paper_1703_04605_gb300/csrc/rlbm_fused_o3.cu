@@ -156,8 +156,16 @@ __device__ __forceinline__ void o3_collide_all(std::integer_sequence<int, Ks...>
   (o3_collide_orbit<Def, Ks>(d, e, nd, a0, ax, ay, out, plane, p), ...);
 }
 
+// Resident blocks of 128 threads per SM: three (168 registers, no spills)
+// up to Q = 104; the larger halo-4/5 sets take 255 registers at two blocks
+// (36-80 bytes spilled), still about twice the generic kernel.
 template <class Def>
-__global__ void __launch_bounds__(128, 3) fused_o3_kernel(const __grid_constant__ FusedO3Params p,
+constexpr int o3_min_blocks() {
+  return Def::Q <= 104 ? 3 : 2;
+}
+
+template <class Def>
+__global__ void __launch_bounds__(128, o3_min_blocks<Def>()) fused_o3_kernel(const __grid_constant__ FusedO3Params p,
                                                           const float* __restrict__ fin, float* __restrict__ fout) {
   static_assert(Def::O.K <= kMaxOrbO3, "orbit constants exceed FusedO3Params::ow");
   const int site = blockIdx.x * blockDim.x + threadIdx.x;
@@ -193,7 +201,10 @@ cudaError_t launch_fused_o3(int kind, const FusedO3Params& p, const void* fin, v
   float* g = static_cast<float*>(fout);
   if (kind == 5) fused_o3_kernel<StencilO3M5><<<grid, 128, 0, s>>>(p, f, g);
   else if (kind == 6) fused_o3_kernel<StencilO3D><<<grid, 128, 0, s>>>(p, f, g);
-  else fused_o3_kernel<StencilO3E><<<grid, 128, 0, s>>>(p, f, g);
+  else if (kind == 7) fused_o3_kernel<StencilO3E><<<grid, 128, 0, s>>>(p, f, g);
+  else if (kind == 8) fused_o3_kernel<StencilO3A><<<grid, 128, 0, s>>>(p, f, g);
+  else if (kind == 9) fused_o3_kernel<StencilO3B><<<grid, 128, 0, s>>>(p, f, g);
+  else fused_o3_kernel<StencilO3C><<<grid, 128, 0, s>>>(p, f, g);
   return cudaGetLastError();
 }
 

@@ -165,8 +165,9 @@ static void fill_fused(rlbm_ctx* c, double nref) {
   f.err = c->d_err;
 }
 
-// Compiled third-order kernels (rlbm_fused_o3.cu): kind 5, 6, 7 for the
-// groups of StencilO3M5, StencilO3D, StencilO3E.
+// Compiled third-order kernels (rlbm_fused_o3.cu): kind 5..10 for the
+// groups of StencilO3M5, StencilO3D, StencilO3E, StencilO3A, StencilO3B,
+// StencilO3C.
 template <class D>
 static bool fused_o3_is(const rlbm_ctx* c) {
   if (c->Q != D::Q || c->sb3->halo != D::halo) return false;
@@ -187,6 +188,9 @@ static int fused_o3_kind(const rlbm_ctx* c) {
   if (fused_o3_is<StencilO3M5>(c)) return 5;
   if (fused_o3_is<StencilO3D>(c)) return 6;
   if (fused_o3_is<StencilO3E>(c)) return 7;
+  if (fused_o3_is<StencilO3A>(c)) return 8;
+  if (fused_o3_is<StencilO3B>(c)) return 9;
+  if (fused_o3_is<StencilO3C>(c)) return 10;
   return 0;
 }
 
@@ -221,9 +225,14 @@ static void fill_fused_o3(rlbm_ctx* c, double nref) {
   f.mb64 = sb.mbar;
   for (int g = 0; g < 11; ++g)
     for (int q = 0; q < 5; ++q) f.gm[g][q] = split(sb.gm[g][q]);
-  if (c->fused == 5) fill_orbits_o3<StencilO3M5>(sb, f);
-  else if (c->fused == 6) fill_orbits_o3<StencilO3D>(sb, f);
-  else fill_orbits_o3<StencilO3E>(sb, f);
+  switch (c->fused) {
+    case 5: fill_orbits_o3<StencilO3M5>(sb, f); break;
+    case 6: fill_orbits_o3<StencilO3D>(sb, f); break;
+    case 7: fill_orbits_o3<StencilO3E>(sb, f); break;
+    case 8: fill_orbits_o3<StencilO3A>(sb, f); break;
+    case 9: fill_orbits_o3<StencilO3B>(sb, f); break;
+    default: fill_orbits_o3<StencilO3C>(sb, f); break;
+  }
   f.rt64 = c->d_rt64;
   f.rt32 = c->d_rt32;
   f.err = c->d_err;

@@ -174,7 +174,7 @@ struct O3Params {
 // the compiled stencil, ow[K] holds the representative (+n_x, +n_y)
 // population's wr_i and its twenty dual-basis values W_il (host table row
 // entries 9..29, multiplicity included) as hi/lo pairs.
-constexpr int kMaxOrbO3 = 40;
+constexpr int kMaxOrbO3 = 44;
 struct FusedO3Params {
   int Nx, Ny;
   long long pitch, plane;
@@ -191,7 +191,8 @@ struct FusedO3Params {
 };
 
 // kind 5, 6, 7: groups {1,2,5,6,7,9,10,11,12,13,15}, {2,3,5,6,7,8,9,10,11,13,15},
-// {1,2,3,6,7,8,9,10,11,13,15}
+// {1,2,3,6,7,8,9,10,11,13,15}; 8, 9, 10: {8,15,20,24,26,27,28,30,36,37,42},
+// {4,10,15,20,24,26,27,28,30,36,37}, {4,8,14,15,16,17,18,21,22,23,26}
 cudaError_t launch_fused_o3(int kind, const FusedO3Params& p, const void* fin, void* fout, cudaStream_t s);
 
 cudaError_t launch_step_o3(rlbm_dtype dt, const O3Params& p, const void* fin, void* fout, cudaStream_t s);

@@ -273,5 +273,8 @@ struct StencilO3Def {
 using StencilO3M5 = StencilO3Def<1, 2, 5, 6, 7, 9, 10, 11, 12, 13, 15>;   // m/T_R in [4.75, 5.19]
 using StencilO3D = StencilO3Def<2, 3, 5, 6, 7, 8, 9, 10, 11, 13, 15>;    // m/T_R in [4.75, 8]
 using StencilO3E = StencilO3Def<1, 2, 3, 6, 7, 8, 9, 10, 11, 13, 15>;    // m/T_R in [6.25, 14]
+using StencilO3A = StencilO3Def<8, 15, 20, 24, 26, 27, 28, 30, 36, 37, 42>;  // m/T_R in [1.875, 2.25]
+using StencilO3B = StencilO3Def<4, 10, 15, 20, 24, 26, 27, 28, 30, 36, 37>;  // m/T_R in [2.0, 3.5]
+using StencilO3C = StencilO3Def<4, 8, 14, 15, 16, 17, 18, 21, 22, 23, 26>;   // m/T_R in [3.25, 5.0]
 
 }  // namespace rlbm

@@ -141,12 +141,13 @@ def test_quadratures_agree_at_third_order():
 
 
 @pytest.mark.parametrize("name,m,dtype,tol,kernel", [("O3_B", 2.5, "f64", 1e-12, 0), ("O3_C", 4.0, "f64", 1e-12, 0),
-                                                     ("O3_A", 2.0, "f32", 1e-5, 0), ("O3_D", 6.0, "f32", 1e-5, 6),
+                                                     ("O3_A", 2.0, "f32", 1e-5, 8), ("O3_B", 2.5, "f32", 1e-5, 9),
+                                                     ("O3_C", 4.0, "f32", 1e-5, 10), ("O3_D", 6.0, "f32", 1e-5, 6),
                                                      ("O3_E", 8.0, "f32", 1e-5, 7)])
 def test_library_stencils_against_oracle(name, m, dtype, tol, kernel):
-    # the third-order stencil library: halo 4-5 sets (133-149 folded
-    # populations) on the generic kernels, the halo-3 sets D and E on their
-    # compiled FP32 kernels
+    # the third-order stencil library on the FP64 generic kernel and on the
+    # compiled FP32 kernels of its five sets (halo 3-5, 99-149 folded
+    # populations)
     from paper_1703_04605_gb300 import quadrature_window, stencils
     groups = list(getattr(stencils, name))
     lo, hi, _ = quadrature_window(groups, m)
