@@ -218,10 +218,15 @@ typedef struct {
                                stencils {5,12,14,17,21,26}, {1..6},
                                {1,14,49,51,60,70}, {3,9,10,14,17,21} (FP32
                                storage, lattice at least a halo wide)         */
+  int order;                /* expansion order of f^eq: 2 or 3 (eleven groups:
+                               the thirty-monomial third-order equilibrium on
+                               the generic kernels)                           */
 } rlbm3_info;
 
 /* As rlbm_create, with Nz >= 1; dtype RLBM_F64 or RLBM_F32 (ENOTSUP for
- * BF16).  More than 160 populations: ENOTSUP. */
+ * BF16).  Six groups: the second-order equilibrium (App. A-B); eleven: the
+ * third-order one, exact to the third moment T^abc (generic kernels).  More
+ * than 160 unfolded populations: ENOTSUP. */
 rlbm_status rlbm3_create(const rlbm_stencil* st, double m, double tau, int Nx, int Ny, int Nz,
                          rlbm_dtype dtype, void* cuda_stream, rlbm_ctx3** out);
 

@@ -44,7 +44,7 @@ class Info3(C.Structure):
     _fields_ = [("Nx", C.c_int), ("Ny", C.c_int), ("Nz", C.c_int), ("Q", C.c_int), ("halo", C.c_int),
                 ("dtype", C.c_int), ("m", C.c_double), ("tau", C.c_double), ("v0", C.c_double),
                 ("t", C.c_longlong), ("bytes_per_site", C.c_size_t), ("device_bytes", C.c_size_t),
-                ("kernel", C.c_int)]
+                ("kernel", C.c_int), ("order", C.c_int)]
 
 
 class RLBMError(RuntimeError):

@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "rlbm_o3_3d.h"
 #include "rlbm_stencil.h"
 #include "rlbm_stencils.h"
 
@@ -40,6 +41,12 @@ struct rlbm_ctx3 {
   int fused = 0;               // 0 generic kernel; 1..4: {5,12,14,17,21,26}, {1..6},
                                // {1,14,49,51,60,70}, {3,9,10,14,17,21} (FP32)
   Fused3Params fp{};
+  // third-order (eleven-group) stencils: the dual-basis tables and the
+  // kernel parameters (q.b mirrors p at every launch)
+  int order = 2;
+  double* d_w64 = nullptr;
+  float* d_w32 = nullptr;
+  Step3O3Params q{};
   std::string last_error;
 };
 
@@ -60,8 +67,8 @@ rlbm_status cuda_fail3(rlbm_ctx3* c, cudaError_t e, const char* where) {
 void release3(rlbm_ctx3* c) {
   if (c->buf[0] || c->buf[1]) cudaStreamSynchronize(c->stream);
   for (void* p : {c->buf[0], c->buf[1], (void*)c->d_err, (void*)c->d_rt64, (void*)c->d_rt32, (void*)c->d_shift, (void*)c->d_off,
-                  (void*)c->d_tab64,
-                  (void*)c->d_tab32, (void*)c->d_fields, (void*)c->d_out})
+                  (void*)c->d_tab64, (void*)c->d_tab32, (void*)c->d_fields, (void*)c->d_out, (void*)c->d_w64,
+                  (void*)c->d_w32})
     if (p) cudaFree(p);
   c->buf[0] = c->buf[1] = nullptr;
 }
@@ -136,7 +143,7 @@ void fill_fused3(rlbm_ctx3* c, double nref) {
 void set_reference3(rlbm_ctx3* c, double nref) {
   if (c->dtype == RLBM_F64) nref = 0.0;
   c->p.nref = nref;
-  c->p.b0ref = nref * c->sb.sb.b0ref1;
+  c->p.b0ref = c->order == 3 ? 0.0 : nref * c->sb.sb.b0ref1;
   for (int k = 0; k < 14; ++k) c->p.mref[k] = nref * c->sb.mref1[k];
   if (c->fused) fill_fused3(c, nref);
 }
@@ -174,8 +181,17 @@ rlbm_status rlbm3_create(const rlbm_stencil* st, double m, double tau, int Nx, i
   std::unique_ptr<rlbm_ctx3> c(new (std::nothrow) rlbm_ctx3);
   if (!c) return fail3(nullptr, RLBM_ENOMEM, "host allocation failed");
   std::string err;
-  rlbm_status s = build_stencil3d(st, m, &c->sb, &err);
-  if (s != RLBM_OK) return fail3(nullptr, s, err);
+  std::unique_ptr<StencilBuild3O3> s3;
+  if (st && st->ngroups == 11) {
+    s3.reset(new StencilBuild3O3);
+    rlbm_status s = build_stencil3d_o3(st, m, s3.get(), &err);
+    if (s != RLBM_OK) return fail3(nullptr, s, err);
+    c->sb = s3->base;
+    c->order = 3;
+  } else {
+    rlbm_status s = build_stencil3d(st, m, &c->sb, &err);
+    if (s != RLBM_OK) return fail3(nullptr, s, err);
+  }
   c->Nx = Nx;
   c->Ny = Ny;
   c->Nz = Nz;
@@ -221,6 +237,19 @@ rlbm_status rlbm3_create(const rlbm_stencil* st, double m, double tau, int Nx, i
             cudaMalloc(&c->d_tab64, t64.size() * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&c->d_tab32, t32.size() * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&c->d_fields, 5 * nsite * sizeof(double)) == cudaSuccess;
+  std::vector<double> w64;
+  std::vector<float> w32;
+  if (ok && c->order == 3) {
+    w64.assign((size_t)kRowW3 * Q, 0.0);
+    w32.assign((size_t)kRowW3 * Q, 0.0f);
+    for (int i = 0; i < Q; ++i)
+      for (int l = 0; l < kRowW3; ++l) {
+        w64[(size_t)i * kRowW3 + l] = s3->wrows[i][l];
+        w32[(size_t)i * kRowW3 + l] = (float)s3->wrows[i][l];
+      }
+    ok = cudaMalloc(&c->d_w64, w64.size() * sizeof(double)) == cudaSuccess &&
+         cudaMalloc(&c->d_w32, w32.size() * sizeof(float)) == cudaSuccess;
+  }
   if (!ok) {
     release3(c.get());
     return fail3(nullptr, RLBM_ENOMEM, "device allocation failed");
@@ -233,6 +262,11 @@ rlbm_status rlbm3_create(const rlbm_stencil* st, double m, double tau, int Nx, i
   if (e == cudaSuccess) e = cudaMemcpy(c->d_off, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_tab64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_tab32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && c->order == 3) {
+    e = cudaMemcpy(c->d_w64, w64.data(), w64.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_w32, w32.data(), w32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    c->device_bytes += w64.size() * 12;
+  }
   if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(unsigned));
   if (e != cudaSuccess) {
     release3(c.get());
@@ -255,7 +289,12 @@ rlbm_status rlbm3_create(const rlbm_stencil* st, double m, double tau, int Nx, i
   p.tab64 = c->d_tab64;
   p.tab32 = c->d_tab32;
   p.err = c->d_err;
-  c->fused = fused3_kind(c.get());
+  c->fused = c->order == 3 ? 0 : fused3_kind(c.get());
+  if (c->order == 3) {
+    c->q.c = s3->c;
+    c->q.w64 = c->d_w64;
+    c->q.w32 = c->d_w32;
+  }
   set_reference3(c.get(), 1.0);
   *out = c.release();
   return RLBM_OK;
@@ -285,7 +324,9 @@ rlbm_status rlbm3_init(rlbm_ctx3* c, const double* n, const double* ux, const do
     if (e != cudaSuccess) return cuda_fail3(c, e, "field upload");
   }
   Field3Ptrs fp{c->d_fields, c->d_fields + N, c->d_fields + 2 * N, c->d_fields + 3 * N, c->d_fields + 4 * N};
-  cudaError_t e = launch_init3d(c->dtype, c->p, fp, c->buf[0], c->buf[1], c->stream);
+  c->q.b = c->p;
+  cudaError_t e = c->order == 3 ? launch_init3d_o3(c->dtype, c->q, fp, c->buf[0], c->buf[1], c->stream)
+                                : launch_init3d(c->dtype, c->p, fp, c->buf[0], c->buf[1], c->stream);
   if (e != cudaSuccess) return cuda_fail3(c, e, "init launch");
   c->cur = 0;
   c->t = 0;
@@ -297,9 +338,12 @@ rlbm_status rlbm3_step(rlbm_ctx3* c, int nsteps) {
   if (!c) return RLBM_EINVAL;
   if (nsteps < 0) return fail3(c, RLBM_EINVAL, "nsteps < 0");
   if (!c->initialised) return fail3(c, RLBM_EINVAL, "rlbm3_init has not been called");
+  c->q.b = c->p;
   for (int k = 0; k < nsteps; ++k) {
-    cudaError_t e = c->fused ? launch_fused3d(c->fused, c->fp, c->buf[c->cur], c->buf[1 - c->cur], c->stream)
-                             : launch_step3d(c->dtype, c->p, c->buf[c->cur], c->buf[1 - c->cur], c->stream);
+    cudaError_t e;
+    if (c->order == 3) e = launch_step3d_o3(c->dtype, c->q, c->buf[c->cur], c->buf[1 - c->cur], c->stream);
+    else if (c->fused) e = launch_fused3d(c->fused, c->fp, c->buf[c->cur], c->buf[1 - c->cur], c->stream);
+    else e = launch_step3d(c->dtype, c->p, c->buf[c->cur], c->buf[1 - c->cur], c->stream);
     if (e != cudaSuccess) return cuda_fail3(c, e, "step launch");
     c->cur = 1 - c->cur;
     ++c->t;
@@ -362,6 +406,7 @@ rlbm_status rlbm3_get_info(const rlbm_ctx3* c, rlbm3_info* info) {
   info->bytes_per_site = 2 * (size_t)c->Q * c->elem;
   info->device_bytes = c->device_bytes + c->out_cap * sizeof(double);
   info->kernel = c->fused;
+  info->order = c->order;
   return RLBM_OK;
 }
 

@@ -1,6 +1,7 @@
 // Native 3D lattices: the step on an Nx x Ny x Nz periodic lattice with the
 // paper's unfolded stencil (Table I orbits with signed n_z), for any six-group
-// second-order stencil (Sec. III C-D).  Per site (Eq. 16-20, 28, 49): pull,
+// second-order stencil (Sec. III C-D) and, with the thirty-monomial
+// third-order equilibrium (rlbm_o3_3d.h), for any eleven-group stencil.  Per site (Eq. 16-20, 28, 49): pull,
 // the 4 + 10 moments N^a, T^ab, the Landau frame T^a_b U^b = e U^a with all
 // three velocity components, n = U.N, T from e/n = 3T + m K1/K2(m/T),
 // the 14 projections of App. B (corrected), f^eq = n sum_k b_k w_i J_k(p_i)
@@ -14,7 +15,10 @@
 // in registers whatever Q is.  The site solve is FP64; FP64 storage holds f_i,
 // FP32 storage d_i = f_i - r_i with FP32 accumulation (as the generic 2D FP32
 // kernel).
+#include <utility>
+
 #include "rlbm_kernels.cuh"
+#include "rlbm_o3_3d.h"
 
 namespace rlbm {
 namespace {
@@ -420,6 +424,178 @@ __global__ void __launch_bounds__(128) moments3d_kernel(const __grid_constant__ 
   report(fl, p.err);
 }
 
+// ------------------------------------------------------------ third order
+// Site quantities of the third-order equilibrium (see rlbm_o3_3d.h and the
+// 2D form in rlbm_o3.cuh): with h = m R + 4T, A3 = m^2 + 6 T h, B3 = -T h,
+// the deviations from rest at T_R of the moments (per unit density) of
+// t^a p^s1 ... p^sr are
+//   r = 0:  a = 0: dR/m           a = 1: dU - c dR/m
+//   r = 1:  a = 0: U_s            a = 1: U_s (h U0 - c)
+//   r = 2:  a = 0: h U_s U_s' + d_ss' dT
+//           a = 1: (A3 U0 - c h) U_s U_s' + d_ss' (T (h U0 - c) - (h_r - c))
+//   r = 3:  A3 U_s U_s' U_s'' + T h (d_ss' U_s'' + d_ss'' U_s' + d_s's'' U_s)
+// (Eq. 4-6, 28-29, 43-44; eta^ab = -delta_ab on the spatial indices).
+template <typename R>
+struct O3Site3 {
+  R n, U[4], dU, dR, dT, m, c, h, Th, Am, hU, sdev, q;
+};
+
+template <int A, int I, int J, int K, typename R>
+__device__ __forceinline__ R o3dev3(const O3Site3<R>& s) {
+  constexpr int r = I + J + K;
+  constexpr int i1 = I > 0 ? 1 : (J > 0 ? 2 : 3);
+  constexpr int i2 = I > 1 ? 1 : (I + J > 1 ? 2 : 3);
+  constexpr int i3 = I > 2 ? 1 : (I + J > 2 ? 2 : 3);
+  if constexpr (r == 0) {
+    return A == 0 ? s.n * s.dR / s.m : s.n * (s.dU - s.c * s.dR / s.m);
+  } else if constexpr (r == 1) {
+    return A == 0 ? s.n * s.U[i1] : s.n * s.U[i1] * s.hU;
+  } else if constexpr (r == 2) {
+    const R uu = s.U[i1] * s.U[i2];
+    if constexpr (A == 0) return s.n * (s.h * uu + (i1 == i2 ? s.dT : R(0)));
+    else return s.n * (s.q * uu + (i1 == i2 ? s.sdev : R(0)));
+  } else {
+    R v = s.Am * s.U[i1] * s.U[i2] * s.U[i3];
+    if constexpr (i1 == i2) v += s.Th * s.U[i3];
+    if constexpr (i1 == i3) v += s.Th * s.U[i2];
+    if constexpr (i2 == i3) v += s.Th * s.U[i1];
+    return s.n * v;
+  }
+}
+
+template <typename R, int... L>
+__device__ __forceinline__ void o3_dev3_all(std::integer_sequence<int, L...>, const O3Site3<R>& s, R* e) {
+  ((e[L] = o3dev3<kO3Exp3.e[L][0], kO3Exp3.e[L][1], kO3Exp3.e[L][2], kO3Exp3.e[L][3], R>(s)), ...);
+}
+
+// e_l = n dmu_l of the thirty monomials from the FP64 site macros.
+template <typename R>
+__device__ __forceinline__ void o3_deviations3(const Macro3& o, double Rr, double mbar, double c, R* e) {
+  O3Site3<R> s;
+  const double Ua2 = o.Ux * o.Ux + o.Uy * o.Uy + o.Uz * o.Uz;
+  const double dU = Ua2 / (o.U0 + 1.0);                   // U0 - 1 without cancellation
+  const double dT = o.T - 1.0;
+  const double h = mbar * o.R + 4.0 * o.T;
+  const double dR = o.R - Rr;
+  const double dh = mbar * dR + 4.0 * dT;
+  const double Th = o.T * h;
+  const double Am = mbar * mbar + 6.0 * Th;
+  const double hU = h * o.U0 - c;
+  s.n = (R)o.n;
+  s.U[0] = (R)o.U0;
+  s.U[1] = (R)o.Ux;
+  s.U[2] = (R)o.Uy;
+  s.U[3] = (R)o.Uz;
+  s.dU = (R)dU;
+  s.dR = (R)dR;
+  s.dT = (R)dT;
+  s.m = (R)mbar;
+  s.c = (R)c;
+  s.h = (R)h;
+  s.Th = (R)Th;
+  s.Am = (R)Am;
+  s.hU = (R)hU;
+  s.sdev = (R)(dT * hU + h * dU + dh);                    // T (h U0 - c) - (h_r - c)
+  s.q = (R)(Am * o.U0 - c * h);
+  o3_dev3_all<R>(std::make_integer_sequence<int, kO3Mono3>{}, s, e);
+}
+
+template <typename A>
+__device__ __forceinline__ const A* wtab(const Step3O3Params& p);
+template <>
+__device__ __forceinline__ const double* wtab<double>(const Step3O3Params& p) { return p.w64; }
+template <>
+__device__ __forceinline__ const float* wtab<float>(const Step3O3Params& p) { return p.w32; }
+
+// Third-order step (generic over the stencil): pull and moments as
+// step3d_kernel, the same site solve, then f^eq_i - nref wr_i =
+// n_d wr_i + sum_l e_l W_il and the Anderson-Witting relaxation.
+template <typename S>
+__global__ void __launch_bounds__(128) step3d_o3_kernel(const __grid_constant__ Step3O3Params q,
+                                                        const S* __restrict__ fin, S* __restrict__ fout) {
+  const Step3Params& p = q.b;
+  const long long nsite = (long long)p.Nx * p.Ny * p.Nz;
+  const long long sidx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned fl = 0;
+  if (sidx < nsite) {
+    int x, y, z;
+    site3(sidx, p, x, y, z);
+    double md[14];
+    moments3<S>(p, fin, x, y, z, md);
+    Macro3 o;
+    if constexpr (sizeof(S) == 4) o = solve3_mixed(md, p.sc, p.rt64, p.rt32, fl);
+    else o = solve3(md, p.sc, p.rt64, fl);
+    S e[kO3Mono3];
+    o3_deviations3<S>(o, p.sc.Rr, p.sc.mbar, q.c, e);
+    const S dn = (S)(o.n - p.nref);
+    const S a0 = (S)(o.U0 * p.inv_tau), ax = (S)(o.Ux * p.inv_tau), ay = (S)(o.Uy * p.inv_tau),
+            az = (S)(o.Uz * p.inv_tau);
+    const S* tab = table<S>(p);
+    const S* wt = wtab<S>(q);
+    const bool in = interior3(p, x, y, z);
+    const long long here = at3(p, x, y, z);
+    S* out = fout + here;
+#pragma unroll 2
+    for (int i = 0; i < p.Q; ++i) {
+      const long long src = in ? here + __ldg(p.off + i) : source3(p, i, x, y, z);
+      const S f = __ldg(fin + (long long)i * p.plane + src);
+      S c[4];
+      ld4(tab + (long long)i * kRow3 + 28, c);               // p^a/p^0
+      S w[32];
+      const S* row = wt + (long long)i * kRowW3;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) ld4(row + 4 * j, w + 4 * j);
+      S feq = dn * __ldg(tab + (long long)i * kRow3 + 14);
+#pragma unroll
+      for (int l = 0; l < kO3Mono3; ++l) feq = fma_t(e[l], w[l], feq);
+      const S om = a0 - ax * c[0] - ay * c[1] - az * c[2];
+      __stcs(out + (long long)i * p.plane, fma_t(om, feq - f, f));
+    }
+  }
+  report(fl, p.err);
+}
+
+// f = f^eq(n, U, T) at third order: S_0 at the site, S_{-1} at x - n_i.
+template <typename S>
+__global__ void __launch_bounds__(128) init3d_o3_kernel(const __grid_constant__ Step3O3Params q, Field3Ptrs fd,
+                                                        S* __restrict__ cur, S* __restrict__ prev) {
+  const Step3Params& p = q.b;
+  const long long nsite = (long long)p.Nx * p.Ny * p.Nz;
+  const long long sidx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned fl = 0;
+  if (sidx < nsite) {
+    int x, y, z;
+    site3(sidx, p, x, y, z);
+    const double ux = fd.ux[sidx], uy = fd.uy[sidx], uz = fd.uz[sidx];
+    const double v2 = ux * ux + uy * uy + uz * uz;
+    if (!(v2 < 1.0)) fl |= ERR_LANDAU;
+    const double g = 1.0 / sqrt(1.0 - v2);
+    Macro3 o;
+    o.n = fd.n[sidx];
+    o.T = fd.T[sidx];
+    if (!(o.n > 0.0)) fl |= ERR_DENSITY;
+    if (!(o.T > 0.0)) fl |= ERR_EOS;
+    o.U0 = g;
+    o.Ux = g * ux;
+    o.Uy = g * uy;
+    o.Uz = g * uz;
+    o.R = ratio64(p.sc.mbar / o.T, p.rt64, fl);
+    double e[kO3Mono3];
+    o3_deviations3<double>(o, p.sc.Rr, p.sc.mbar, q.c, e);
+    const double dn = o.n - p.nref;
+    const long long here = at3(p, x, y, z);
+#pragma unroll 1
+    for (int i = 0; i < p.Q; ++i) {
+      double feq = dn * __ldg(p.tab64 + (long long)i * kRow3 + 14);
+#pragma unroll
+      for (int l = 0; l < kO3Mono3; ++l) feq = fma(e[l], __ldg(q.w64 + (long long)i * kRowW3 + l), feq);
+      cur[(long long)i * p.plane + here] = (S)feq;
+      prev[(long long)i * p.plane + source3(p, i, x, y, z)] = (S)feq;
+    }
+  }
+  report(fl, p.err);
+}
+
 unsigned grid3(const Step3Params& p) {
   return (unsigned)(((long long)p.Nx * p.Ny * p.Nz + 127) / 128);
 }
@@ -449,6 +625,23 @@ cudaError_t launch_moments3d(rlbm_dtype dt, const Step3Params& p, const void* pr
     moments3d_kernel<double><<<grid3(p), 128, 0, s>>>(p, static_cast<const double*>(prev), o);
   else
     moments3d_kernel<float><<<grid3(p), 128, 0, s>>>(p, static_cast<const float*>(prev), o);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step3d_o3(rlbm_dtype dt, const Step3O3Params& p, const void* fin, void* fout, cudaStream_t s) {
+  if (dt == RLBM_F64)
+    step3d_o3_kernel<double><<<grid3(p.b), 128, 0, s>>>(p, static_cast<const double*>(fin), static_cast<double*>(fout));
+  else
+    step3d_o3_kernel<float><<<grid3(p.b), 128, 0, s>>>(p, static_cast<const float*>(fin), static_cast<float*>(fout));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init3d_o3(rlbm_dtype dt, const Step3O3Params& p, Field3Ptrs f, void* cur, void* prev,
+                             cudaStream_t s) {
+  if (dt == RLBM_F64)
+    init3d_o3_kernel<double><<<grid3(p.b), 128, 0, s>>>(p, f, static_cast<double*>(cur), static_cast<double*>(prev));
+  else
+    init3d_o3_kernel<float><<<grid3(p.b), 128, 0, s>>>(p, f, static_cast<float*>(cur), static_cast<float*>(prev));
   return cudaGetLastError();
 }
 

@@ -734,6 +734,101 @@ rlbm_status build_stencil_o3(const rlbm_stencil* st, double m, StencilBuildO3* o
   return RLBM_OK;
 }
 
+rlbm_status build_stencil3d_o3(const rlbm_stencil* st, double m, StencilBuild3O3* out, std::string* err) {
+  // weights, v0 and site constants as for the folded third-order build
+  StencilBuildO3 f;
+  rlbm_status s = build_stencil_o3(st, m, &f, err);
+  if (s != RLBM_OK) return s;
+  for (int k = 0; k < 11; ++k) {
+    out->groups[k] = f.groups[k];
+    out->w_group[k] = f.w_group[k];
+  }
+  out->c = f.c;
+  StencilBuild& sb = out->base.sb;
+  sb.mbar = m;
+  sb.v0 = f.v0;
+  sb.sc = f.sc;
+  sb.cv_r = f.cv_r;
+  sb.halo = 0;
+  const double v0 = f.v0;
+  qf wq[11];
+  weights_q<11>(f.groups, m, v0, wq);
+  const qf mq = (qf)m;
+  qf k1, k2, k3;
+  bessel_k123_scaled(mq, &k1, &k2, &k3);
+  const qf c = mq * k2 / k1;
+  const qf wr1 = k1 / (k2 * mq);           // K1/K2(mbar)/mbar
+  struct PopQ {
+    qf p0, px, py, pz, w;
+  };
+  std::vector<PopQ> pq;
+  out->base.pops.clear();
+  out->base.halo = 0;
+  for (int k = 0; k < 11; ++k) {
+    const qf len2 = (qf)group_len2(f.groups[k]);
+    const qf gam = 1 / q_sqrt(1 - (qf)v0 * (qf)v0 * len2);
+    const qf p0 = mq * gam, ps = mq * gam * (qf)v0;
+    for (const auto& v : group_orbit(f.groups[k])) {   // lexicographic (n_x, n_y, n_z)
+      Pop3 q{};
+      q.group = k;
+      q.nx = v[0];
+      q.ny = v[1];
+      q.nz = v[2];
+      out->base.pops.push_back(q);
+      for (int a = 0; a < 3; ++a) out->base.halo = std::max(out->base.halo, std::abs(v[a]));
+      pq.push_back(PopQ{p0, ps * v[0], ps * v[1], ps * v[2], wq[k]});
+    }
+  }
+  const int Q = (int)pq.size();
+  if (Q > kMaxPop3) {
+    *err = "unfolded stencil has more populations than the compiled maximum (160)";
+    return RLBM_ENOTSUP;
+  }
+  const int K = kO3Mono3;
+  auto pw = [](qf x, int e) {
+    qf r = 1;
+    for (int j = 0; j < e; ++j) r *= x;
+    return r;
+  };
+  std::vector<qf> phi((size_t)Q * K), G((size_t)K * K, (qf)0);
+  for (int i = 0; i < Q; ++i) {
+    const qf t = pq[i].p0 - c;
+    for (int l = 0; l < K; ++l) {
+      const int* e = kO3Exp3.e[l];
+      phi[(size_t)i * K + l] = pw(t, e[0]) * pw(pq[i].px, e[1]) * pw(pq[i].py, e[2]) * pw(pq[i].pz, e[3]);
+    }
+    for (int a = 0; a < K; ++a)
+      for (int b = 0; b < K; ++b) G[(size_t)a * K + b] += pq[i].w * phi[(size_t)i * K + a] * phi[(size_t)i * K + b];
+  }
+  if (!invert_q(G, K)) {
+    *err = "singular third-order Gram matrix (the stencil is not third order)";
+    return RLBM_ENOQUAD;
+  }
+  qf mref[14] = {};
+  out->wrows.assign(Q, {});
+  for (int i = 0; i < Q; ++i) {
+    const PopQ& P = pq[i];
+    const qf mom[14] = {P.p0, P.px, P.py, P.pz, P.p0 * P.p0, P.p0 * P.px, P.p0 * P.py, P.p0 * P.pz,
+                        P.px * P.px, P.px * P.py, P.px * P.pz, P.py * P.py, P.py * P.pz, P.pz * P.pz};
+    Pop3& q = out->base.pops[i];
+    for (int k = 0; k < 14; ++k) {
+      q.c[k] = (double)mom[k];
+      mref[k] += P.w * wr1 * mom[k];
+    }
+    q.c[14] = (double)(P.w * wr1);
+    q.c[28] = (double)(P.px / P.p0);
+    q.c[29] = (double)(P.py / P.p0);
+    q.c[30] = (double)(P.pz / P.p0);
+    for (int l = 0; l < K; ++l) {
+      qf acc = 0;
+      for (int b = 0; b < K; ++b) acc += G[(size_t)l * K + b] * phi[(size_t)i * K + b];
+      out->wrows[i][l] = (double)(P.w * acc);
+    }
+  }
+  for (int k = 0; k < 14; ++k) out->base.mref1[k] = (double)mref[k];
+  return RLBM_OK;
+}
+
 rlbm_status build_stencil3d(const rlbm_stencil* st, double m, StencilBuild3* out, std::string* err) {
   rlbm_status s = build_stencil(st, m, &out->sb, err);
   if (s != RLBM_OK) return s;

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "rlbm_internal.h"
+#include "rlbm_o3_3d.h"
 
 namespace rlbm {
 
@@ -113,6 +114,20 @@ struct StencilBuildO3 {
 };
 
 rlbm_status build_stencil_o3(const rlbm_stencil* st, double m, StencilBuildO3* out, std::string* err);
+
+// Third-order stencil unfolded for 3D lattices: base.pops in the order of
+// build_stencil3d with c[0..13] the momentum products, c[14] the rest-frame
+// weight w_i K1/K2(mbar)/mbar and c[28..30] p^a/p^0; base.mref1 the moments of
+// that weight; wrows the dual basis of the thirty monomials of kO3Exp3.
+struct StencilBuild3O3 {
+  StencilBuild3 base;       // base.sb holds v0, mbar and the site constants
+  int groups[11];
+  double w_group[11];
+  double c;                 // centring shift mbar K2/K1(mbar)
+  std::vector<std::array<double, kRowW3>> wrows;
+};
+
+rlbm_status build_stencil3d_o3(const rlbm_stencil* st, double m, StencilBuild3O3* out, std::string* err);
 
 // Per-population constant table for the kernels (CT = float or double).
 template <typename CT>

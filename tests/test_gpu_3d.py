@@ -152,3 +152,54 @@ def test_conservation_and_t0():
     scale = abs(m0["T00"].sum())
     for k in ("N0", "T00", "T0x", "T0y", "T0z"):
         assert abs(m1[k].sum() - m0[k].sum()) < 1e-12 * scale, k
+
+
+# ---------------------------------------------------------------- third order
+def test_third_order_f64_against_oracle():
+    # eleven groups unfolded (159 populations), the thirty-monomial equilibrium
+    st = W.STENCIL_O3
+    f = smooth3(7, 6, 5, seed=37, dn=0.05, dT=0.05, du=0.06)
+    got, info = gpu3(st, 0.8, f, 3)
+    assert info["Q"] == 159 and info["order"] == 3 and info["kernel"] == 0
+    ref = oracle3(st, 0.8, f, 3)
+    e = errors3(got, ref)
+    assert max(e.values()) < 1e-12, e
+
+
+def test_third_order_f32_against_oracle():
+    st = W.STENCIL_O3
+    f = smooth3(8, 7, 6, seed=38, dn=0.05, dT=0.05, du=0.06)
+    got, info = gpu3(st, 0.8, f, 8, dtype="f32")
+    assert info["order"] == 3
+    ref = oracle3(st, 0.8, f, 8)
+    e = errors3(got, ref)
+    # per-population FP32 constants (as the generic FP32 kernels)
+    assert e["n"] < 1e-5 and e["T"] < 1e-5 and e["u"] < 1e-4, e
+
+
+def test_third_order_nz1_equals_folded_2d():
+    from paper_1703_04605_gb300 import Lattice
+    st = W.STENCIL_O3
+    f = smooth3(20, 18, 1, seed=39, dn=0.05, dT=0.05, du=0.06)
+    f["uz"] = np.zeros_like(f["uz"])
+    got, _ = gpu3(st, 0.9, f, 6)
+    with Lattice(st["groups"], st["m"], 0.9, 20, 18, dtype="f64", v0=st["v0"]) as lat:
+        lat.init(f["n"][0], f["ux"][0], f["uy"][0], f["T"][0])
+        lat.step(6)
+        ref2 = lat.moments()
+    for k in ("n", "T"):
+        assert np.max(np.abs(got[k][0] / ref2[k] - 1)) < 1e-12, k
+    for k in ("ux", "uy"):
+        assert np.max(np.abs(got[k][0] - ref2[k])) < 1e-13, k
+    assert np.max(np.abs(got["uz"])) < 1e-15
+
+
+def test_third_order_conservation():
+    from paper_1703_04605_gb300 import _abi as A
+    st = W.STENCIL_O3
+    f = smooth3(9, 8, 7, seed=40, dn=0.08, dT=0.08, du=0.06)
+    m0, _ = gpu3(st, 0.7, f, 0, mask=A.M_NVEC | A.M_TMN)
+    m1, _ = gpu3(st, 0.7, f, 10, mask=A.M_NVEC | A.M_TMN)
+    scale = abs(m0["T00"].sum())
+    for k in ("N0", "T00", "T0x", "T0y", "T0z"):
+        assert abs(m1[k].sum() - m0[k].sum()) < 1e-12 * scale, k
