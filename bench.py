@@ -202,6 +202,24 @@ def cpu_baseline_o3(seconds=10.0, side=24, procs=None):
                           len(res), side, min(r["steps"] for r in res), max(r["steps"] for r in res))}
 
 
+# FP64 paths are bound by the FP64 pipe.  FLOPs per site of the FP64 step
+# kernels on the benchmarked stencils, from ncu's FP64 instruction counts
+# (profiles/fp64_kernels_alu_1024.md); the peak is GB300's nominal FP64 rate.
+FP64_PEAK_TFLOPS = 1.25
+FP64_FLOP_PER_SITE = {"step_f64_kernel/5,12,14,17,21,26": 3271.0,
+                      "step_o3_kernel/1,2,5,6,7,9,10,11,12,13,15": 7352.0}
+
+
+def fp64_alu(mlups, key):
+    flop = FP64_FLOP_PER_SITE.get(key)
+    if flop is None:
+        return None
+    achieved = mlups * 1e6 * flop / 1e12
+    return {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+            "peak_kind": "nominal", "frac": achieved / FP64_PEAK_TFLOPS, "flop_per_site": flop,
+            "flop_source": "ncu FP64 instruction counts (profiles/fp64_kernels_alu_1024.md)"}
+
+
 def kernel_name(dtype, variant):
     stencil = {1: "5,12,14,17,21,26", 2: "1,2,3,4,5,6", 3: "1,14,49,51,60,70", 4: "3,9,10,14,17,21"}.get(variant)
     if dtype == "f64":
@@ -674,7 +692,9 @@ def run_third_order(args):
                                     if info["kernel"] >= 5 else "step_o3_kernel<float>"),
                          "bytes_per_site": info["bytes_per_site"]},
             "f64": {"MLUPS": sites / (ms64 / 1e3) / 1e6, "ms_per_step": ms64, "steps": k64,
-                    "frac_hbm": info64["bytes_per_site"] * sites / (ms64 / 1e3) / 1e9 / peak},
+                    "frac_hbm": info64["bytes_per_site"] * sites / (ms64 / 1e3) / 1e9 / peak,
+                    "alu": fp64_alu(sites / (ms64 / 1e3) / 1e6,
+                                    "step_o3_kernel/" + ",".join(str(g) for g in sorted(st["groups"])))},
             "error_vs_f64": err, "gpu_launches": args.steps, "clocks": clk.summary()}
     if not args.no_cpu_baseline and rank == 0:
         line["cpu_baseline"] = cpu_baseline_o3()
@@ -798,6 +818,8 @@ def main():
             if dt != "f64":
                 l2.step(nsteps - (args.warmup + k))
                 rec["error_vs_f64"] = dict(errs(l2.moments(), rm), steps=nsteps)
+            else:
+                rec["alu"] = fp64_alu(rec["MLUPS"], "step_f64_kernel/" + ",".join(str(g) for g in st["groups"]))
             by_dtype[dt] = rec
             l2.close()
 
