@@ -70,7 +70,8 @@ typedef enum { RLBM_F64 = 0, RLBM_F32 = 1, RLBM_BF16_DEV = 2 } rlbm_dtype;
  * is used as given (it must make every weight positive and v0 ||n_k|| < 1);
  * v0 == 0 selects the centre of the widest interval of v0 where all weights
  * are positive (Sec. III D).  Third-order contexts take FP64 or FP32 storage
- * (ENOTSUP for BF16_DEV), are not accepted by rlbm_batch_step, and their
+ * (ENOTSUP for BF16_DEV), join rlbm_batch_step on a compiled stencil with
+ * FP32 storage, and their
  * equilibrium is the unique w_i times a polynomial of degree <= 3 in p_i
  * whose moments up to rank 3 (N^a, T^ab, T^abc, Eq. 4-6) equal those of the
  * Maxwell-Juttner distribution. */
@@ -178,9 +179,10 @@ void rlbm_destroy(rlbm_ctx* ctx);
  * each on the first call for a batch with nsteps >= 42 (those steps count
  * towards nsteps) and caches the choice; rlbm_batch_tuning reports it.
  * Graphs are cached per batch and buffer parity; rlbm_init or rlbm_destroy of
- * a member drops them.  Requirements: every context initialised, FP32 or
- * BF16-deviation storage, a compiled stencil (rlbm_info.kernel != 0), all on
- * the same CUDA stream, no context listed twice.  Asynchronous on that stream
+ * a member drops them.  Requirements: every context initialised, a compiled
+ * stencil (rlbm_info.kernel != 0) with FP32 or BF16-deviation storage (FP32
+ * only at third order; second- and third-order contexts may be mixed), all
+ * on the same CUDA stream, no context listed twice.  Asynchronous on that stream
  * (a NULL stream is bridged to an internal stream with events).  Not
  * thread-safe against rlbm_step on the same contexts.  The paper has no
  * counterpart (it advances one lattice at a time).  Errors: EINVAL (violated

@@ -30,6 +30,10 @@ template <>
 const void* fused_kernel_fn<StencilE5>(bool);
 template <>
 const void* fused_kernel_fn<StencilS2>(bool);
+// The compiled third-order kernel of kind 5..10 (FusedO3Params, const float*
+// fin, float* fout), for graph kernel nodes; grid (Nx Ny + 127)/128, block
+// 128, no dynamic shared memory (rlbm_fused_o3.cu).
+const void* fused_o3_kernel_fn(int kind);
 // BF16 deviation storage: what = 0 init (fields -> coefficients, S_0, S_{-1}),
 // what = 1 read-out of the pull of prev.
 template <class Def>

@@ -208,4 +208,13 @@ cudaError_t launch_fused_o3(int kind, const FusedO3Params& p, const void* fin, v
   return cudaGetLastError();
 }
 
+const void* fused_o3_kernel_fn(int kind) {
+  if (kind == 5) return (const void*)&fused_o3_kernel<StencilO3M5>;
+  if (kind == 6) return (const void*)&fused_o3_kernel<StencilO3D>;
+  if (kind == 7) return (const void*)&fused_o3_kernel<StencilO3E>;
+  if (kind == 8) return (const void*)&fused_o3_kernel<StencilO3A>;
+  if (kind == 9) return (const void*)&fused_o3_kernel<StencilO3B>;
+  return (const void*)&fused_o3_kernel<StencilO3C>;
+}
+
 }  // namespace rlbm

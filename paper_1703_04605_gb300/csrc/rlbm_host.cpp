@@ -682,11 +682,13 @@ double rlbm_bessel_ratio(double zeta, int precision) { return ratio_eval_host(ze
 // Independent lattices advanced together: one CUDA graph per batch holds, for
 // every lattice, a chain of G step-kernel nodes (step k+1 depends on step k
 // of the same lattice) and no edge between lattices, so the GPU overlaps the
-// chains; each node runs the single-lattice kernel with that lattice's
-// parameters in its own constant bank.  G (steps per graph) is autotuned.
+// chains; each node runs the single-lattice kernel (second or third order)
+// with that lattice's parameters in its own constant bank.  G (steps per
+// graph) is autotuned.
 namespace {
 
 const void* kernel_of(const rlbm_ctx* c) {
+  if (c->order == 3) return fused_o3_kernel_fn(c->fused);
   const bool bf = c->dtype == RLBM_BF16_DEV;
   switch (c->fused) {
     case 1: return fused_kernel_fn<StencilM1>(bf);
@@ -696,22 +698,29 @@ const void* kernel_of(const rlbm_ctx* c) {
   }
 }
 
-// Arguments of the k-th step from now (buffers by parity).
+// Arguments of the k-th step from now (buffers by parity); params[0] points
+// at the FusedParams copy (second order) or at the context's FusedO3Params.
 struct NodeArgs {
   FusedParams p;
   const void* fin;
   void* fout;
+  void* params[3];
 };
 
-NodeArgs args_of(const rlbm_ctx* c, int k) {
+void args_of(const rlbm_ctx* c, int k, NodeArgs& a) {
   const int cur = c->cur ^ (k & 1);
-  NodeArgs a;
-  a.p = *c->fp;
-  a.p.cin = c->coef[cur];
-  a.p.cout = c->coef[1 - cur];
+  if (c->order == 3) {
+    a.params[0] = c->fo3.get();
+  } else {
+    a.p = *c->fp;
+    a.p.cin = c->coef[cur];
+    a.p.cout = c->coef[1 - cur];
+    a.params[0] = &a.p;
+  }
   a.fin = c->buf[cur];
   a.fout = c->buf[1 - cur];
-  return a;
+  a.params[1] = &a.fin;
+  a.params[2] = &a.fout;
 }
 
 unsigned grid_of(const rlbm_ctx* c) { return (unsigned)(((long long)c->Nx * c->Ny + 127) / 128); }
@@ -753,14 +762,14 @@ cudaError_t build_graph(const std::vector<rlbm_ctx*>& v, int gsteps, cudaStream_
   for (rlbm_ctx* c : by_size(v)) {
     cudaGraphNode_t prev = nullptr;
     for (int k = 0; k < gsteps && e == cudaSuccess; ++k) {
-      NodeArgs a = args_of(c, k);
-      void* params[3] = {&a.p, &a.fin, &a.fout};
+      NodeArgs a;
+      args_of(c, k, a);
       cudaKernelNodeParams kp = {};
       kp.func = const_cast<void*>(kernel_of(c));
       kp.gridDim = dim3(grid_of(c));
       kp.blockDim = dim3(128);
       kp.sharedMemBytes = 0;
-      kp.kernelParams = params;
+      kp.kernelParams = a.params;
       cudaGraphNode_t node = nullptr;
       e = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
       prev = node;
@@ -776,9 +785,9 @@ cudaError_t build_graph(const std::vector<rlbm_ctx*>& v, int gsteps, cudaStream_
 
 cudaError_t single_step(const std::vector<rlbm_ctx*>& v, cudaStream_t s) {
   for (rlbm_ctx* c : by_size(v)) {
-    NodeArgs a = args_of(c, 0);
-    void* params[3] = {&a.p, &a.fin, &a.fout};
-    cudaError_t e = cudaLaunchKernel(kernel_of(c), dim3(grid_of(c)), dim3(128), params, 0, s);
+    NodeArgs a;
+    args_of(c, 0, a);
+    cudaError_t e = cudaLaunchKernel(kernel_of(c), dim3(grid_of(c)), dim3(128), a.params, 0, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -835,10 +844,9 @@ extern "C" rlbm_status rlbm_batch_step(rlbm_ctx* const* ctxs, int count, int nst
   for (int i = 0; i < count; ++i) {
     rlbm_ctx* c = ctxs[i];
     if (!c || !c->initialised) return fail(nullptr, RLBM_EINVAL, "batch: a context is missing or not initialised");
-    if (c->order != 2)
-      return fail(nullptr, RLBM_ENOTSUP, "batch: third-order contexts are stepped one at a time (rlbm_step)");
-    if ((c->dtype != RLBM_F32 && c->dtype != RLBM_BF16_DEV) || !c->fused)
-      return fail(nullptr, RLBM_ENOTSUP, "batch: every context needs FP32 or BF16 storage and a compiled stencil");
+    if (c->order == 3 ? !c->fo3 : ((c->dtype != RLBM_F32 && c->dtype != RLBM_BF16_DEV) || !c->fused))
+      return fail(nullptr, RLBM_ENOTSUP,
+                  "batch: every context needs a compiled stencil and FP32 storage (or BF16 at second order)");
     if (c->stream != ctxs[0]->stream) return fail(nullptr, RLBM_EINVAL, "batch: contexts on different streams");
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == c) return fail(nullptr, RLBM_EINVAL, "batch: a context is listed twice");

@@ -1,6 +1,6 @@
 """rlbm_batch_step: many independent lattices of different stencils, sizes,
-masses and relaxation times advanced together must give what each lattice
-gives when advanced alone (the graph nodes run the single-lattice kernel, so
+masses and relaxation times (second and third order) advanced together must
+give what each lattice gives when advanced alone (the graph nodes run the single-lattice kernel, so
 the results are identical), and what the oracle gives."""
 import numpy as np
 import pytest
@@ -16,10 +16,10 @@ SPECS = [  # (mbar, tau, Nx, Ny)
 ]
 
 
-def _make(spec, seed, dtype="f32"):
+def _make(spec, seed, dtype="f32", order=2):
     from paper_1703_04605_gb300 import Lattice
     m, tau, Nx, Ny = spec
-    groups, mu = stencils.choose(m)
+    groups, mu = stencils.choose(m, order=order)
     lat = Lattice(groups, mu, tau, Nx, Ny, dtype=dtype, v0=0.0)
     f = smooth_fields(Nx, Ny, seed=seed, du=0.08)
     lat.init(f["n"], f["ux"], f["uy"], f["T"])
@@ -82,6 +82,27 @@ def test_batch_bf16_equals_single_lattices():
         lat.close()
 
 
+def test_batch_third_order_equals_single_lattices():
+    # compiled third-order kernels of five library sets (halo 3-5) beside a
+    # second-order lattice, in one graph: identical to stepping each alone
+    from paper_1703_04605_gb300 import batch_step
+    specs = [(2.0, 0.8, 33, 29, 3), (2.5, 1.1, 40, 21, 3), (5.0, 0.9, 27, 36, 3), (6.0, 0.7, 24, 24, 3),
+             (8.0, 1.3, 45, 18, 3), (1.0, 0.8, 40, 37, 2)]
+    batch = [_make(s[:4], 300 + i, order=s[4]) for i, s in enumerate(specs)]
+    alone = [_make(s[:4], 300 + i, order=s[4]) for i, s in enumerate(specs)]
+    assert [b.info()["kernel"] for b in batch[:5]] == [8, 9, 5, 6, 7]
+    batch_step(batch, 9)         # graph of 8 steps and one single step
+    batch_step(batch, 45)        # autotune (42 steps), then a graph of 2 and one single step
+    for lat in alone:
+        lat.step(54)
+    for b, a in zip(batch, alone):
+        assert b.info()["t"] == 54
+        e = errors(b.moments(), a.moments())
+        assert max(e.values()) < 1e-12, e      # same kernel, same inputs: identical
+    for lat in batch + alone:
+        lat.close()
+
+
 def test_batch_rejections():
     from paper_1703_04605_gb300 import RLBMError, batch_step
     a = _make(SPECS[0], 1)
@@ -90,8 +111,15 @@ def test_batch_rejections():
         batch_step([a, b], 2)
     with pytest.raises(RLBMError):
         batch_step([a, a], 2)
-    a.close()
-    b.close()
+    # third order: FP64 storage, or FP32 on the generic kernel (narrower than the halo)
+    c = _make((5.0, 0.8, 16, 16), 3, dtype="f64", order=3)
+    d = _make((5.0, 0.8, 2, 16), 4, order=3)
+    assert d.info()["kernel"] == 0
+    for other in (c, d):
+        with pytest.raises(RLBMError, match="ENOTSUP"):
+            batch_step([a, other], 2)
+    for lat in (a, b, c, d):
+        lat.close()
 
 
 def test_batch_workload_sample():

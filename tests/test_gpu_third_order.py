@@ -10,7 +10,8 @@ m/T_R = 5 (Q = 100 folded, halo 3).
 * global N^0 and T^{0 nu} conserved over many steps; moments at t = 0 are the
   input fields; a uniform rest state at T_R is stationary;
 * the library's own positive-weight window and weights agree with the
-  oracle's; BF16 storage and batches are rejected (ENOTSUP)."""
+  oracle's; BF16 storage is rejected (ENOTSUP).  Batches of third-order
+  lattices: tests/test_gpu_batch.py."""
 import numpy as np
 import pytest
 
@@ -101,13 +102,9 @@ def test_conservation_t0_and_rest():
 
 
 def test_unsupported_modes():
-    from paper_1703_04605_gb300 import Lattice, RLBMError, batch_step
+    from paper_1703_04605_gb300 import Lattice, RLBMError
     with pytest.raises(RLBMError, match="ENOTSUP"):
         Lattice(ST["groups"], ST["m"], 0.8, 16, 16, dtype="bf16dev", v0=ST["v0"])
-    with Lattice(ST["groups"], ST["m"], 0.8, 16, 16, dtype="f32", v0=ST["v0"]) as lat:
-        lat.init(np.ones((16, 16)), 0.0, 0.0, 1.0)
-        with pytest.raises(RLBMError, match="ENOTSUP"):
-            batch_step([lat], 1)
 
 
 def test_quadratures_agree_at_third_order():
