@@ -112,7 +112,8 @@ typedef struct {
 /* Create a lattice context.
  *  st     stencil (copied); m = particle mass in units of T_R (m > 0);
  *  tau    relaxation time in lattice steps (tau > 1/2);
- *  Nx,Ny  lattice size (>= 1 each);  dtype  population storage;
+ *  Nx,Ny  lattice size (>= 1 each, Nx Ny <= 2^31 - 1: the kernels index
+ *         sites with 32-bit integers);  dtype  population storage;
  *  cuda_stream  a cudaStream_t (NULL = legacy default stream), borrowed.
  * Builds the stencil tables on the host (weights of Eq. 52 in binary128),
  * uploads them and allocates two population buffers.  *out is set only on
@@ -225,7 +226,7 @@ typedef struct {
                                the generic kernels)                           */
 } rlbm3_info;
 
-/* As rlbm_create, with Nz >= 1; dtype RLBM_F64 or RLBM_F32 (ENOTSUP for
+/* As rlbm_create, with Nz >= 1 and Nx Ny Nz <= 2^31 - 1; dtype RLBM_F64 or RLBM_F32 (ENOTSUP for
  * BF16).  Six groups: the second-order equilibrium (App. A-B); eleven: the
  * third-order one, exact to the third moment T^abc (generic kernels).  More
  * than 160 unfolded populations: ENOTSUP. */

@@ -1,6 +1,7 @@
 // C ABI of the library (include/rlbm.h): context lifetime, validation,
 // device buffers, launches and error reporting.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -394,6 +395,8 @@ rlbm_status rlbm_create(const rlbm_stencil* st, double m, double tau, int Nx, in
   if (!out) return fail(nullptr, RLBM_EINVAL, "out is NULL");
   *out = nullptr;
   if (Nx < 1 || Ny < 1) return fail(nullptr, RLBM_EINVAL, "Nx and Ny must be >= 1");
+  if ((long long)Nx * Ny > INT_MAX)
+    return fail(nullptr, RLBM_EINVAL, "Nx * Ny exceeds 2^31 - 1 (the kernels index sites with 32-bit integers)");
   if (!(tau > 0.5) || !std::isfinite(tau)) return fail(nullptr, RLBM_EINVAL, "tau must exceed 1/2");
   if (dtype != RLBM_F64 && dtype != RLBM_F32 && dtype != RLBM_BF16_DEV)
     return fail(nullptr, RLBM_EINVAL, "unknown dtype");

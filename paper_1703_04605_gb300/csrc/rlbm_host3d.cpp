@@ -1,4 +1,5 @@
 // C ABI of the native 3D lattices (include/rlbm.h, "native 3D lattices").
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -175,6 +176,8 @@ rlbm_status rlbm3_create(const rlbm_stencil* st, double m, double tau, int Nx, i
   if (!out) return fail3(nullptr, RLBM_EINVAL, "out is NULL");
   *out = nullptr;
   if (Nx < 1 || Ny < 1 || Nz < 1) return fail3(nullptr, RLBM_EINVAL, "Nx, Ny and Nz must be >= 1");
+  if ((long long)Nx * Ny * Nz > INT_MAX)
+    return fail3(nullptr, RLBM_EINVAL, "Nx * Ny * Nz exceeds 2^31 - 1 (the kernels index sites with 32-bit integers)");
   if (!(tau > 0.5) || !std::isfinite(tau)) return fail3(nullptr, RLBM_EINVAL, "tau must exceed 1/2");
   if (dtype == RLBM_BF16_DEV) return fail3(nullptr, RLBM_ENOTSUP, "3D lattices store FP64 or FP32");
   if (dtype != RLBM_F64 && dtype != RLBM_F32) return fail3(nullptr, RLBM_EINVAL, "unknown dtype");

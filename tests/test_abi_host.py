@@ -116,6 +116,7 @@ def _create(lib, groups=(5, 12, 14, 17, 21, 26), m=1.0, tau=0.8, Nx=8, Ny=8, dty
 def test_create_validates_before_device(lib):
     assert _create(lib, tau=0.5)[0] == A.RLBM_EINVAL
     assert _create(lib, Nx=0)[0] == A.RLBM_EINVAL
+    assert _create(lib, Nx=65536, Ny=32768)[0] == A.RLBM_EINVAL      # 2^31 sites: 32-bit site index
     assert _create(lib, groups=(5, 12, 14, 17, 21))[0] == A.RLBM_EINVAL
     assert _create(lib, groups=(5, 12, 14, 17, 21, 21))[0] == A.RLBM_EINVAL
     assert _create(lib, groups=(5, 12, 14, 17, 21, 85))[0] == A.RLBM_EINVAL
@@ -158,6 +159,7 @@ def test_3d_entry_points_without_device(lib):
     st = A.Stencil(6, g, 0.398)
     ctx = C.c_void_p()
     assert lib.rlbm3_create(C.byref(st), 5.0, 0.8, 4, 4, 0, 0, None, C.byref(ctx)) == A.RLBM_EINVAL
+    assert lib.rlbm3_create(C.byref(st), 5.0, 0.8, 2048, 1024, 1024, 0, None, C.byref(ctx)) == A.RLBM_EINVAL
     assert lib.rlbm3_create(C.byref(st), 5.0, 0.5, 4, 4, 4, 0, None, C.byref(ctx)) == A.RLBM_EINVAL
     assert lib.rlbm3_create(C.byref(st), 5.0, 0.8, 4, 4, 4, 2, None, C.byref(ctx)) == A.RLBM_ENOTSUP
     s = lib.rlbm3_create(C.byref(st), 5.0, 0.8, 4, 4, 4, 0, None, C.byref(ctx))
