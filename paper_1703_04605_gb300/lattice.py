@@ -68,9 +68,13 @@ class Lattice:
         self._chk(self._lib.rlbm_init(self._ctx, *ptrs))
 
     def init_device(self, n, ux, uy, T):
-        """Device fields: four contiguous CUDA float64 tensors of Nx*Ny elements."""
+        """Device fields: four contiguous CUDA float64 tensors of Nx*Ny elements
+        (the kernel reads Nx*Ny doubles from each pointer, so any other dtype
+        or size is refused here)."""
+        import torch
         for t in (n, ux, uy, T):
-            if not (t.is_cuda and t.is_contiguous() and t.numel() == self.Nx * self.Ny):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+                    and t.is_contiguous() and t.numel() == self.Nx * self.Ny):
                 raise ValueError("device fields must be contiguous CUDA tensors of Nx*Ny float64")
         self._chk(self._lib.rlbm_init_device(self._ctx, *[C.c_void_p(t.data_ptr()) for t in (n, ux, uy, T)]))
 

@@ -169,3 +169,16 @@ def test_3d_entry_points_without_device(lib):
     assert lib.rlbm3_sync(None) == A.RLBM_EINVAL
     assert lib.rlbm3_moments_size(None, 1) == 0
     lib.rlbm3_destroy(None)
+
+
+def test_init_device_refuses_fields_it_cannot_read():
+    # the device initialiser reads Nx*Ny doubles per pointer: host arrays,
+    # CPU tensors, other dtypes and other sizes are refused before the call
+    torch = pytest.importorskip("torch")
+    from paper_1703_04605_gb300.lattice import Lattice
+    lat = Lattice.__new__(Lattice)
+    lat.Nx, lat.Ny = 4, 3
+    ok = torch.zeros(12, dtype=torch.float64)
+    for bad in (np.zeros(12), ok, torch.zeros(12, dtype=torch.float32), torch.zeros(11, dtype=torch.float64)):
+        with pytest.raises(ValueError):
+            lat.init_device(bad, ok, ok, ok)
