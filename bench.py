@@ -308,9 +308,11 @@ def run_reference(args):
         vals.append(cpu_baseline(seconds=5.0, side=side))
     v = float(np.mean([d["value"] for d in vals]))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f64",
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": N_SIDE * N_SIDE / (v * 1e6) * 1e3, "higher_is_better": True, "dtype": "f64",
             "data": "synthetic", "scaling": "weak",
-            "config": {"workload": WORKLOAD, "sample": "%dx%d lattice of the same generator per step" % (side, side)},
+            "config": {"workload": WORKLOAD, "sample": "%dx%d lattice of the same generator per step" % (side, side),
+                       "ms_per_step": "one %dx%d step at the measured rate" % (N_SIDE, N_SIDE)},
             "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": vals[-1]["cores"], "kind": "oracle",
                              "sample": vals[-1]["sample"]},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
