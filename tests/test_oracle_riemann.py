@@ -1,0 +1,116 @@
+"""The shock-tube workload (Sec. IV: the relativistic Riemann problem the paper
+runs against other solvers) pinned to the exact solution of the ideal
+Maxwell-Juttner fluid, with no lattice code in the reference
+(`riemann_exact.py`).
+
+* the exact solver itself: its jump conditions hold to round-off; the
+  ultra-relativistic rarefaction has the closed form
+  atanh(v) = (sqrt3/4) ln(P_L/P); a vanishing shock moves at the sound
+  speed; for m >> T it approaches the classical (gamma = 5/3) Sod solution;
+* the oracle lattice on the workload's states, stencil and tau (eta/s = 0.1)
+  on a tube long enough that the waves of its two jumps have not met: the
+  intermediate pressure and velocity, the shock position and the rarefaction
+  fan agree with the ideal-fluid solution within what viscosity leaves
+  (measured: P* 0.17 %, v* 0.03 %, shock 0.15 cells of 372, fan 1.6 %)."""
+import math
+
+import numpy as np
+import pytest
+from scipy import optimize
+
+import riemann_exact as R
+from oracle import lattice as OL
+from paper_1703_04605_gb300 import workloads as W
+
+NL, TL, NR, TR = 1.0, 1.0, 0.5, 0.8       # the workload's left and right states (m = 1)
+
+
+def test_exact_solution_satisfies_the_jump_conditions():
+    s = R.solve(NL, TL, NR, TR, 1.0)
+    assert abs(s["v"] - s["v_shock_side"]) < 1e-12
+    assert max(R.jump_residuals((NR, TR, 0.0), (s["nR"], s["TR"], s["v"]), s["V"], 1.0)) < 1e-12
+    # P* between the two pressures; density rises across the shock, falls across the fan
+    assert NR * TR < s["P"] < NL * TL and s["nR"] > NR and s["nL"] < NL
+    # the left intermediate state lies on the left state's isentrope
+    assert abs(R.entropy_per_particle(s["nL"], s["TL"], 1.0) - R.entropy_per_particle(NL, TL, 1.0)) < 1e-11
+
+
+def test_ultrarelativistic_rarefaction_closed_form():
+    # c_s = 1/sqrt3 and P ~ n^(4/3) along an isentrope: atanh v = (sqrt3/4) ln(P_L/P)
+    m = 1e-7
+    for P in (0.9, 0.5, 0.2):
+        _, _, v = R.rarefaction(P, NL, TL, m)
+        assert abs(math.atanh(v) - math.sqrt(3.0) / 4.0 * math.log(NL * TL / P)) < 1e-9
+
+
+def test_sound_speed_limits_and_weak_shock():
+    assert abs(R.sound_speed(1.0, 1e-7) - 1.0 / math.sqrt(3.0)) < 1e-9
+    assert abs(R.sound_speed(1.0, 1e4) / math.sqrt(5.0 / 3.0 / 1e4) - 1.0) < 1e-3
+    # a vanishing shock is an acoustic wave (its speed differs from c_s by
+    # O(strength); weaker shocks lose digits to cancellation in the solver)
+    _, _, vb, V = R.shock(NR * TR * (1.0 + 1e-4), NR, TR, 1.0)
+    assert vb < 1e-4 and abs(V / R.sound_speed(TR, 1.0) - 1.0) < 1e-4
+
+
+def _classical_sod(rhoL, pL, rhoR, pR, gamma=5.0 / 3.0):
+    """p*, u* of the classical ideal-gas Riemann problem (both sides at rest):
+    rarefaction on the left, shock on the right (textbook exact solver)."""
+    cL = math.sqrt(gamma * pL / rhoL)
+    fL = lambda p: 2.0 * cL / (gamma - 1.0) * ((p / pL) ** ((gamma - 1.0) / (2.0 * gamma)) - 1.0)
+    A, B = 2.0 / ((gamma + 1.0) * rhoR), (gamma - 1.0) / (gamma + 1.0) * pR
+    fR = lambda p: (p - pR) * math.sqrt(A / (p + B))
+    p = optimize.brentq(lambda p: fL(p) + fR(p), pR, pL, xtol=1e-15, rtol=1e-14)
+    return p, -fL(p)
+
+
+def test_nonrelativistic_limit_is_the_classical_sod_solution():
+    # m >> T: mass density m n, pressure n T, gamma = 5/3; corrections O(T/m)
+    m = 2000.0
+    s = R.solve(NL, TL, NR, TR, m)
+    p, u = _classical_sod(m * NL, NL * TL, m * NR, NR * TR)
+    assert abs(s["P"] / p - 1.0) < 2e-3
+    assert abs(s["v"] / u - 1.0) < 2e-3
+
+
+@pytest.fixture(scope="module")
+def sod_run():
+    st = W.STENCIL_M1
+    Nx, steps = 2000, 140
+    x0 = Nx // 2
+    f = W.sod(Nx, 1, n=(NL, NR), T=(TL, TR), x0=x0)
+    lat = OL.make_lattice(st["groups"], st["m"], st["v0"], W.sod_tau(), (1, Nx))
+    lat.init(f["n"], f["ux"], f["uy"], f["T"])
+    lat.step(steps)
+    mac = lat.macros()
+    return dict(P=(mac["n"] * mac["T"])[0], v=mac["ux"][0], x=np.arange(Nx) + 0.5 - x0, t=steps,
+                v0=st["v0"], exact=R.solve(NL, TL, NR, TR, st["m"]))
+
+
+def _crossing(x, y, level, sel):
+    """x where y falls through level inside the selection (last sample above)."""
+    i = np.where(sel & (y > level))[0].max()
+    return x[i] + (y[i] - level) / (y[i] - y[i + 1])
+
+
+def test_oracle_sod_intermediate_state(sod_run):
+    r, ex = sod_run, sod_run["exact"]
+    # between the contact (x ~ 110) and the shock (x ~ 372): P and v are continuous
+    w = (r["x"] > 40) & (r["x"] < 140)
+    assert abs(np.median(r["P"][w]) / ex["P"] - 1.0) < 5e-3
+    assert abs(np.median(r["v"][w]) / ex["v"] - 1.0) < 2e-3
+
+
+def test_oracle_sod_wave_positions(sod_run):
+    r, ex = sod_run, sod_run["exact"]
+    t_c = r["t"] / r["v0"]                # one cell per step is v0 (dt = dx/v0)
+    # shock: half-way point between P* and P_R against x = V t
+    xs = _crossing(r["x"], r["P"], 0.5 * (ex["P"] + NR * TR), (r["x"] > 0) & (r["x"] < 500))
+    assert abs(xs - ex["V"] * t_c) < 2.0
+    # rarefaction fan: where P is half-way between P_L and P*, against the
+    # self-similar fan x/t = (v - c_s)/(1 - v c_s) at that pressure
+    mid = 0.5 * (NL * TL + ex["P"])
+    xf = _crossing(r["x"], r["P"], mid, (r["x"] > -480) & (r["x"] < 0))
+    _, Tm, vm = R.rarefaction(mid, NL, TL, 1.0)
+    cm = R.sound_speed(Tm, 1.0)
+    xi = (vm - cm) / (1.0 - vm * cm) * t_c
+    assert abs(xf / xi - 1.0) < 0.03
