@@ -11,7 +11,9 @@ Maxwell-Juttner fluid, with no lattice code in the reference
   on a tube long enough that the waves of its two jumps have not met: the
   intermediate pressure and velocity, the shock position and the rarefaction
   fan agree with the ideal-fluid solution within what viscosity leaves
-  (measured: P* 0.17 %, v* 0.03 %, shock 0.15 cells of 372, fan 1.6 %)."""
+  (measured: P* 0.17 %, v* 0.03 %, shock 0.15 cells of 372, fan 1.6 %);
+* the strong Riemann problem of the mass sweep (Sec. V) on the library's
+  stencils at m/T_R = 0.36, 1, 4, 5, against the same exact solution."""
 import math
 
 import numpy as np
@@ -114,3 +116,40 @@ def test_oracle_sod_wave_positions(sod_run):
     cm = R.sound_speed(Tm, 1.0)
     xi = (vm - cm) / (1.0 - vm * cm) * t_c
     assert abs(xf / xi - 1.0) < 0.03
+
+
+# v0 inside each library stencil's positive-weight window (Sec. III D; the
+# test checks the oracle's weights are positive there)
+SWEEP_V0 = {0.36: 0.1488232, 1.0: 0.23342, 4.0: 0.22195, 5.0: 0.21651}
+
+
+@pytest.mark.parametrize("m", W.RIEMANN_SWEEP_M)
+def test_oracle_strong_riemann_sweep(m):
+    """Sec. V: the strong Riemann problem (n 1 -> 0.124, T 1 -> 0.5, pressure
+    ratio 16) at eta/s = 0.1 over the mass sweep, after t = 500 dx/c, against
+    the ideal fluid (measured: P* within 0.1-1.1 %, v* within 0.07-0.24 %, the
+    shock 1-1.7 % behind V t, the lag of a viscous shock's formation)."""
+    from paper_1703_04605_gb300 import stencils
+    nL, nR = W.RIEMANN_STATES["n"]
+    TL_, TR_ = W.RIEMANN_STATES["T"]
+    groups, mb = stencils.choose(m)
+    v0 = SWEEP_V0[m]
+    Nx = 4000
+    x0 = Nx // 2
+    f = W.riemann(Nx, 1, x0=x0)
+    steps = int(round(500.0 * v0))
+    lat = OL.make_lattice(groups, mb, v0, W.sod_tau(0.1, v0=v0), (1, Nx))
+    assert min(lat.w) > 0
+    lat.init(f["n"], f["ux"], f["uy"], f["T"])
+    lat.step(steps)
+    mac = lat.macros()
+    P, v = (mac["n"] * mac["T"])[0], mac["ux"][0]
+    x = np.arange(Nx) + 0.5 - x0
+    ex = R.solve(nL, TL_, nR, TR_, mb)
+    t_c = steps / v0
+    xc, xsh = ex["v"] * t_c, ex["V"] * t_c             # contact and shock of the ideal fluid
+    w = (x > xc + 0.2 * (xsh - xc)) & (x < xc + 0.6 * (xsh - xc))
+    assert abs(np.median(P[w]) / ex["P"] - 1.0) < 2e-2
+    assert abs(np.median(v[w]) / ex["v"] - 1.0) < 5e-3
+    xs = _crossing(x, P, 0.5 * (ex["P"] + nR * TR_), (x > 0) & (x < Nx / 4))
+    assert abs(xs / xsh - 1.0) < 0.025
