@@ -79,3 +79,16 @@ def test_traffic_record_requires_matching_sources(tmp_path, monkeypatch):
     assert bench.profiled_traffic("k.md", bench.FUSED_SOURCES) == 1234.0
     assert bench.profiled_traffic("old.md", bench.FUSED_SOURCES) is None
     assert bench.profiled_traffic("missing.md", bench.FUSED_SOURCES) is None
+
+
+def test_clock_records_that_disqualify_a_number():
+    sys.path.insert(0, ROOT)
+    import bench
+    ok = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 5}
+    assert not bench.clocks_rejected(ok)
+    assert not bench.clocks_rejected(dict(ok, reasons=["sw_power_cap"], sm_mhz=1500.0))   # kept, noted
+    for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
+        assert bench.clocks_rejected(dict(ok, reasons=[r]))
+    assert bench.clocks_rejected(dict(ok, sm_mhz=1200.0))       # stuck low with no reason: a lock
+    assert not bench.clocks_rejected(dict(ok, sm_mhz=None, sm_max_mhz=None, samples=0))
+    assert not bench.clocks_rejected(None)
