@@ -293,14 +293,15 @@ rlbm_status rlbm_quadrature_weights(const int* groups, int ngroups, double m, do
                                     double* w_out);
 
 /* The widest v0 interval (lo, hi) in which all weights (6 or 11 groups) are
- * positive, and the count of disjoint positive intervals; ENOQUAD if there is
- * none. */
+ * positive (Sec. III D: v0 is free inside it), and the count of disjoint
+ * positive intervals; ENOQUAD if there is none. */
 rlbm_status rlbm_quadrature_window(const int* groups, int ngroups, double m, double* lo,
                                    double* hi, int* nwindows);
 
-/* R(zeta) = K1(zeta)/K2(zeta) from the library's piecewise-polynomial tables,
- * evaluated on the host by the same formulas the kernels use (precision 64
- * or 32).  For validation of the tables. */
+/* R(zeta) = K1(zeta)/K2(zeta), the Bessel ratio of the equation of state
+ * (Eq. 28), from the library's piecewise-polynomial tables, evaluated on the
+ * host by the same formulas the kernels use (precision 64 or 32).  For
+ * validation of the tables. */
 double rlbm_bessel_ratio(double zeta, int precision);
 
 /* Library version string. */
