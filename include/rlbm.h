@@ -169,6 +169,26 @@ const char* rlbm_last_error(const rlbm_ctx* ctx);
 /* Release the context and its device memory (synchronises its stream). */
 void rlbm_destroy(rlbm_ctx* ctx);
 
+/* ---- device memory ---------------------------------------------------
+ * Contexts own their device buffers (populations, tables, staging) and by
+ * default take them from cudaMalloc.  rlbm_set_allocator installs a
+ * caller-supplied allocator instead -- a framework's caching allocator, for
+ * instance -- for the contexts (2D and 3D) created after the call:
+ *   alloc(bytes, device, stream, user) returns device memory of at least
+ *     bytes on that device, aligned to 256 bytes, for use on that stream
+ *     (the context's; NULL = legacy default stream), or NULL (ENOMEM; a
+ *     block that is not 256-byte aligned is handed back and counts as NULL);
+ *   free_fn(ptr, user) takes back a block alloc returned.
+ * A context keeps the pair it was created with and frees through it, on
+ * rlbm_destroy (after synchronising its stream) and when rlbm_moments grows
+ * its read-out buffer.  alloc and free_fn both NULL restore cudaMalloc and
+ * cudaFree; exactly one NULL is EINVAL.  Process-wide; the setting is
+ * copied under a lock, so it may change while other threads create contexts.
+ * The paper has no counterpart.  rlbm_moments_noalloc allocates nothing. */
+typedef void* (*rlbm_alloc_fn)(size_t bytes, int device, void* cuda_stream, void* user);
+typedef void (*rlbm_free_fn)(void* ptr, void* user);
+rlbm_status rlbm_set_allocator(rlbm_alloc_fn alloc, rlbm_free_fn free_fn, void* user);
+
 /* Advance count contexts by nsteps each, as one batch (the independent
  * lattices of a parameter sweep or an ensemble).  Equivalent to calling
  * rlbm_step(ctxs[i], nsteps) for every i, with identical results.  The steps

@@ -7,6 +7,6 @@ equilibrium / Anderson-Witting collision step.  This package only marshals
 arguments; it has no host implementation of the step."""
 from . import _abi
 from ._abi import RLBMError, load, quadrature_weights, quadrature_window, bessel_ratio
-from .lattice import Lattice, Lattice3D, batch_step, batch_tuning
+from .lattice import Lattice, Lattice3D, batch_step, batch_tuning, use_cuda_malloc, use_torch_allocator
 
-__all__ = ["Lattice", "Lattice3D", "batch_step", "batch_tuning", "RLBMError", "load", "quadrature_weights", "quadrature_window", "bessel_ratio"]
+__all__ = ["Lattice", "Lattice3D", "batch_step", "batch_tuning", "use_torch_allocator", "use_cuda_malloc", "RLBMError", "load", "quadrature_weights", "quadrature_window", "bessel_ratio"]

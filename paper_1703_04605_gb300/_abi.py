@@ -23,9 +23,14 @@ MASK_PLANES3 = [(M_N, ["n"]), (M_UX, ["ux"]), (M_UY, ["uy"]), (M_T, ["T"]), (M_E
 EXPORTS = ["rlbm_create", "rlbm_init", "rlbm_init_device", "rlbm_step", "rlbm_moments",
            "rlbm_moments_size", "rlbm_sync", "rlbm_get_info", "rlbm_last_error", "rlbm_destroy",
            "rlbm_quadrature_weights", "rlbm_quadrature_window", "rlbm_bessel_ratio", "rlbm_version",
-           "rlbm_moments_noalloc", "rlbm_batch_step", "rlbm_batch_tuning",
+           "rlbm_moments_noalloc", "rlbm_batch_step", "rlbm_batch_tuning", "rlbm_set_allocator",
            "rlbm3_create", "rlbm3_init", "rlbm3_step", "rlbm3_moments", "rlbm3_moments_size", "rlbm3_sync",
            "rlbm3_get_info", "rlbm3_last_error", "rlbm3_destroy"]
+
+
+# rlbm_alloc_fn(bytes, device, stream, user) -> pointer; rlbm_free_fn(ptr, user)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_int, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
 
 class Stencil(C.Structure):
@@ -90,6 +95,9 @@ def load():
         "rlbm_bessel_ratio": (C.c_double, [C.c_double, C.c_int]),
         "rlbm_version": (C.c_char_p, []),
         "rlbm_batch_step": (C.c_int, [C.POINTER(P), C.c_int, C.c_int]),
+        # the two callbacks as pointers (ALLOC_FN / FREE_FN instances cast to
+        # c_void_p, or None for NULL)
+        "rlbm_set_allocator": (C.c_int, [P, P, P]),
         "rlbm_batch_tuning": (C.c_int, [C.POINTER(P), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "rlbm_moments_noalloc": (C.c_int, [ip, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, P, dp,
                                            C.c_uint, P]),

@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include "rlbm_devmem.h"
 #include "rlbm_fused_launch.h"
 #include "rlbm_stencil.h"
 
@@ -52,11 +53,28 @@ struct rlbm_ctx {
   long long* d_off = nullptr;
   double* d_tab64 = nullptr;
   float* d_tab32 = nullptr;
+  DevMem mem;                    // device allocator (rlbm_set_allocator at creation)
   std::string last_error;
 };
 
 static thread_local std::string g_create_error;
 static void batch_forget(const rlbm_ctx* c);   // drop cached batch graphs that use c
+
+// The allocator installed by rlbm_set_allocator (all null: cudaMalloc).
+static std::mutex g_alloc_mutex;
+static DevMem g_alloc;
+
+DevMem rlbm::current_devmem(cudaStream_t stream) {
+  DevMem m;
+  {
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    m = g_alloc;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) m.device = dev;
+  m.stream = stream;
+  return m;
+}
 
 void rlbm::set_global_error(const std::string& msg) { g_create_error = msg; }
 
@@ -76,7 +94,7 @@ static void release(rlbm_ctx* c) {
   for (void* p : {c->buf[0], c->buf[1], c->coef[0], c->coef[1], (void*)c->d_err, (void*)c->d_rt64, (void*)c->d_rt32,
                   (void*)c->d_fields, (void*)c->d_out, (void*)c->d_shift, (void*)c->d_off, (void*)c->d_tab64,
                   (void*)c->d_tab32})
-    if (p) cudaFree(p);
+    c->mem.put(p);
 }
 
 template <typename CT>
@@ -306,10 +324,11 @@ static rlbm_status create_o3(const rlbm_stencil* st, double m, double tau, int N
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess || ndev == 0) return fail(nullptr, RLBM_ECUDA, "no CUDA device available");
+  c->mem = current_devmem(c->stream);
   const int Q = c->Q;
   const size_t fbytes = (size_t)Q * (size_t)c->plane * c->elem;
   for (int b = 0; b < 2; ++b) {
-    e = cudaMalloc(&c->buf[b], fbytes);
+    e = c->mem.get(&c->buf[b], fbytes);
     if (e != cudaSuccess) {
       release(c.get());
       return fail(nullptr, RLBM_ENOMEM, "population buffers: " + std::string(cudaGetErrorString(e)));
@@ -319,14 +338,14 @@ static rlbm_status create_o3(const rlbm_stencil* st, double m, double tau, int N
   const auto& t32 = ratio_table32();
   const size_t nsite = (size_t)Nx * Ny;
   const size_t tbytes = (size_t)Q * kRowO3;
-  bool ok = cudaMalloc(&c->d_err, sizeof(unsigned)) == cudaSuccess &&
-            cudaMalloc(&c->d_rt64, t64.size() * sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&c->d_rt32, t32.size() * sizeof(float)) == cudaSuccess &&
-            cudaMalloc(&c->d_fields, 4 * nsite * sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&c->d_shift, 2 * Q * sizeof(int)) == cudaSuccess &&
-            cudaMalloc(&c->d_off, Q * sizeof(long long)) == cudaSuccess &&
-            cudaMalloc(&c->d_tab64, tbytes * sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&c->d_tab32, tbytes * sizeof(float)) == cudaSuccess;
+  bool ok = c->mem.get(&c->d_err, sizeof(unsigned)) == cudaSuccess &&
+            c->mem.get(&c->d_rt64, t64.size() * sizeof(double)) == cudaSuccess &&
+            c->mem.get(&c->d_rt32, t32.size() * sizeof(float)) == cudaSuccess &&
+            c->mem.get(&c->d_fields, 4 * nsite * sizeof(double)) == cudaSuccess &&
+            c->mem.get(&c->d_shift, 2 * Q * sizeof(int)) == cudaSuccess &&
+            c->mem.get(&c->d_off, Q * sizeof(long long)) == cudaSuccess &&
+            c->mem.get(&c->d_tab64, tbytes * sizeof(double)) == cudaSuccess &&
+            c->mem.get(&c->d_tab32, tbytes * sizeof(float)) == cudaSuccess;
   if (!ok) {
     release(c.get());
     return fail(nullptr, RLBM_ENOMEM, "device allocation failed");
@@ -390,6 +409,16 @@ extern "C" {
 
 const char* rlbm_version(void) { return "rlbm-gb300 0.1 (sm_103a)"; }
 
+rlbm_status rlbm_set_allocator(rlbm_alloc_fn alloc, rlbm_free_fn free_fn, void* user) {
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(nullptr, RLBM_EINVAL, "rlbm_set_allocator: give both alloc and free_fn, or neither");
+  std::lock_guard<std::mutex> lock(g_alloc_mutex);
+  g_alloc.alloc = alloc;
+  g_alloc.release = free_fn;
+  g_alloc.user = alloc ? user : nullptr;
+  return RLBM_OK;
+}
+
 rlbm_status rlbm_create(const rlbm_stencil* st, double m, double tau, int Nx, int Ny,
                         rlbm_dtype dtype, void* cuda_stream, rlbm_ctx** out) {
   if (!out) return fail(nullptr, RLBM_EINVAL, "out is NULL");
@@ -426,9 +455,10 @@ rlbm_status rlbm_create(const rlbm_stencil* st, double m, double tau, int Nx, in
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess || ndev == 0) return fail(nullptr, RLBM_ECUDA, "no CUDA device available");
+  c->mem = current_devmem(c->stream);
   const size_t fbytes = (size_t)c->Q * (size_t)c->plane * c->elem;
   for (int b = 0; b < 2; ++b) {
-    e = cudaMalloc(&c->buf[b], fbytes);
+    e = c->mem.get(&c->buf[b], fbytes);
     if (e != cudaSuccess) {
       release(c.get());
       return fail(nullptr, RLBM_ENOMEM, "population buffers: " + std::string(cudaGetErrorString(e)));
@@ -437,10 +467,10 @@ rlbm_status rlbm_create(const rlbm_stencil* st, double m, double tau, int Nx, in
   const auto& t64 = ratio_table64();
   const auto& t32 = ratio_table32();
   const size_t nsite = (size_t)Nx * Ny;
-  bool ok = cudaMalloc(&c->d_err, sizeof(unsigned)) == cudaSuccess &&
-            cudaMalloc(&c->d_rt64, t64.size() * sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&c->d_rt32, t32.size() * sizeof(float)) == cudaSuccess &&
-            cudaMalloc(&c->d_fields, 4 * nsite * sizeof(double)) == cudaSuccess;
+  bool ok = c->mem.get(&c->d_err, sizeof(unsigned)) == cudaSuccess &&
+            c->mem.get(&c->d_rt64, t64.size() * sizeof(double)) == cudaSuccess &&
+            c->mem.get(&c->d_rt32, t32.size() * sizeof(float)) == cudaSuccess &&
+            c->mem.get(&c->d_fields, 4 * nsite * sizeof(double)) == cudaSuccess;
   if (!ok) {
     release(c.get());
     return fail(nullptr, RLBM_ENOMEM, "device allocation failed");
@@ -473,7 +503,7 @@ rlbm_status rlbm_create(const rlbm_stencil* st, double m, double tau, int Nx, in
     }
     const size_t cbytes = (size_t)6 * (size_t)c->plane * 8;
     for (int b = 0; b < 2; ++b) {
-      e = cudaMalloc(&c->coef[b], cbytes);
+      e = c->mem.get(&c->coef[b], cbytes);
       if (e != cudaSuccess) {
         release(c.get());
         return fail(nullptr, RLBM_ENOMEM, "coefficient buffers: " + std::string(cudaGetErrorString(e)));
@@ -589,10 +619,10 @@ rlbm_status rlbm_moments(rlbm_ctx* c, double* out, unsigned mask) {
   const size_t need = rlbm_moments_size(c, mask);
   if (need == 0) return RLBM_OK;
   if (need > c->out_cap) {
-    if (c->d_out) cudaFree(c->d_out);
+    c->mem.put(c->d_out);
     c->d_out = nullptr;
     c->out_cap = 0;
-    cudaError_t e = cudaMalloc(&c->d_out, need * sizeof(double));
+    cudaError_t e = c->mem.get(&c->d_out, need * sizeof(double));
     if (e != cudaSuccess) return fail(c, RLBM_ENOMEM, "read-out buffer");
     c->out_cap = need;
   }

@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "rlbm_devmem.h"
 #include "rlbm_o3_3d.h"
 #include "rlbm_stencil.h"
 #include "rlbm_stencils.h"
@@ -48,6 +49,7 @@ struct rlbm_ctx3 {
   double* d_w64 = nullptr;
   float* d_w32 = nullptr;
   Step3O3Params q{};
+  DevMem mem;                  // device allocator (rlbm_set_allocator at creation)
   std::string last_error;
 };
 
@@ -70,7 +72,7 @@ void release3(rlbm_ctx3* c) {
   for (void* p : {c->buf[0], c->buf[1], (void*)c->d_err, (void*)c->d_rt64, (void*)c->d_rt32, (void*)c->d_shift, (void*)c->d_off,
                   (void*)c->d_tab64, (void*)c->d_tab32, (void*)c->d_fields, (void*)c->d_out, (void*)c->d_w64,
                   (void*)c->d_w32})
-    if (p) cudaFree(p);
+    c->mem.put(p);
   c->buf[0] = c->buf[1] = nullptr;
 }
 
@@ -209,6 +211,7 @@ rlbm_status rlbm3_create(const rlbm_stencil* st, double m, double tau, int Nx, i
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess || ndev == 0) return fail3(nullptr, RLBM_ECUDA, "no CUDA device available");
+  c->mem = current_devmem(c->stream);
   // constant table [Q][kRow3], shifts [3][Q], interior offsets [Q]
   const int Q = c->Q;
   const long long pitch = ((long long)Nx + 31) / 32 * 32;
@@ -231,15 +234,15 @@ rlbm_status rlbm3_create(const rlbm_stencil* st, double m, double tau, int Nx, i
   const size_t nsite = (size_t)Nx * Ny * Nz;
   const auto& r64 = ratio_table64();
   const auto& r32 = ratio_table32();
-  bool ok = cudaMalloc(&c->buf[0], fbytes) == cudaSuccess && cudaMalloc(&c->buf[1], fbytes) == cudaSuccess &&
-            cudaMalloc(&c->d_err, sizeof(unsigned)) == cudaSuccess &&
-            cudaMalloc(&c->d_rt64, r64.size() * sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&c->d_rt32, r32.size() * sizeof(float)) == cudaSuccess &&
-            cudaMalloc(&c->d_shift, sh.size() * sizeof(int)) == cudaSuccess &&
-            cudaMalloc(&c->d_off, off.size() * sizeof(long long)) == cudaSuccess &&
-            cudaMalloc(&c->d_tab64, t64.size() * sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&c->d_tab32, t32.size() * sizeof(float)) == cudaSuccess &&
-            cudaMalloc(&c->d_fields, 5 * nsite * sizeof(double)) == cudaSuccess;
+  bool ok = c->mem.get(&c->buf[0], fbytes) == cudaSuccess && c->mem.get(&c->buf[1], fbytes) == cudaSuccess &&
+            c->mem.get(&c->d_err, sizeof(unsigned)) == cudaSuccess &&
+            c->mem.get(&c->d_rt64, r64.size() * sizeof(double)) == cudaSuccess &&
+            c->mem.get(&c->d_rt32, r32.size() * sizeof(float)) == cudaSuccess &&
+            c->mem.get(&c->d_shift, sh.size() * sizeof(int)) == cudaSuccess &&
+            c->mem.get(&c->d_off, off.size() * sizeof(long long)) == cudaSuccess &&
+            c->mem.get(&c->d_tab64, t64.size() * sizeof(double)) == cudaSuccess &&
+            c->mem.get(&c->d_tab32, t32.size() * sizeof(float)) == cudaSuccess &&
+            c->mem.get(&c->d_fields, 5 * nsite * sizeof(double)) == cudaSuccess;
   std::vector<double> w64;
   std::vector<float> w32;
   if (ok && c->order == 3) {
@@ -250,8 +253,8 @@ rlbm_status rlbm3_create(const rlbm_stencil* st, double m, double tau, int Nx, i
         w64[(size_t)i * kRowW3 + l] = s3->wrows[i][l];
         w32[(size_t)i * kRowW3 + l] = (float)s3->wrows[i][l];
       }
-    ok = cudaMalloc(&c->d_w64, w64.size() * sizeof(double)) == cudaSuccess &&
-         cudaMalloc(&c->d_w32, w32.size() * sizeof(float)) == cudaSuccess;
+    ok = c->mem.get(&c->d_w64, w64.size() * sizeof(double)) == cudaSuccess &&
+         c->mem.get(&c->d_w32, w32.size() * sizeof(float)) == cudaSuccess;
   }
   if (!ok) {
     release3(c.get());
@@ -372,10 +375,10 @@ rlbm_status rlbm3_moments(rlbm_ctx3* c, double* out, unsigned mask) {
   const size_t need = rlbm3_moments_size(c, mask);
   if (need == 0) return RLBM_OK;
   if (need > c->out_cap) {
-    if (c->d_out) cudaFree(c->d_out);
+    c->mem.put(c->d_out);
     c->d_out = nullptr;
     c->out_cap = 0;
-    cudaError_t e = cudaMalloc(&c->d_out, need * sizeof(double));
+    cudaError_t e = c->mem.get(&c->d_out, need * sizeof(double));
     if (e != cudaSuccess) return fail3(c, RLBM_ENOMEM, "read-out buffer");
     c->out_cap = need;
   }

@@ -106,6 +106,40 @@ class Lattice:
         return out
 
 
+# The callbacks handed to rlbm_set_allocator stay referenced for the life of
+# the process: a context frees through the pair it was created with.
+_ALLOCATORS = []
+
+
+def _torch_alloc(nbytes, device, stream, user):
+    try:
+        import torch
+        return torch.cuda.caching_allocator_alloc(int(nbytes), device=int(device), stream=int(stream or 0))
+    except Exception:
+        return None            # the library reports ENOMEM
+
+
+def _torch_free(ptr, user):
+    try:
+        import torch
+        torch.cuda.caching_allocator_delete(int(ptr))
+    except Exception:
+        pass
+
+
+def use_torch_allocator():
+    """Contexts created from now on (2D and 3D) take their device memory from
+    torch's caching allocator, on the context's stream (rlbm_set_allocator)."""
+    pair = (A.ALLOC_FN(_torch_alloc), A.FREE_FN(_torch_free))
+    _ALLOCATORS.append(pair)
+    A.check(A.load().rlbm_set_allocator(C.cast(pair[0], C.c_void_p), C.cast(pair[1], C.c_void_p), None))
+
+
+def use_cuda_malloc():
+    """Contexts created from now on allocate with cudaMalloc (the default)."""
+    A.check(A.load().rlbm_set_allocator(None, None, None))
+
+
 def batch_step(lattices, k=1):
     """Advance every lattice by k steps as one batch (rlbm_batch_step)."""
     L = A.load()

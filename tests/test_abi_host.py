@@ -182,3 +182,17 @@ def test_init_device_refuses_fields_it_cannot_read():
     for bad in (np.zeros(12), ok, torch.zeros(12, dtype=torch.float32), torch.zeros(11, dtype=torch.float64)):
         with pytest.raises(ValueError):
             lat.init_device(bad, ok, ok, ok)
+
+
+def test_allocator_setter_validates_and_resets(lib):
+    from paper_1703_04605_gb300 import use_cuda_malloc, use_torch_allocator
+    fa = A.ALLOC_FN(lambda nbytes, dev, stream, user: None)
+    ff = A.FREE_FN(lambda ptr, user: None)
+    alloc, free = C.cast(fa, C.c_void_p), C.cast(ff, C.c_void_p)
+    assert lib.rlbm_set_allocator(alloc, None, None) == A.RLBM_EINVAL
+    assert lib.rlbm_set_allocator(None, free, None) == A.RLBM_EINVAL
+    assert b"both" in lib.rlbm_last_error(None)
+    assert lib.rlbm_set_allocator(alloc, free, None) == A.RLBM_OK
+    assert lib.rlbm_set_allocator(None, None, None) == A.RLBM_OK
+    use_torch_allocator()           # installs ctypes callbacks; no device is touched
+    use_cuda_malloc()
