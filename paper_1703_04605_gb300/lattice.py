@@ -6,6 +6,12 @@ import numpy as np
 from . import _abi as A
 
 
+def _dtype_code(dtype, allowed):
+    if dtype not in allowed:
+        raise ValueError("dtype must be one of %s, not %r" % (", ".join(repr(d) for d in allowed), dtype))
+    return A.DTYPES[dtype]
+
+
 def _default_stream():
     try:
         import torch
@@ -33,7 +39,8 @@ class Lattice:
         st = A.Stencil(len(groups), self._groups, float(v0))
         if stream is None:
             stream = _default_stream()
-        A.check(L.rlbm_create(C.byref(st), float(m), float(tau), int(Nx), int(Ny), A.DTYPES[dtype],
+        code = _dtype_code(dtype, ("f64", "f32", "bf16dev"))
+        A.check(L.rlbm_create(C.byref(st), float(m), float(tau), int(Nx), int(Ny), code,
                               C.c_void_p(stream) if stream else None, C.byref(self._ctx)))
         self.Nx, self.Ny = int(Nx), int(Ny)
         self.dtype = dtype
@@ -170,7 +177,8 @@ class Lattice3D:
         st = A.Stencil(len(groups), self._groups, float(v0))
         if stream is None:
             stream = _default_stream()
-        A.check(L.rlbm3_create(C.byref(st), float(m), float(tau), int(Nx), int(Ny), int(Nz), A.DTYPES[dtype],
+        code = _dtype_code(dtype, ("f64", "f32", "bf16dev"))
+        A.check(L.rlbm3_create(C.byref(st), float(m), float(tau), int(Nx), int(Ny), int(Nz), code,
                                C.c_void_p(stream) if stream else None, C.byref(self._ctx)), None, True)
         self.Nx, self.Ny, self.Nz = int(Nx), int(Ny), int(Nz)
         self.dtype = dtype

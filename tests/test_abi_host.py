@@ -196,3 +196,11 @@ def test_allocator_setter_validates_and_resets(lib):
     assert lib.rlbm_set_allocator(None, None, None) == A.RLBM_OK
     use_torch_allocator()           # installs ctypes callbacks; no device is touched
     use_cuda_malloc()
+
+
+def test_binding_rejects_unknown_storage_types():
+    from paper_1703_04605_gb300 import Lattice, Lattice3D
+    with pytest.raises(ValueError, match="dtype"):
+        Lattice([5, 12, 14, 17, 21, 26], 1.0, 0.8, 8, 8, dtype="f16")
+    with pytest.raises(ValueError, match="dtype"):
+        Lattice3D([5, 12, 14, 17, 21, 26], 1.0, 0.8, 4, 4, 4, dtype="fp32")
