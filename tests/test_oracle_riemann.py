@@ -13,7 +13,9 @@ Maxwell-Juttner fluid, with no lattice code in the reference
   fan agree with the ideal-fluid solution within what viscosity leaves
   (measured: P* 0.17 %, v* 0.03 %, shock 0.15 cells of 372, fan 1.6 %);
 * the strong Riemann problem of the mass sweep (Sec. V) on the library's
-  stencils at m/T_R = 0.36, 1, 4, 5, against the same exact solution."""
+  stencils at m/T_R = 0.36, 1, 4, 5, against the same exact solution;
+* its small-amplitude limit: a density pulse moves at the adiabatic sound
+  speed on the same stencils."""
 import math
 
 import numpy as np
@@ -153,3 +155,32 @@ def test_oracle_strong_riemann_sweep(m):
     assert abs(np.median(v[w]) / ex["v"] - 1.0) < 5e-3
     xs = _crossing(x, P, 0.5 * (ex["P"] + nR * TR_), (x > 0) & (x < Nx / 4))
     assert abs(xs / xsh - 1.0) < 0.025
+
+
+@pytest.mark.parametrize("m", W.RIEMANN_SWEEP_M)
+def test_oracle_sound_speed(m):
+    """The small-amplitude limit of the same physics: a 1e-3 density pulse on
+    the oracle lattice (tau = 0.55) splits into acoustic pulses that move at
+    the adiabatic sound speed of the Maxwell-Juttner gas,
+    c_s^2 = (c_p/c_v) T/H (measured within 0.23 % at m/T_R = 0.36 and better
+    for heavier gases)."""
+    from paper_1703_04605_gb300 import stencils
+    groups, mb = stencils.choose(m)
+    v0 = SWEEP_V0[m]
+    Nx = 1024
+    f = W.sound_pulse(Nx, 1, amp=1e-3, sigma=24.0)
+    cs = R.sound_speed(1.0, mb)
+    lat = OL.make_lattice(groups, mb, v0, 0.55, (1, Nx))
+    lat.init(f["n"], f["ux"], f["uy"], f["T"])
+    steps = [int(round(d / (cs / v0))) for d in (120.0, 240.0)]
+    pos, done = [], 0
+    for k in steps:
+        lat.step(k - done)
+        done = k
+        dn = lat.macros()["n"][0] - 1.0
+        lo = Nx // 2 + 60
+        j = lo + int(np.argmax(dn[lo:]))
+        a, b, c = dn[j - 1], dn[j], dn[j + 1]
+        pos.append(j + 0.5 + 0.5 * (a - c) / (a - 2 * b + c))    # parabolic peak
+    speed = (pos[1] - pos[0]) / (steps[1] - steps[0]) * v0          # one cell per step is v0
+    assert abs(speed / cs - 1.0) < 5e-3
