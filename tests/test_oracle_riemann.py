@@ -15,7 +15,8 @@ Maxwell-Juttner fluid, with no lattice code in the reference
 * the strong Riemann problem of the mass sweep (Sec. V) on the library's
   stencils at m/T_R = 0.36, 1, 4, 5, against the same exact solution;
 * its small-amplitude limit: a density pulse moves at the adiabatic sound
-  speed on the same stencils."""
+  speed on the same stencils;
+* the third-order scheme on the shock tube's states at m/T_R = 5."""
 import math
 
 import numpy as np
@@ -184,3 +185,31 @@ def test_oracle_sound_speed(m):
         pos.append(j + 0.5 + 0.5 * (a - c) / (a - 2 * b + c))    # parabolic peak
     speed = (pos[1] - pos[0]) / (steps[1] - steps[0]) * v0          # one cell per step is v0
     assert abs(speed / cs - 1.0) < 5e-3
+
+
+def test_oracle_third_order_shock_tube():
+    """The third-order scheme (Sec. III at N = 3) on the shock tube's states
+    at m/T_R = 5 (stencil G1,G2,G5,G6,G7,G9,G10,G11,G12,G13,G15, eta/s = 0.1,
+    t = 500 dx/c) against the same ideal-fluid solution (measured: P* within
+    0.25 %, v* within 0.12 %, the shock within 0.6 % of V t)."""
+    st = W.STENCIL_O3
+    Nx = 1600
+    x0 = Nx // 2
+    f = W.sod(Nx, 1, n=(NL, NR), T=(TL, TR), x0=x0)
+    v0 = st["v0"]
+    steps = int(round(500.0 * v0))
+    lat = OL.make_lattice(st["groups"], st["m"], v0, W.sod_tau(0.1, v0=v0), (1, Nx))
+    assert lat.order == 3
+    lat.init(f["n"], f["ux"], f["uy"], f["T"])
+    lat.step(steps)
+    mac = lat.macros()
+    P, v = (mac["n"] * mac["T"])[0], mac["ux"][0]
+    x = np.arange(Nx) + 0.5 - x0
+    ex = R.solve(NL, TL, NR, TR, st["m"])
+    t_c = steps / v0
+    xc, xsh = ex["v"] * t_c, ex["V"] * t_c
+    w = (x > xc + 0.2 * (xsh - xc)) & (x < xc + 0.6 * (xsh - xc))
+    assert abs(np.median(P[w]) / ex["P"] - 1.0) < 1e-2
+    assert abs(np.median(v[w]) / ex["v"] - 1.0) < 5e-3
+    xs = _crossing(x, P, 0.5 * (ex["P"] + NR * TR), (x > 0) & (x < Nx / 4))
+    assert abs(xs / xsh - 1.0) < 0.015
