@@ -15,7 +15,8 @@ moments mu_j per unit density
                         p^a p^b -> (e+P) U^a U^b - P eta^ab   (Eq. 8, 28-29)
 
 f_i^eq = n w_i sum_j c_j phi_j(p_i) with G c = mu.
-"""
+
+TEST INFRASTRUCTURE ONLY (see the package docstring)."""
 import numpy as np
 
 from . import polynomials as P

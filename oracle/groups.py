@@ -10,7 +10,8 @@ Misprint: the printed lengths of rows 17 and 18 are exchanged.  Row 17,
 (3,2,2), has length sqrt(17), and row 18, (3,3,1), has length sqrt(19); the
 table prints sqrt(19) and sqrt(17).  Every computation therefore takes the
 length from the vector (``length2``), never from the printed column.
-"""
+
+TEST INFRASTRUCTURE ONLY (see the package docstring)."""
 import itertools
 import math
 

@@ -20,7 +20,8 @@ Per site (Sec. II A, Eq. 16-20, 28-29, 49):
 Metric diag(1,-1,-1,-1) (Sec. II), c = k_B = T_R = 1, lattice units dx = 1.
 For the folded stencil the z components are absent from the moments (they
 vanish by symmetry while U^z = 0) and the eigenproblem is 3 x 3.
-"""
+
+TEST INFRASTRUCTURE ONLY (see the package docstring)."""
 import numpy as np
 
 from . import equilibrium as EQ

@@ -24,7 +24,8 @@ independent projection):
    appears in J_00 (J_00 has p0 (3/X - 3)), and the last term is -T/T_R:
    b_00 = [mbar K3/K2(zeta) U_0^2 + 3(1/X - 1) U_0 + K1/K2(zeta) Y - T/T_R]/(sqrt3 C)
    with Y the mbar-fraction printed in b_00.
-"""
+
+TEST INFRASTRUCTURE ONLY (see the package docstring)."""
 import math
 
 import numpy as np

@@ -21,7 +21,8 @@ every monomial of degree <= 6, and the eleven monomials of
 independent components at third order).  It is solved in 60-digit
 decimal arithmetic (the system is ill conditioned for small mbar, Sec. III D)
 and rounded to FP64 at the end.
-"""
+
+TEST INFRASTRUCTURE ONLY (see the package docstring)."""
 from decimal import Decimal
 
 import numpy as np

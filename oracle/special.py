@@ -13,7 +13,8 @@ Extended precision (python ``decimal``, 60 significant digits):
 
 FP64: ``kv`` (scipy's Bessel K, a library routine) and the ratio
 R(zeta) = K1(zeta)/K2(zeta) used by the equation of state, Eq. 28.
-"""
+
+TEST INFRASTRUCTURE ONLY (see the package docstring)."""
 from decimal import Decimal, getcontext
 
 import numpy as np
