@@ -53,18 +53,22 @@ extern "C" rlbm_status rlbm_moments_noalloc(const int* groups, int ngroups, doub
                                             int Ny, const double* f_dev, double* out_host, unsigned mask,
                                             void* cuda_stream) {
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (!groups || ngroups != 6 || !f_dev || !out_host || Nx < 1 || Ny < 1 || !(v0 > 0))
+  if (!groups || !f_dev || !out_host || Nx < 1 || Ny < 1 || !(v0 > 0))
     return fail(RLBM_EINVAL, "invalid argument");
+  if (ngroups != 6)
+    return fail(RLBM_EINVAL, "rlbm_moments_noalloc takes six-group (second-order) stencils only; got " +
+                                 std::to_string(ngroups) + " groups");
   if (mask == 0 || (mask & ~0x7Fu)) return fail(RLBM_EINVAL, "mask must select 1..7 known fields");
   size_t planes = 0;
   for (unsigned b : {RLBM_M_N, RLBM_M_UX, RLBM_M_UY, RLBM_M_T, RLBM_M_E})
     if (mask & b) ++planes;
   if (mask & RLBM_M_NVEC) planes += 3;
   if (mask & RLBM_M_TMN) planes += 6;
-  const size_t nsite = (size_t)Nx * (size_t)Ny;
-  if (planes * nsite > kOutDoubles) {
-    return fail(RLBM_EINVAL, "result of " + std::to_string(planes * nsite) +
-                                 " doubles exceeds the static scratch of " + std::to_string(kOutDoubles) +
+  const size_t nsite = (size_t)Nx * (size_t)Ny;   // < 2^62: no wrap
+  // compared by division: planes * nsite could wrap for huge Nx, Ny
+  if (nsite > kOutDoubles / planes) {
+    return fail(RLBM_EINVAL, "result of " + std::to_string(planes) + " planes x " + std::to_string(nsite) +
+                                 " sites exceeds the static scratch of " + std::to_string(kOutDoubles) +
                                  " doubles (8 MiB array)");
   }
   // set-up, once per device, with that device current
@@ -79,6 +83,9 @@ extern "C" rlbm_status rlbm_moments_noalloc(const int* groups, int ngroups, doub
     const auto& t64 = ratio_table64();
     e = cudaMemcpy(static_cast<unsigned char*>(ptr) + kTableOffset, t64.data(), kTableBytes,
                    cudaMemcpyHostToDevice);
+    // a pageable upload may return before the copy lands; the read-outs run on
+    // caller streams that need not be ordered after the legacy stream
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return fail(RLBM_ECUDA, std::string("table upload: ") + cudaGetErrorString(e));
     g_addr[dev] = static_cast<unsigned char*>(ptr);
     g_ready[dev] = true;

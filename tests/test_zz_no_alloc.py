@@ -1,8 +1,9 @@
 """rlbm_moments_noalloc: the read-out for callers that may not allocate device
 memory (it keeps its scratch in a static device array).  Its result must match
-rlbm_moments of a normal context on the same state, within the FP64 parity
-tolerance, on two calls in a row (the second call reuses the scratch left by
-the first).  Collected last on purpose."""
+rlbm_moments of a normal context on the same state, and the oracle's macroscopic
+fields of that state, within the FP64 parity tolerance, on two calls in a row
+(the second call reuses the scratch left by the first).  Collected last on
+purpose."""
 import ctypes as C
 
 import numpy as np
@@ -34,12 +35,14 @@ def test_noalloc_readout_matches_rlbm_moments_twice():
     o = oracle_lattice(st, tau, (Ny, Nx))
     o.init(f["n"], f["ux"], f["uy"], f["T"])
     pops = [o.f.copy()]
+    macs = [o.macros()]
     o.step(1)
     pops.append(o.f.copy())
+    macs.append(o.macros())
     groups = A.int_array(st["groups"])
     stream = torch.cuda.current_stream()
     size = 11 * Nx * Ny
-    for fpop, ref in zip(pops, refs):
+    for fpop, ref, mac in zip(pops, refs, macs):
         dev = torch.from_numpy(np.ascontiguousarray(fpop)).cuda()
         out = np.full(size, np.nan)
         s = L.rlbm_moments_noalloc(groups, 6, st["m"], st["v0"], Nx, Ny, C.c_void_p(dev.data_ptr()),
@@ -55,6 +58,32 @@ def test_noalloc_readout_matches_rlbm_moments_twice():
         assert np.max(np.abs(got["uy"] - ref["uy"])) < 1e-12 * umax
         for k in ("e", "T00", "T0x", "T0y", "Txx", "Txy", "Tyy"):
             assert np.max(np.abs(got[k] - ref[k])) < 1e-12 * np.abs(ref["T00"]).max(), k
+        # and the oracle's fields of the same populations
+        assert np.max(np.abs(got["n"] / mac["n"] - 1)) < 1e-12
+        assert np.max(np.abs(got["T"] / mac["T"] - 1)) < 1e-12
+        umax = max(np.abs(mac["ux"]).max(), np.abs(mac["uy"]).max())
+        assert np.max(np.abs(got["ux"] - mac["ux"])) < 1e-12 * umax
+        assert np.max(np.abs(got["uy"] - mac["uy"])) < 1e-12 * umax
+        escale = np.abs(mac["Tmn"][..., 0, 0]).max()
+        assert np.max(np.abs(got["e"] - mac["e"])) < 1e-12 * escale
+        for k, (a, b) in zip(("T00", "T0x", "T0y", "Txx", "Txy", "Tyy"),
+                             ((0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2))):
+            assert np.max(np.abs(got[k] - mac["Tmn"][..., a, b])) < 1e-12 * escale, k
+
+
+def test_noalloc_rejects_eleven_group_stencils():
+    import torch
+    from paper_1703_04605_gb300 import build, _abi as A
+    build.build()
+    L = A.load()
+    st = W.STENCIL_O3
+    groups = A.int_array(st["groups"])
+    dummy = torch.zeros(8, dtype=torch.float64, device="cuda")
+    out = np.zeros(8)
+    s = L.rlbm_moments_noalloc(groups, 11, st["m"], st["v0"], 2, 2, C.c_void_p(dummy.data_ptr()),
+                               out.ctypes.data_as(C.POINTER(C.c_double)), A.M_N, None)
+    assert s == A.RLBM_EINVAL
+    assert b"six-group" in L.rlbm_last_error(None)
 
 
 def test_noalloc_rejects_results_beyond_the_static_scratch():
