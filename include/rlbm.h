@@ -59,10 +59,15 @@ typedef enum {
                         compiled maximum)                                      */
 } rlbm_status;
 
-/* Population storage.  Arithmetic: F64 computes everything in FP64; F32 and
- * BF16_DEV accumulate in FP32 and solve the Landau frame and the EOS with an
- * FP64 correction step.  BF16_DEV stores d_i = f_i - f_i^eq in bfloat16 plus
- * per-site FP32 macroscopic fields used to rebuild f_i^eq. */
+/* Population storage.  Arithmetic: F64 computes everything in FP64.  F32
+ * and BF16_DEV accumulate the moments in FP32, solve the Landau frame in
+ * FP32 and the EOS by FP32 Newton iterations finished by one FP64 Newton
+ * step with the FP64 R(zeta) table (the only FP64 work of their step).
+ * BF16_DEV stores, per population, the bfloat16 deviation of f_i from a
+ * reference polynomial mult_i (a + b_x n_x + b_y n_y + q (n_x^2 + n_y^2))
+ * of the writing site's equilibrium, and beside the populations the four
+ * bfloat16 coefficients (a, b_x, b_y, q) of each of the six groups per site
+ * (6 x 8 bytes), from which the reader rebuilds f_i. */
 typedef enum { RLBM_F64 = 0, RLBM_F32 = 1, RLBM_BF16_DEV = 2 } rlbm_dtype;
 
 /* A stencil (Sec. III C-D): six distinct groups of Table I (ids 1..84) for
@@ -107,6 +112,8 @@ typedef struct {
                                {4,8,14,15,16,17,18,21,22,23,26} (FP32
                                storage, lattice at least a halo wide)          */
   int order;                /* expansion order of f^eq: 2 or 3               */
+  int extended_sums;        /* 1: the FP32 step forms its moment sums with
+                               extended precision (rlbm_set_extended_sums)   */
 } rlbm_info;
 
 /* Create a lattice context.
@@ -137,6 +144,21 @@ rlbm_status rlbm_init_device(rlbm_ctx* ctx, const double* n, const double* ux, c
 /* Advance nsteps >= 0 time steps (Eq. 49 applied nsteps times).
  * Asynchronous on the context stream: returns after enqueueing. */
 rlbm_status rlbm_step(rlbm_ctx* ctx, int nsteps);
+
+/* Moment sums of the FP32 step on a compiled second-order stencil
+ * (rlbm_info.kernel 1..4, FP32 storage).  on = 1: the conserved moments N^a
+ * and the kinetic moments K^a = T^0a - m N^a (Eq. 4-5, 18) are accumulated
+ * to about 2^-40 relative -- each pulled value split exactly into a part on a
+ * per-group grid and a small remainder, the group sums combined by
+ * error-free products and sums -- and e - m n (Eq. 19-20) is formed from K^a,
+ * without cancelling the rest-mass energy.  This keeps FP32 storage within
+ * 1e-5 of FP64 over thousands of steps on steep, sloshing flows of massive
+ * particles, where plain FP32 moment sums drift (they break mass and energy
+ * conservation by about one rounding per step and site).  on = 0: plain FP32
+ * sums (fewer instructions).  Takes effect at the next step; cached batch
+ * graphs of the context are dropped.  Errors: EINVAL (NULL ctx), ENOTSUP
+ * (no compiled FP32 second-order kernel for this context). */
+rlbm_status rlbm_set_extended_sums(rlbm_ctx* ctx, int on);
 
 /* Macroscopic fields of the current pre-collision state f(., t).
  * mask selects fields (bits below); out receives, in bit order, one
@@ -287,18 +309,24 @@ void rlbm3_destroy(rlbm_ctx3* ctx);
  * layout [Q][Ny][Nx] doubles.  The populations are read as they are (no
  * streaming).  out_host receives the planes selected by mask (same layout as
  * rlbm_moments).  groups/m/v0 describe the stencil as in rlbm_create
- * (v0 > 0 required).  Runs on cuda_stream and synchronises it.
+ * (v0 > 0 required); only six-group (second-order) stencils are accepted,
+ * any other ngroups is RLBM_EINVAL.
+ *
+ * Synchronisation: every call copies the result and the error word back to
+ * the host and synchronises cuda_stream before it returns, so it must never
+ * be called while any stream is being captured into a CUDA graph.
  *
  * Memory: allocates no device memory.  Its device scratch -- the error
  * word, the R(zeta) table and the result staging -- is one static 8 MiB
  * array that every GPU loading the library holds until exit; results larger
  * than 1,045,728 doubles (planes x Nx x Ny) are rejected with RLBM_EINVAL.
- * The first call on a device sets the array up (symbol address, table copy),
- * so that call must come before any stream capture; the first call for a new
- * stencil or lattice size builds host tables.  All calls share the array and
- * it keeps the last call's contents (the error word is cleared per call):
- * calls that overlap on the GPU, from any thread or stream, race.  Errors
- * are described by rlbm_last_error(NULL). */
+ * The first call on a device sets the array up (symbol address, table copy,
+ * then a device synchronisation); the first call for a new stencil or
+ * lattice size builds host tables.  All calls share the array, which keeps
+ * the last call's contents (the error word is cleared per call).  Within one
+ * process the calls are serialised by a lock and each one synchronises its
+ * stream, so they cannot overlap; two processes on one GPU have separate
+ * copies of the array.  Errors are described by rlbm_last_error(NULL). */
 rlbm_status rlbm_moments_noalloc(const int* groups, int ngroups, double m, double v0, int Nx, int Ny,
                                  const double* f_dev, double* out_host, unsigned mask,
                                  void* cuda_stream);
@@ -323,6 +351,14 @@ rlbm_status rlbm_quadrature_window(const int* groups, int ngroups, double m, dou
  * host by the same formulas the kernels use (precision 64 or 32).  For
  * validation of the tables. */
 double rlbm_bessel_ratio(double zeta, int precision);
+
+/* Measurement helper (not part of the method): the device's FP64 fused
+ * multiply-add throughput in TFLOP/s (2 flops per FMA), timed with CUDA
+ * events on cuda_stream (NULL = legacy default stream) as the best of five
+ * launches of a kernel whose threads run eight independent FMA chains each.
+ * The denominator of the FP64 step kernels' ALU roofline.  Synchronises the
+ * stream; about 0.1 s.  Errors: EINVAL (NULL tflops), ECUDA. */
+rlbm_status rlbm_fp64_fma_rate(void* cuda_stream, double* tflops);
 
 /* Library version string. */
 const char* rlbm_version(void);

@@ -154,6 +154,22 @@ def test_null_context_calls(lib):
     assert lib.rlbm_batch_tuning(null2, 2, None, None) == A.RLBM_EINVAL
 
 
+def test_noalloc_size_check_does_not_wrap(lib):
+    """planes x Nx x Ny beyond 2^64 must still be rejected by the size check,
+    which runs before any device call (the pointer is never dereferenced)."""
+    g = A.int_array([5, 12, 14, 17, 21, 26])
+    out = np.zeros(1)
+    big = 2 ** 31 - 1                                  # 11 x big^2 wraps 64 bits
+    s = lib.rlbm_moments_noalloc(g, 6, 1.0, 0.23342, big, big, C.c_void_p(256),
+                                 out.ctypes.data_as(C.POINTER(C.c_double)), 0x7F, None)
+    assert s == A.RLBM_EINVAL
+    assert b"static scratch" in lib.rlbm_last_error(None)
+    s = lib.rlbm_moments_noalloc(g, 11, 1.0, 0.23342, 4, 4, C.c_void_p(256),
+                                 out.ctypes.data_as(C.POINTER(C.c_double)), 0x01, None)
+    assert s == A.RLBM_EINVAL
+    assert b"six-group" in lib.rlbm_last_error(None)
+
+
 def test_3d_entry_points_without_device(lib):
     g = A.int_array([1, 2, 3, 4, 5, 6])
     st = A.Stencil(6, g, 0.398)
