@@ -43,33 +43,104 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+class _NVMLClocks:
+    """Read-only NVML queries through ctypes (SM clock, its maximum and the
+    clock-event reasons); the device is matched to the CUDA device by PCI bus
+    id when torch reports it, else by index."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, gpu_index):
+        import ctypes
+        self.C = ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        bus = None
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(gpu_index)
+            bus = ("%08X:%02X:%02X.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)).encode()
+        except Exception:
+            bus = None
+        if not (bus and lib.nvmlDeviceGetHandleByPciBusId_v2(bus, ctypes.byref(h)) == 0):
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(gpu_index), ctypes.byref(h)) != 0:
+                raise RuntimeError("no NVML handle")
+        self.lib, self.h = lib, h
+        self.reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint()
+        self.max_mhz = float(mx.value) if lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0 else None
+
+    def sample(self):
+        C = self.C
+        mhz, rs = C.c_uint(), C.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.h, 1, C.byref(mhz)) != 0:
+            return None
+        if self.reasons_fn(self.h, C.byref(rs)) != 0:
+            return None
+        return float(mhz.value), [nm for bit, nm in self.REASONS.items() if rs.value & bit]
+
+
 class ClockSampler:
-    """nvidia-smi samples during the timed region (read-only queries)."""
+    """SM clock samples during the timed region (read-only queries): NVML
+    polled every 2 ms from a thread where libnvidia-ml is loadable, else
+    nvidia-smi every 20 ms.  Started before the region and stopped after it."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index):
         self.idx = gpu_index
-        self.rows = []
+        self.rows = []          # (sm_mhz, max_mhz, [reasons])
         self.proc = None
+        self.nvml = None
+        self.stop = threading.Event()
+        self.source = None
 
     def __enter__(self):
         try:
+            self.nvml = _NVMLClocks(self.idx)
+            self.source = "nvml, 2 ms"
+            self.t = threading.Thread(target=self._poll, daemon=True)
+            self.t.start()
+            return self
+        except Exception:
+            self.nvml = None
+        try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.source = "nvidia-smi, 20 ms"
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            time.sleep(0.3)     # the first query row is out before the region starts
         except Exception:
             self.proc = None
         return self
 
+    def _poll(self):
+        while not self.stop.is_set():
+            r = self.nvml.sample()
+            if r:
+                self.rows.append((r[0], self.nvml.max_mhz, r[1]))
+            time.sleep(0.002)
+
     def _read(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.proc.stdout:
-            self.rows.append([c.strip() for c in line.split(",")])
+            r = [c.strip() for c in line.split(",")]
+            try:
+                self.rows.append((float(r[1]), float(r[2]),
+                                  [nm for k, nm in enumerate(names) if r[5 + k].lower().startswith("active")]))
+            except Exception:
+                continue
 
     def __exit__(self, *exc):
+        self.stop.set()
+        if self.nvml:
+            self.t.join(timeout=1)
         if self.proc:
             self.proc.terminate()
             try:
@@ -78,19 +149,11 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
-            try:
-                sm.append(float(r[1]))
-                mx = float(r[2])
-                for k, nm in enumerate(names):
-                    if r[5 + k].lower().startswith("active"):
-                        reasons.add(nm)
-            except Exception:
-                continue
+        sm = [r[0] for r in self.rows]
+        mx = next((r[1] for r in reversed(self.rows) if r[1]), None)
+        reasons = sorted({nm for r in self.rows for nm in r[2]})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": reasons, "samples": len(sm), "source": self.source}
 
 
 def cpu_baseline(seconds=12.0, side=96, procs=None):
@@ -100,6 +163,7 @@ def cpu_baseline(seconds=12.0, side=96, procs=None):
     amplitudes and seed) for about `seconds` of CPU time.  Value = the site
     updates of all processes / wall time."""
     procs = procs or os.cpu_count() or 1
+    w0 = time.perf_counter()
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = (
         "import sys, time, json; sys.path.insert(0, %r)\n"
@@ -128,6 +192,8 @@ def cpu_baseline(seconds=12.0, side=96, procs=None):
         return {"value": None, "unit": "MLUPS", "cores": procs, "kind": "oracle", "sample": "failed: " + errs[0]}
     mlups = sum(side * side * r["steps"] / r["seconds"] for r in res) / 1e6
     return {"value": mlups, "unit": "MLUPS", "cores": len(res), "kind": "oracle",
+            "wall_ms": (time.perf_counter() - w0) * 1e3,
+            "site_updates": sum(side * side * r["steps"] for r in res),
             "sample": "%d processes x one %dx%d lattice of the same generator, %d-%d steps each in %.1f s wall, "
                       "1 thread each" % (len(res), side, side, min(r["steps"] for r in res),
                                          max(r["steps"] for r in res), max(r["seconds"] for r in res))}
@@ -210,13 +276,32 @@ FP64_FLOP_PER_SITE = {"step_f64_kernel/5,12,14,17,21,26": 3271.0,
                       "step_o3_kernel/1,2,5,6,7,9,10,11,12,13,15": 7352.0}
 
 
+_FP64_PEAK = []
+
+
+def fp64_peak():
+    """(TFLOP/s, kind): the FP64 FMA rate measured on this GPU by the
+    library's own probe (rlbm_fp64_fma_rate, CUDA events), once per process;
+    the nominal figure if the probe fails."""
+    if not _FP64_PEAK:
+        import ctypes as C
+        from paper_1703_04605_gb300 import _abi as A
+        v = C.c_double()
+        ok = A.load().rlbm_fp64_fma_rate(None, C.byref(v)) == A.RLBM_OK and v.value > 0
+        _FP64_PEAK.append((v.value, "measured (rlbm_fp64_fma_rate: FMA chains, best of 5, CUDA events)")
+                          if ok else (FP64_PEAK_TFLOPS, "nominal"))
+    return _FP64_PEAK[0]
+
+
 def fp64_alu(mlups, key):
     flop = FP64_FLOP_PER_SITE.get(key)
     if flop is None:
         return None
     achieved = mlups * 1e6 * flop / 1e12
-    return {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-            "peak_kind": "nominal", "frac": achieved / FP64_PEAK_TFLOPS, "flop_per_site": flop,
+    peak, kind = fp64_peak()
+    return {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": peak,
+            "peak_kind": kind, "frac": achieved / peak, "flop_per_site": flop,
+            "nominal_peak": FP64_PEAK_TFLOPS,
             "flop_source": "ncu FP64 instruction counts (profiles/fp64_kernels_alu_1024.md)"}
 
 
@@ -323,12 +408,17 @@ def run_reference(args):
     for _ in range(args.steps):
         vals.append(cpu_baseline(seconds=5.0, side=side))
     v = float(np.mean([d["value"] for d in vals]))
+    ms = float(np.mean([d["wall_ms"] for d in vals]))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": N_SIDE * N_SIDE / (v * 1e6) * 1e3, "higher_is_better": True, "dtype": "f64",
+            "ms_per_step": ms, "higher_is_better": True, "dtype": "f64",
             "data": "synthetic", "scaling": "weak",
-            "config": {"workload": WORKLOAD, "sample": "%dx%d lattice of the same generator per step" % (side, side),
-                       "ms_per_step": "one %dx%d step at the measured rate" % (N_SIDE, N_SIDE)},
+            "config": {"workload": WORKLOAD,
+                       "sample": "each bench step is one bounded sample of the workload: %s (%.1f M site updates "
+                                 "on average); value = the sum over the processes of their site-update rates"
+                                 % (vals[-1]["sample"], float(np.mean([d["site_updates"] for d in vals])) / 1e6),
+                       "ms_per_step": "wall time of one such sample (process start to last result), "
+                                      "not a %dx%d step" % (N_SIDE, N_SIDE)},
             "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": vals[-1]["cores"], "kind": "oracle",
                              "sample": vals[-1]["sample"]},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -853,22 +943,28 @@ def main():
     if rank == 0:
         pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in f.items()}
         hostf = {k: v.numpy() for k, v in pin.items()}
+        mask = 0x1F                                   # n, u_x, u_y, T, e
+        pout = torch.empty(lat.moments_size(mask), dtype=torch.float64, pin_memory=True).numpy()
         ke = max(10, args.steps)          # the device-timed region's step count
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         lat.init(hostf["n"], hostf["ux"], hostf["uy"], hostf["T"])
+        t1 = time.perf_counter()
         for _ in range(ke):
             lat.step(1)
             lat.sync()
-        out = lat.moments()
-        t1 = time.perf_counter()
+        t2 = time.perf_counter()
+        out = lat.moments(mask, out=pout)
+        t3 = time.perf_counter()
         assert np.isfinite(out["n"]).all()
-        e2e = {"value": sites * ke / (t1 - t0) / 1e6, "unit": "MLUPS",
+        e2e = {"value": sites * ke / (t3 - t0) / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": int(4 * 8 * sites / ke),
                "d2h_bytes_per_step": int(4 + 5 * 8 * sites / ke),
                "steps": ke,
-               "region": "rlbm_init from pinned host fields, %d steps with the status word read back "
-                         "after each, rlbm_moments of n, u_x, u_y, T, e back to the host" % ke}
+               "breakdown_ms": {"init": (t1 - t0) * 1e3, "steps": (t2 - t1) * 1e3, "readout": (t3 - t2) * 1e3},
+               "region": "rlbm_init from pinned host fields (upload overlapped with the host validation "
+                         "scan, then the init kernel), %d steps with the status word read back after each, "
+                         "rlbm_moments of n, u_x, u_y, T, e into a pinned host buffer" % ke}
     lat.close()
 
     if rank != 0:

@@ -23,7 +23,7 @@ MASK_PLANES3 = [(M_N, ["n"]), (M_UX, ["ux"]), (M_UY, ["uy"]), (M_T, ["T"]), (M_E
 EXPORTS = ["rlbm_create", "rlbm_init", "rlbm_init_device", "rlbm_step", "rlbm_moments",
            "rlbm_moments_size", "rlbm_sync", "rlbm_get_info", "rlbm_last_error", "rlbm_destroy",
            "rlbm_quadrature_weights", "rlbm_quadrature_window", "rlbm_bessel_ratio", "rlbm_version",
-           "rlbm_moments_noalloc", "rlbm_batch_step", "rlbm_batch_tuning", "rlbm_set_allocator",
+           "rlbm_moments_noalloc", "rlbm_batch_step", "rlbm_set_extended_sums", "rlbm_fp64_fma_rate", "rlbm_batch_tuning", "rlbm_set_allocator",
            "rlbm3_create", "rlbm3_init", "rlbm3_step", "rlbm3_moments", "rlbm3_moments_size", "rlbm3_sync",
            "rlbm3_get_info", "rlbm3_last_error", "rlbm3_destroy"]
 
@@ -42,7 +42,7 @@ class Info(C.Structure):
                 ("dtype", C.c_int), ("m", C.c_double), ("tau", C.c_double), ("v0", C.c_double),
                 ("w_group", C.c_double * 11), ("t", C.c_longlong), ("bytes_per_site", C.c_size_t),
                 ("extra_bytes_per_site", C.c_size_t), ("device_bytes", C.c_size_t), ("kernel", C.c_int),
-                ("order", C.c_int)]
+                ("order", C.c_int), ("extended_sums", C.c_int)]
 
 
 class Info3(C.Structure):
@@ -84,6 +84,8 @@ def load():
         "rlbm_init": (C.c_int, [P, dp, dp, dp, dp]),
         "rlbm_init_device": (C.c_int, [P, P, P, P, P]),
         "rlbm_step": (C.c_int, [P, C.c_int]),
+        "rlbm_set_extended_sums": (C.c_int, [P, C.c_int]),
+        "rlbm_fp64_fma_rate": (C.c_int, [P, dp]),
         "rlbm_moments": (C.c_int, [P, dp, C.c_uint]),
         "rlbm_moments_size": (C.c_size_t, [P, C.c_uint]),
         "rlbm_sync": (C.c_int, [P]),

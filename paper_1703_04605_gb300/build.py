@@ -14,7 +14,7 @@ LIB = os.path.join(PKG, "librlbm.so")
 
 CUDA_SOURCES = ["rlbm_kernels_f64.cu", "rlbm_kernels_f32.cu", "rlbm_kernels_io.cu",
                 "rlbm_fused_m1.cu", "rlbm_fused_g16.cu", "rlbm_fused_e5.cu", "rlbm_fused_s2.cu", "rlbm_noalloc.cu",
-                "rlbm_kernels3d.cu", "rlbm_fused3d.cu", "rlbm_kernels_o3.cu", "rlbm_fused_o3.cu"]
+                "rlbm_kernels3d.cu", "rlbm_fused3d.cu", "rlbm_kernels_o3.cu", "rlbm_fused_o3.cu", "rlbm_peak.cu"]
 CXX_SOURCES = ["rlbm_stencil.cpp", "rlbm_host.cpp", "rlbm_host3d.cpp"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -58,12 +58,12 @@ def build(force=False, verbose=False):
                      "-Xptxas", "-v", *inc, "-c", os.path.join(CSRC, src), "-o", obj])
     for src in CXX_SOURCES:
         obj = os.path.join(BUILD, src + ".o")
-        jobs.append(["g++", "-std=c++17", "-O2", "-fPIC", "-Wall", *inc, "-c",
+        jobs.append(["g++", "-std=c++17", "-O2", "-fPIC", "-Wall", "-pthread", *inc, "-c",
                      os.path.join(CSRC, src), "-o", obj])
     with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
         logs = list(ex.map(_run, jobs))
     objs = [os.path.join(BUILD, s + ".o") for s in CUDA_SOURCES + CXX_SOURCES]
-    libs = ["-lquadmath"] if platform.machine() in ("x86_64", "i686") else []
+    libs = (["-lquadmath"] if platform.machine() in ("x86_64", "i686") else []) + ["-lpthread"]
     tmp = LIB + ".tmp"
     _run([nvcc, *GENCODE, "-shared", "-o", tmp, *objs, *libs])
     os.replace(tmp, LIB)

@@ -23,6 +23,20 @@
 //    the EOS and the projections, which keeps the energy of f^eq equal to the
 //    Landau energy (Eq. 20, 28).
 //
+// Extended moment sums (template flag EX, FP32 storage): the deviation
+// moments N^a and K^a = T^0a - m N^a are formed to about 2^-40 relative
+// instead of FP32 rounding, because on long runs of steep, sloshing flows
+// (massive Sod tubes, thousands of steps) the FP32 rounding of the moment
+// sums breaks mass and energy conservation by about one rounding per step
+// and site, which adds up.  Each pulled d_i is split exactly into a part h_i
+// on a grid of its group (a power of two well below the group's reference
+// value) and a remainder l_i = d_i - h_i; sums of the h_i with integer
+// weights are exact in FP32, sums of the l_i lose only the rounding of
+// numbers 2^11 times smaller, and the six group sums are combined with the
+// group constants by error-free products and two-sums (float-float).  The
+// kinetic moments K^a are accumulated directly, so the energy above the rest
+// mass, e - m n, is formed without the cancellation of e and m n.
+//
 // BF16 deviation storage (template flag BF): the stored value is
 // d_i = (f_i - r_i) - ref_i(x), rounded to bfloat16, where ref_i(x) =
 // mult_i (a + b_x n_x + b_y n_y + q (n_x^2 + n_y^2)) uses the equilibrium
@@ -120,6 +134,136 @@ __device__ __forceinline__ void fused_acc_orbit(const float (&d)[Def::Q], float 
     s[g][4] = fmaf((float)(ax * ay), q - w, s[g][4]);
     s[g][5] = fmaf((float)(ay * ay), S, s[g][5]);
   }
+}
+
+// ---------------------------------------------------- extended moment sums
+// A value held as the unevaluated sum hi + lo of two FP32 numbers.
+struct FF {
+  float hi, lo;
+};
+
+// a + b = s + e exactly (two-sum; branch-free); the _rn intrinsics keep the
+// compiler from contracting or reassociating these operations.
+__device__ __forceinline__ float ex_two_sum(float a, float b, float& e) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return s;
+}
+
+// acc += (c.hi + c.lo)(xh + xl) with xh exact: the product c.hi xh and its
+// addition to acc.hi are error-free; the remaining small terms go to acc.lo.
+__device__ __forceinline__ void ex_acc(FF& acc, const HL& c, float xh, float xl) {
+  const float p = __fmul_rn(c.hi, xh);
+  const float pe = __fmaf_rn(c.hi, xh, -p);
+  float se;
+  acc.hi = ex_two_sum(acc.hi, p, se);
+  acc.lo += (se + pe) + fmaf(c.lo, xh, c.hi * xl);
+}
+
+// d = h + l exactly, h on the grid of spacing q, C = 1.5 2^23 q (|d| < 2^22 q)
+__device__ __forceinline__ void ex_split(float d, float C, float& h, float& l) {
+  h = __fsub_rn(__fadd_rn(d, C), C);
+  l = __fsub_rn(d, h);
+}
+
+// Running sums of one group: sums of h and of l with weights 1, n_x, n_y
+// (k = 0, 1, 2) and plain FP32 sums of d with n_x^2, n_x n_y, n_y^2.
+struct ExGroup {
+  float h[3], l[3], d[3];
+};
+
+// Moments of the extended path: N^0, N^x, N^y, K^0, K^x, K^y as float-float,
+// T^xx, T^xy, T^yy in FP32 (all deviations: the reference r_i excluded).
+struct ExMoments {
+  FF N0, Nx, Ny, K0, Kx, Ky;
+  float Txx, Txy, Tyy;
+};
+
+template <class Def, int K>
+__device__ __forceinline__ void ex_acc_orbit(const float (&d)[Def::Q], const float (&C)[6], ExGroup& s) {
+  constexpr int kind = Def::O.kind[K], g = Def::O.grp[K], ax = Def::O.ax[K], ay = Def::O.ay[K];
+  constexpr int i0 = Def::O.idx[K][0], i1 = Def::O.idx[K][1], i2 = Def::O.idx[K][2], i3 = Def::O.idx[K][3];
+  if constexpr (kind == 1) {
+    float h, l;
+    ex_split(d[i0], C[g], h, l);
+    s.h[0] = __fadd_rn(s.h[0], h);
+    s.l[0] += l;
+  } else if constexpr (kind == 2 || kind == 3) {
+    constexpr int j1 = kind == 2 ? i1 : i2;
+    constexpr int a = kind == 2 ? ax : ay;
+    constexpr int k = kind == 2 ? 1 : 2;
+    float h0, l0, h1, l1;
+    ex_split(d[i0], C[g], h0, l0);
+    ex_split(d[j1], C[g], h1, l1);
+    const float Sh = __fadd_rn(h0, h1), Dh = __fsub_rn(h0, h1);
+    const float Sl = l0 + l1, Dl = l0 - l1;
+    s.h[0] = __fadd_rn(s.h[0], Sh);
+    s.h[k] = __fmaf_rn((float)a, Dh, s.h[k]);
+    s.l[0] += Sl;
+    s.l[k] = fmaf((float)a, Dl, s.l[k]);
+    const float S = Sh + Sl;
+    s.d[kind == 2 ? 0 : 2] = fmaf((float)(a * a), S, s.d[kind == 2 ? 0 : 2]);
+  } else {
+    float h[4], l[4];
+    ex_split(d[i0], C[g], h[0], l[0]);
+    ex_split(d[i1], C[g], h[1], l[1]);
+    ex_split(d[i2], C[g], h[2], l[2]);
+    ex_split(d[i3], C[g], h[3], l[3]);
+    const float ph = __fadd_rn(h[0], h[1]), qh = __fsub_rn(h[0], h[1]);
+    const float rh = __fadd_rn(h[2], h[3]), wh = __fsub_rn(h[2], h[3]);
+    const float pl = l[0] + l[1], ql = l[0] - l[1], rl = l[2] + l[3], wl = l[2] - l[3];
+    const float Sh = __fadd_rn(ph, rh), Sl = pl + rl;
+    s.h[0] = __fadd_rn(s.h[0], Sh);
+    s.h[1] = __fmaf_rn((float)ax, __fadd_rn(qh, wh), s.h[1]);
+    s.h[2] = __fmaf_rn((float)ay, __fsub_rn(ph, rh), s.h[2]);
+    s.l[0] += Sl;
+    s.l[1] = fmaf((float)ax, ql + wl, s.l[1]);
+    s.l[2] = fmaf((float)ay, pl - rl, s.l[2]);
+    const float S = Sh + Sl;
+    s.d[0] = fmaf((float)(ax * ax), S, s.d[0]);
+    s.d[1] = fmaf((float)(ax * ay), (qh - wh) + (ql - wl), s.d[1]);
+    s.d[2] = fmaf((float)(ay * ay), S, s.d[2]);
+  }
+}
+
+// Last orbit of its group (the orbits run group by group).
+template <class Def, int K>
+__host__ __device__ constexpr bool ex_group_ends() {
+  return K + 1 == Def::O.K || Def::O.grp[K + 1] != Def::O.grp[K];
+}
+
+// Orbit K, then, at the end of a group, that group's sums into the moments.
+template <class Def, int K>
+__device__ __forceinline__ void ex_orbit_step(const float (&d)[Def::Q], const FusedParams& p,
+                                              const float (&C)[6], ExGroup& s, ExMoments& M) {
+  ex_acc_orbit<Def, K>(d, C, s);
+  if constexpr (ex_group_ends<Def, K>()) {
+    constexpr int g = Def::O.grp[K];
+    ex_acc(M.N0, p.gm[g][0], s.h[0], s.l[0]);
+    ex_acc(M.K0, p.gk[g][0], s.h[0], s.l[0]);
+    ex_acc(M.Nx, p.gm[g][2], s.h[1], s.l[1]);
+    ex_acc(M.Kx, p.gk[g][1], s.h[1], s.l[1]);
+    ex_acc(M.Ny, p.gm[g][2], s.h[2], s.l[2]);
+    ex_acc(M.Ky, p.gk[g][1], s.h[2], s.l[2]);
+    M.Txx = hl_fma(p.gm[g][4], s.d[0], M.Txx);
+    M.Txy = hl_fma(p.gm[g][4], s.d[1], M.Txy);
+    M.Tyy = hl_fma(p.gm[g][4], s.d[2], M.Tyy);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) s.h[k] = s.l[k] = s.d[k] = 0.0f;
+  }
+}
+
+template <class Def, int... Ks>
+__device__ __forceinline__ void ex_acc_all(std::integer_sequence<int, Ks...>, const float (&d)[Def::Q],
+                                           const FusedParams& p, ExMoments& M) {
+  float C[6];
+#pragma unroll
+  for (int g = 0; g < 6; ++g) C[g] = p.exC[g];
+  ExGroup s;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) s.h[k] = s.l[k] = s.d[k] = 0.0f;
+  (ex_orbit_step<Def, Ks>(d, p, C, s, M), ...);
 }
 
 // Relaxation and store of population I with equilibrium value e (f^eq - r).
@@ -259,8 +403,11 @@ struct SplitSite {
 
 // P: FusedParams or FusedO3Params (fields mref, nr, yr, Rr, mb, cv_r, mb64,
 // Rr64, rt64, rt32).
-template <class P>
-__device__ __forceinline__ SplitSite split_solve(const P& p, const float (&M)[9], unsigned& fl) {
+// With EX, em holds the extended moments (M their FP32 roundings): the
+// density deviation and e - m n are formed from them (see ExMoments).
+template <bool EX = false, class P>
+__device__ __forceinline__ SplitSite split_solve(const P& p, const float (&M)[9], unsigned& fl,
+                                                 const ExMoments* em = nullptr) {
   // Landau frame: FP32 Newton on the full moments.  v = T^0i/(...) is well
   // conditioned (relative error ~ FP32 rounding); the cancelling parts of the
   // energy and density are formed below from the deviation moments.
@@ -284,13 +431,31 @@ __device__ __forceinline__ SplitSite split_solve(const P& p, const float (&M)[9]
   const float dg = __fdividef(v2, sq * (1.0f + sq));  // gamma - 1
   const float U0 = 1.0f + dg, Ux = U0 * vx, Uy = U0 * vy;
   // n = U.N = n_r + n_d
-  const float Xi = M[0] - vx * M[1] - vy * M[2];
+  float Xi;
+  if constexpr (EX) Xi = em->N0.hi + ((em->N0.lo - vx * M[1]) - vy * M[2]);
+  else Xi = M[0] - vx * M[1] - vy * M[2];
   const float nd = fmaf(dg, p.nr.lo, fmaf(dg, Xi + p.nr.hi, Xi));
   const float n = p.nr.hi + (p.nr.lo + nd);
   if (!(n > 0.0f)) fl |= ERR_DENSITY;
   // e/n = y_r + y_d
-  const float ed = M[3] - M[4] * vx - M[5] * vy;
-  const float yd = __fdividef(ed - fmaf(p.yr.hi, nd, p.yr.lo * nd), n);
+  float yd;
+  if constexpr (EX) {
+    // e - m n = U0^2 (K^0 - 2 v.K + v.T.v) + m U0 ((U0 - 1) N^0 - (2 U0 - 1) v.N)
+    // on the full moments (reference + deviation); no term cancels e or m n
+    const float K0 = p.k0r.hi + ((p.k0r.lo + em->K0.hi) + em->K0.lo);
+    const float Kx = em->Kx.hi + em->Kx.lo, Ky = em->Ky.hi + em->Ky.lo;
+    const float Txx = p.mref[6].hi + (p.mref[6].lo + M[6]);
+    const float Tyy = p.mref[8].hi + (p.mref[8].lo + M[8]);
+    const float vTv = fmaf(vx * vx, Txx, fmaf(2.0f * vx * vy, M[7], vy * vy * Tyy));
+    const float kin = fmaf(-2.0f, fmaf(vx, Kx, vy * Ky), K0) + vTv;
+    const float N0 = p.nr.hi + ((p.nr.lo + em->N0.hi) + em->N0.lo);
+    const float vN = fmaf(vx, M[1], vy * M[2]);
+    const float W = fmaf(U0 * U0, kin, p.mb * U0 * fmaf(dg, N0, -fmaf(2.0f, dg, 1.0f) * vN));
+    yd = (__fdividef(W, n) - p.ykr.hi) - p.ykr.lo;
+  } else {
+    const float ed = M[3] - M[4] * vx - M[5] * vy;
+    yd = __fdividef(ed - fmaf(p.yr.hi, nd, p.yr.lo * nd), n);
+  }
   if (!(p.yr.hi + yd > p.mb)) fl |= ERR_EOS;
   // EOS: T = 1 + T_d solves 3 T_d + m (R(m/T) - R_r) = y_d.  FP32 Newton ...
   float Td = yd / p.cv_r, slope = p.cv_r, R32 = p.Rr.hi;
@@ -344,9 +509,10 @@ __device__ __forceinline__ SplitSite split_solve(const P& p, const float (&M)[9]
 }
 
 // One site update (see the header comment); p describes the lattice.
-template <class Def, bool BF>
+template <class Def, bool BF, bool EX = false>
 __device__ __forceinline__ void fused_site(const FusedParams& p, const void* __restrict__ fin,
                                            void* __restrict__ fout, int site, unsigned& fl) {
+  static_assert(!(BF && EX), "extended moment sums are for FP32 storage");
   constexpr int Q = Def::Q;
   using Seq = std::make_integer_sequence<int, Q>;
   {
@@ -355,33 +521,49 @@ __device__ __forceinline__ void fused_site(const FusedParams& p, const void* __r
     float d[Q];
     fused_load_all<Def, BF>(Seq{}, d, fin, static_cast<const uint2*>(p.cin), p.plane, p.pitch, x, y, p.Nx,
                             p.Ny);
-    float s[6][6];
-#pragma unroll
-    for (int g = 0; g < 6; ++g)
-#pragma unroll
-      for (int k = 0; k < 6; ++k) s[g][k] = 0.0f;
     using Orb = std::make_integer_sequence<int, Def::O.K>;
-    if constexpr (fused_use_orbits<Def, BF>()) fused_acc_all<Def>(Orb{}, d, s);
-    else fused_acc_pop_all<Def>(Seq{}, d, s);
-
     // deviation moments N0 Nx Ny T00 T0x T0y Txx Txy Tyy (reference excluded)
     float M[9];
+    SplitSite ss;
+    if constexpr (EX) {
+      ExMoments em;
+      em.N0 = em.Nx = em.Ny = em.K0 = em.Kx = em.Ky = FF{0.0f, 0.0f};
+      em.Txx = em.Txy = em.Tyy = 0.0f;
+      ex_acc_all<Def>(Orb{}, d, p, em);
+      M[0] = em.N0.hi + em.N0.lo;
+      M[1] = em.Nx.hi + em.Nx.lo;
+      M[2] = em.Ny.hi + em.Ny.lo;
+      M[3] = fmaf(p.mb, M[0], em.K0.hi + em.K0.lo);
+      M[4] = fmaf(p.mb, M[1], em.Kx.hi + em.Kx.lo);
+      M[5] = fmaf(p.mb, M[2], em.Ky.hi + em.Ky.lo);
+      M[6] = em.Txx;
+      M[7] = em.Txy;
+      M[8] = em.Tyy;
+      ss = split_solve<true>(p, M, fl, &em);
+    } else {
+      float s[6][6];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) M[k] = 0.0f;
+      for (int g = 0; g < 6; ++g)
 #pragma unroll
-    for (int g = 0; g < 6; ++g) {
-      M[0] = hl_fma(p.gm[g][0], s[g][0], M[0]);
-      M[3] = hl_fma(p.gm[g][1], s[g][0], M[3]);
-      M[1] = hl_fma(p.gm[g][2], s[g][1], M[1]);
-      M[2] = hl_fma(p.gm[g][2], s[g][2], M[2]);
-      M[4] = hl_fma(p.gm[g][3], s[g][1], M[4]);
-      M[5] = hl_fma(p.gm[g][3], s[g][2], M[5]);
-      M[6] = hl_fma(p.gm[g][4], s[g][3], M[6]);
-      M[7] = hl_fma(p.gm[g][4], s[g][4], M[7]);
-      M[8] = hl_fma(p.gm[g][4], s[g][5], M[8]);
+        for (int k = 0; k < 6; ++k) s[g][k] = 0.0f;
+      if constexpr (fused_use_orbits<Def, BF>()) fused_acc_all<Def>(Orb{}, d, s);
+      else fused_acc_pop_all<Def>(Seq{}, d, s);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) M[k] = 0.0f;
+#pragma unroll
+      for (int g = 0; g < 6; ++g) {
+        M[0] = hl_fma(p.gm[g][0], s[g][0], M[0]);
+        M[3] = hl_fma(p.gm[g][1], s[g][0], M[3]);
+        M[1] = hl_fma(p.gm[g][2], s[g][1], M[1]);
+        M[2] = hl_fma(p.gm[g][2], s[g][2], M[2]);
+        M[4] = hl_fma(p.gm[g][3], s[g][1], M[4]);
+        M[5] = hl_fma(p.gm[g][3], s[g][2], M[5]);
+        M[6] = hl_fma(p.gm[g][4], s[g][3], M[6]);
+        M[7] = hl_fma(p.gm[g][4], s[g][4], M[7]);
+        M[8] = hl_fma(p.gm[g][4], s[g][5], M[8]);
+      }
+      ss = split_solve(p, M, fl);
     }
-
-    const SplitSite ss = split_solve(p, M, fl);
     const float dg = ss.dg, U0 = ss.U0, Ux = ss.Ux, Uy = ss.Uy, n = ss.n, nd = ss.nd;
     const float Td = ss.Td, dR = ss.dR, R = ss.R, T = ss.T;
     // projections without their normalisations (those live in p.gf)
@@ -435,26 +617,39 @@ __device__ __forceinline__ void fused_site(const FusedParams& p, const void* __r
 // per stencil size on GB300: Q <= 40: 6 in FP32 (80 registers), 5 in BF16;
 // Q <= 64: 5 in FP32 (96 registers), 4 in BF16; larger stencils 4 (128
 // registers), where fewer registers would spill.
-template <class Def, bool BF>
+template <class Def, bool BF, bool EX = false>
 constexpr int fused_min_blocks() {
-  return Def::Q <= 40 ? (BF ? 5 : 6) : ((Def::Q <= 64 && !BF) ? 5 : 4);
+  return Def::Q <= 40 ? ((BF || EX) ? 5 : 6) : ((Def::Q <= 64 && !BF && !EX) ? 5 : 4);
 }
 
-template <class Def, bool BF>
-__global__ void __launch_bounds__(128, fused_min_blocks<Def, BF>()) fused_f32_kernel(const __grid_constant__ FusedParams p,
+template <class Def, bool BF, bool EX = false>
+__global__ void __launch_bounds__(128, fused_min_blocks<Def, BF, EX>()) fused_f32_kernel(const __grid_constant__ FusedParams p,
                                                         const void* __restrict__ fin,
                                                         void* __restrict__ fout) {
   const int site = blockIdx.x * blockDim.x + threadIdx.x;
   unsigned fl = 0;
-  if (site < p.Nx * p.Ny) fused_site<Def, BF>(p, fin, fout, site, fl);
+  if (site < p.Nx * p.Ny) fused_site<Def, BF, EX>(p, fin, fout, site, fl);
   report(fl, p.err);
 }
 
 // Entry point of the step kernel of a stencil, for CUDA graph kernel nodes
 // (rlbm_batch_step); the node's grid is (Nx Ny + 127)/128 blocks of 128.
+// mode: 0 FP32, 1 BF16 deviation, 2 FP32 with extended moment sums.
 template <class Def>
-const void* fused_kernel_fn_impl(bool bf16) {
-  return bf16 ? (const void*)&fused_f32_kernel<Def, true> : (const void*)&fused_f32_kernel<Def, false>;
+const void* fused_kernel_fn_impl(int mode) {
+  return mode == 1 ? (const void*)&fused_f32_kernel<Def, true>
+         : mode == 2 ? (const void*)&fused_f32_kernel<Def, false, true>
+                     : (const void*)&fused_f32_kernel<Def, false>;
+}
+
+template <class Def>
+cudaError_t launch_fused_impl(const FusedParams& p, const void* fin, void* fout, int mode, cudaStream_t s) {
+  const long long nsite = (long long)p.Nx * p.Ny;
+  const unsigned grid = (unsigned)((nsite + 127) / 128);
+  if (mode == 1) fused_f32_kernel<Def, true><<<grid, 128, 0, s>>>(p, fin, fout);
+  else if (mode == 2) fused_f32_kernel<Def, false, true><<<grid, 128, 0, s>>>(p, fin, fout);
+  else fused_f32_kernel<Def, false><<<grid, 128, 0, s>>>(p, fin, fout);
+  return cudaGetLastError();
 }
 
 }  // namespace rlbm

@@ -4,12 +4,8 @@
 
 namespace rlbm {
 template <>
-cudaError_t launch_fused<StencilE5>(const FusedParams& p, const void* fin, void* fout, bool bf16, cudaStream_t s) {
-  const long long nsite = (long long)p.Nx * p.Ny;
-  const unsigned grid = (unsigned)((nsite + 127) / 128);
-  if (bf16) fused_f32_kernel<StencilE5, true><<<grid, 128, 0, s>>>(p, fin, fout);
-  else fused_f32_kernel<StencilE5, false><<<grid, 128, 0, s>>>(p, fin, fout);
-  return cudaGetLastError();
+cudaError_t launch_fused<StencilE5>(const FusedParams& p, const void* fin, void* fout, int mode, cudaStream_t s) {
+  return launch_fused_impl<StencilE5>(p, fin, fout, mode, s);
 }
 template <>
 cudaError_t launch_bf16_io<StencilE5>(int what, const FusedParams& fp, const StepParams<double>& p, FieldPtrs fd,
@@ -17,7 +13,7 @@ cudaError_t launch_bf16_io<StencilE5>(int what, const FusedParams& fp, const Ste
   return launch_bf16_io_impl<StencilE5>(what, fp, p, fd, cur, prev, ccur, cprev, mo, s);
 }
 template <>
-const void* fused_kernel_fn<StencilE5>(bool bf16) {
-  return fused_kernel_fn_impl<StencilE5>(bf16);
+const void* fused_kernel_fn<StencilE5>(int mode) {
+  return fused_kernel_fn_impl<StencilE5>(mode);
 }
 }  // namespace rlbm

@@ -7,29 +7,31 @@
 #include "rlbm_stencils.h"
 
 namespace rlbm {
+// mode: 0 FP32 storage, 1 BF16 deviation storage, 2 FP32 storage with
+// extended moment sums (rlbm_fused.cuh).
 template <class Def>
-cudaError_t launch_fused(const FusedParams& p, const void* fin, void* fout, bool bf16, cudaStream_t s);
+cudaError_t launch_fused(const FusedParams& p, const void* fin, void* fout, int mode, cudaStream_t s);
 template <>
-cudaError_t launch_fused<StencilM1>(const FusedParams&, const void*, void*, bool, cudaStream_t);
+cudaError_t launch_fused<StencilM1>(const FusedParams&, const void*, void*, int, cudaStream_t);
 template <>
-cudaError_t launch_fused<StencilG16>(const FusedParams&, const void*, void*, bool, cudaStream_t);
+cudaError_t launch_fused<StencilG16>(const FusedParams&, const void*, void*, int, cudaStream_t);
 template <>
-cudaError_t launch_fused<StencilE5>(const FusedParams&, const void*, void*, bool, cudaStream_t);
+cudaError_t launch_fused<StencilE5>(const FusedParams&, const void*, void*, int, cudaStream_t);
 template <>
-cudaError_t launch_fused<StencilS2>(const FusedParams&, const void*, void*, bool, cudaStream_t);
+cudaError_t launch_fused<StencilS2>(const FusedParams&, const void*, void*, int, cudaStream_t);
 
 // The step kernel itself (FusedParams, const void* fin, void* fout), for graph
 // kernel nodes; grid (Nx Ny + 127)/128, block 128, no dynamic shared memory.
 template <class Def>
-const void* fused_kernel_fn(bool bf16);
+const void* fused_kernel_fn(int mode);
 template <>
-const void* fused_kernel_fn<StencilM1>(bool);
+const void* fused_kernel_fn<StencilM1>(int);
 template <>
-const void* fused_kernel_fn<StencilG16>(bool);
+const void* fused_kernel_fn<StencilG16>(int);
 template <>
-const void* fused_kernel_fn<StencilE5>(bool);
+const void* fused_kernel_fn<StencilE5>(int);
 template <>
-const void* fused_kernel_fn<StencilS2>(bool);
+const void* fused_kernel_fn<StencilS2>(int);
 // The compiled third-order kernel of kind 5..10 (FusedO3Params, const float*
 // fin, float* fout), for graph kernel nodes; grid (Nx Ny + 127)/128, block
 // 128, no dynamic shared memory (rlbm_fused_o3.cu).

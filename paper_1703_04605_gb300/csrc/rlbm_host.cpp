@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "rlbm_devmem.h"
+#include "rlbm_fieldscan.h"
 #include "rlbm_fused_launch.h"
 #include "rlbm_stencil.h"
 
@@ -43,6 +44,7 @@ struct rlbm_ctx {
   std::unique_ptr<StepParams<double>> p64;
   std::unique_ptr<StepParams<float>> p32;
   int fused = 0;                 // 1: M1, 2: G1..G6, 3: E5, 4: S2; 0: generic kernel
+  int ext = 0;                   // FP32 storage on a compiled stencil: extended moment sums
   std::unique_ptr<FusedParams> fp;
   // third-order stencils (eleven groups)
   int order = 2;
@@ -59,6 +61,12 @@ struct rlbm_ctx {
 
 static thread_local std::string g_create_error;
 static void batch_forget(const rlbm_ctx* c);   // drop cached batch graphs that use c
+
+// Variant of the compiled second-order kernel: 0 FP32, 1 BF16 deviation,
+// 2 FP32 with extended moment sums.
+static int fused_mode(const rlbm_ctx* c) {
+  return c->dtype == RLBM_BF16_DEV ? 1 : (c->ext ? 2 : 0);
+}
 
 // The allocator installed by rlbm_set_allocator (all null: cudaMalloc).
 static std::mutex g_alloc_mutex;
@@ -178,7 +186,15 @@ static void fill_fused(rlbm_ctx* c, double nref) {
   for (int g = 0; g < 6; ++g) {
     for (int q = 0; q < 5; ++q) f.gm[g][q] = split(sb.gm[g][q]);
     for (int q = 0; q < 10; ++q) f.gf[g][q] = split(sb.gf[g][q]);
+    for (int q = 0; q < 2; ++q) f.gk[g][q] = split(sb.gk[g][q]);
+    // split grid q = 2^(ceil(log2 r_g) - 11), r_g the group's largest
+    // reference population: its h-sums (at most 24 members, weights up to 6)
+    // stay exact while the pulled values stay below about 50 r_g
+    const int e = (int)std::ceil(std::log2(nref * sb.rmax1[g]));
+    f.exC[g] = (float)std::ldexp(1.5, 23 + e - 11);
   }
+  f.k0r = split(nref * sb.kref1);
+  f.ykr = split(sb.ykr1);
   f.rt64 = c->d_rt64;
   f.rt32 = c->d_rt32;
   f.err = c->d_err;
@@ -546,30 +562,43 @@ rlbm_status rlbm_init(rlbm_ctx* c, const double* n, const double* ux, const doub
   if (!c) return RLBM_EINVAL;
   if (!n || !ux || !uy || !T) return fail(c, RLBM_EINVAL, "NULL field pointer");
   const size_t N = (size_t)c->Nx * c->Ny;
-  for (size_t s = 0; s < N; ++s) {
-    const double v2 = ux[s] * ux[s] + uy[s] * uy[s];
-    if (!(n[s] > 0) || !(T[s] > 0) || !(v2 < 1) || !std::isfinite(n[s]) || !std::isfinite(T[s])) {
-      char b[160];
-      std::snprintf(b, sizeof b, "invalid field at site %zu (x=%zu, y=%zu): need n>0, T>0, |u|<1",
-                    s, s % (size_t)c->Nx, s / (size_t)c->Nx);
-      return fail(c, RLBM_EINVAL, b);
-    }
-  }
-  double nsum = 0;
-  for (size_t s = 0; s < N; ++s) nsum += n[s];
-  set_reference(c, nsum / (double)N);
+  // the upload (asynchronous from pinned memory) overlaps the host scan; the
+  // populations are written only after the scan has passed
   const double* src[4] = {n, ux, uy, T};
   for (int k = 0; k < 4; ++k) {
     cudaError_t e = cudaMemcpyAsync(c->d_fields + k * N, src[k], N * sizeof(double),
                                     cudaMemcpyHostToDevice, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "field upload");
+    if (e != cudaSuccess) {
+      cudaStreamSynchronize(c->stream);
+      return cuda_fail(c, e, "field upload");
+    }
   }
+  const FieldScan fs = scan_fields(n, ux, uy, nullptr, T, N);
+  if (fs.first_bad < N) {
+    cudaStreamSynchronize(c->stream);   // the caller's arrays stay read until here
+    const size_t s = fs.first_bad;
+    char b[160];
+    std::snprintf(b, sizeof b, "invalid field at site %zu (x=%zu, y=%zu): need n>0, T>0, |u|<1",
+                  s, s % (size_t)c->Nx, s / (size_t)c->Nx);
+    return fail(c, RLBM_EINVAL, b);
+  }
+  set_reference(c, fs.nsum / (double)N);
   c->host_init = true;
   rlbm_status s = rlbm_init_device(c, c->d_fields, c->d_fields + N, c->d_fields + 2 * N,
                                    c->d_fields + 3 * N);
   c->host_init = false;
   if (s != RLBM_OK) return s;
   return check_device_error(c);
+}
+
+rlbm_status rlbm_set_extended_sums(rlbm_ctx* c, int on) {
+  if (!c) return RLBM_EINVAL;
+  if (c->order != 2 || c->dtype != RLBM_F32 || !c->fused)
+    return fail(c, RLBM_ENOTSUP, "extended moment sums need FP32 storage on a compiled second-order stencil");
+  const int v = on ? 1 : 0;
+  if (v != c->ext) batch_forget(c);
+  c->ext = v;
+  return RLBM_OK;
 }
 
 rlbm_status rlbm_step(rlbm_ctx* c, int nsteps) {
@@ -585,13 +614,13 @@ rlbm_status rlbm_step(rlbm_ctx* c, int nsteps) {
                  : launch_step_o3(c->dtype, *c->o3, fin, fout, c->stream);
     else if (c->dtype == RLBM_F64) e = launch_step_f64(*c->p64, fin, fout, c->qb, c->stream);
     else if (c->fused) {
-      const bool bf = c->dtype == RLBM_BF16_DEV;
+      const int mode = fused_mode(c);
       c->fp->cin = c->coef[c->cur];
       c->fp->cout = c->coef[1 - c->cur];
-      if (c->fused == 1) e = launch_fused<StencilM1>(*c->fp, fin, fout, bf, c->stream);
-      else if (c->fused == 2) e = launch_fused<StencilG16>(*c->fp, fin, fout, bf, c->stream);
-      else if (c->fused == 3) e = launch_fused<StencilE5>(*c->fp, fin, fout, bf, c->stream);
-      else e = launch_fused<StencilS2>(*c->fp, fin, fout, bf, c->stream);
+      if (c->fused == 1) e = launch_fused<StencilM1>(*c->fp, fin, fout, mode, c->stream);
+      else if (c->fused == 2) e = launch_fused<StencilG16>(*c->fp, fin, fout, mode, c->stream);
+      else if (c->fused == 3) e = launch_fused<StencilE5>(*c->fp, fin, fout, mode, c->stream);
+      else e = launch_fused<StencilS2>(*c->fp, fin, fout, mode, c->stream);
     }
     else e = launch_step_f32(*c->p32, fin, fout, c->qb, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
@@ -675,6 +704,7 @@ rlbm_status rlbm_get_info(const rlbm_ctx* c, rlbm_info* info) {
   info->extra_bytes_per_site = (c->dtype == RLBM_BF16_DEV) ? 2 * 6 * 8 : 0;   // coefficients read + written
   info->device_bytes = c->device_bytes + c->out_cap * sizeof(double);
   info->kernel = c->fused;
+  info->extended_sums = c->ext;
   return RLBM_OK;
 }
 
@@ -722,12 +752,12 @@ namespace {
 
 const void* kernel_of(const rlbm_ctx* c) {
   if (c->order == 3) return fused_o3_kernel_fn(c->fused);
-  const bool bf = c->dtype == RLBM_BF16_DEV;
+  const int mode = fused_mode(c);
   switch (c->fused) {
-    case 1: return fused_kernel_fn<StencilM1>(bf);
-    case 2: return fused_kernel_fn<StencilG16>(bf);
-    case 3: return fused_kernel_fn<StencilE5>(bf);
-    default: return fused_kernel_fn<StencilS2>(bf);
+    case 1: return fused_kernel_fn<StencilM1>(mode);
+    case 2: return fused_kernel_fn<StencilG16>(mode);
+    case 3: return fused_kernel_fn<StencilE5>(mode);
+    default: return fused_kernel_fn<StencilS2>(mode);
   }
 }
 

@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "rlbm_fieldscan.h"
 #include "rlbm_devmem.h"
 #include "rlbm_o3_3d.h"
 #include "rlbm_stencil.h"
@@ -311,24 +312,26 @@ rlbm_status rlbm3_init(rlbm_ctx3* c, const double* n, const double* ux, const do
   if (!c) return RLBM_EINVAL;
   if (!n || !ux || !uy || !uz || !T) return fail3(c, RLBM_EINVAL, "NULL field pointer");
   const size_t N = (size_t)c->Nx * c->Ny * c->Nz;
-  double nsum = 0;
-  for (size_t s = 0; s < N; ++s) {
-    const double v2 = ux[s] * ux[s] + uy[s] * uy[s] + uz[s] * uz[s];
-    if (!(n[s] > 0) || !(T[s] > 0) || !(v2 < 1) || !std::isfinite(n[s]) || !std::isfinite(T[s])) {
-      char b[200];
-      std::snprintf(b, sizeof b, "invalid field at site %zu (x=%zu, y=%zu, z=%zu): need n>0, T>0, |u|<1", s,
-                    s % (size_t)c->Nx, (s / (size_t)c->Nx) % (size_t)c->Ny, s / ((size_t)c->Nx * c->Ny));
-      return fail3(c, RLBM_EINVAL, b);
-    }
-    nsum += n[s];
-  }
-  set_reference3(c, nsum / (double)N);
+  // the upload overlaps the host scan; populations are written after it passed
   const double* src[5] = {n, ux, uy, uz, T};
   for (int k = 0; k < 5; ++k) {
     cudaError_t e = cudaMemcpyAsync(c->d_fields + k * N, src[k], N * sizeof(double), cudaMemcpyHostToDevice,
                                     c->stream);
-    if (e != cudaSuccess) return cuda_fail3(c, e, "field upload");
+    if (e != cudaSuccess) {
+      cudaStreamSynchronize(c->stream);
+      return cuda_fail3(c, e, "field upload");
+    }
   }
+  const FieldScan fs = scan_fields(n, ux, uy, uz, T, N);
+  if (fs.first_bad < N) {
+    cudaStreamSynchronize(c->stream);   // the caller's arrays stay read until here
+    const size_t s = fs.first_bad;
+    char b[200];
+    std::snprintf(b, sizeof b, "invalid field at site %zu (x=%zu, y=%zu, z=%zu): need n>0, T>0, |u|<1", s,
+                  s % (size_t)c->Nx, (s / (size_t)c->Nx) % (size_t)c->Ny, s / ((size_t)c->Nx * c->Ny));
+    return fail3(c, RLBM_EINVAL, b);
+  }
+  set_reference3(c, fs.nsum / (double)N);
   Field3Ptrs fp{c->d_fields, c->d_fields + N, c->d_fields + 2 * N, c->d_fields + 3 * N, c->d_fields + 4 * N};
   c->q.b = c->p;
   cudaError_t e = c->order == 3 ? launch_init3d_o3(c->dtype, c->q, fp, c->buf[0], c->buf[1], c->stream)

@@ -112,6 +112,12 @@ struct FusedParams {
   double Rr64, hr64, mb64, nr64;
   HL gm[6][5];         // per group: P0, P0^2, Pv, P0 Pv, Pv^2 (P0 = m gamma, Pv = m gamma v0)
   HL gf[6][10];        // per group: a0 a1 a4 a7 a8 bx2 bx5 q78 qy7 q9 (see host)
+  // extended moment sums only: per group P0 (P0 - m), Pv (P0 - m); the
+  // reference's kinetic moment K^0 and (e - m n)/n; per group the magic
+  // constant 1.5 2^23 q of the exact split grid q
+  HL gk[6][2];
+  HL k0r, ykr;
+  float exC[6];
   const double* rt64;
   const float* rt32;
   unsigned* err;

@@ -468,6 +468,7 @@ rlbm_status build_stencil(const rlbm_stencil* st, double m, StencilBuild* out, s
     out->cv_r = (double)(3 - z * z * (Rr * Rr + 3 * Rr / z - 1));
   }
   qf mref[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  qf kref = 0;
   // fold: merge (nx, ny, +nz) with (nx, ny, -nz) inside each group
   out->pops.clear();
   out->popc.clear();
@@ -492,6 +493,9 @@ rlbm_status build_stencil(const rlbm_stencil* st, double m, StencilBuild* out, s
                          w * Pv2 / (Eq * Eq)};
       for (int q = 0; q < 5; ++q) out->gm[k][q] = (double)gm[q];
       for (int q = 0; q < 10; ++q) out->gf[k][q] = (double)gf[q];
+      out->gk[k][0] = (double)(P0 * (P0 - mq));
+      out->gk[k][1] = (double)(Pv * (P0 - mq));
+      out->rmax1[k] = 0;
     }
     std::vector<std::array<int, 3>> seen;
     std::vector<int> mult;
@@ -532,6 +536,8 @@ rlbm_status build_stencil(const rlbm_stencil* st, double m, StencilBuild* out, s
         row[q] = (double)mom[q];
         mref[q] += pc.w * b0r * mom[q];
       }
+      kref += pc.w * b0r * pc.p0 * (pc.p0 - (qf)m);
+      out->rmax1[k] = std::max(out->rmax1[k], (double)(pc.w * b0r));
       for (int q = 0; q < NJ; ++q) row[9 + q] = (double)(pc.w * pc.J[q]);
       row[19] = (double)(pc.px / pc.p0);
       row[20] = (double)(pc.py / pc.p0);
@@ -539,6 +545,8 @@ rlbm_status build_stencil(const rlbm_stencil* st, double m, StencilBuild* out, s
     }
   }
   for (int q = 0; q < 9; ++q) out->mref1[q] = (double)mref[q];
+  out->kref1 = (double)kref;
+  out->ykr1 = (double)(kref / mref[0]);
   if ((int)out->pops.size() > QMAX) {
     *err = "folded stencil has more populations than the compiled maximum (96)";
     return RLBM_ENOTSUP;

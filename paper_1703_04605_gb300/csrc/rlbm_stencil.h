@@ -36,6 +36,12 @@ struct StencilBuild {
   // gf = a0 a1 a4 a7 a8 bx2 bx5 q78 qy7 q9 (App. A/B normalisations folded in)
   double gm[6][5];
   double gf[6][10];
+  // extended moment sums: per group P0 (P0 - m) and Pv (P0 - m) (kinetic
+  // moments K^0, K^a = T^0a - m N^a); the reference's K^0 per unit density
+  // and per particle; the largest reference population of each group
+  double gk[6][2];
+  double kref1, ykr1;
+  double rmax1[6];
   double cv_r;          // 3 - mbar^2 R'(mbar): specific heat per particle at T_R
   int halo;
   SiteConsts sc;

@@ -85,15 +85,34 @@ class Lattice:
                 raise ValueError("device fields must be contiguous CUDA tensors of Nx*Ny float64")
         self._chk(self._lib.rlbm_init_device(self._ctx, *[C.c_void_p(t.data_ptr()) for t in (n, ux, uy, T)]))
 
+    def set_extended_sums(self, on=True):
+        """FP32 storage on a compiled stencil: moment sums in extended
+        precision (rlbm_set_extended_sums)."""
+        self._chk(self._lib.rlbm_set_extended_sums(self._ctx, 1 if on else 0))
+
     def step(self, k=1):
         self._chk(self._lib.rlbm_step(self._ctx, int(k)))
 
     def sync(self):
         self._chk(self._lib.rlbm_sync(self._ctx))
 
-    def moments(self, mask=A.M_N | A.M_UX | A.M_UY | A.M_T | A.M_E):
+    def moments_size(self, mask=A.M_N | A.M_UX | A.M_UY | A.M_T | A.M_E):
+        """Doubles that moments(mask) writes (rlbm_moments_size)."""
+        return int(self._lib.rlbm_moments_size(self._ctx, mask))
+
+    def moments(self, mask=A.M_N | A.M_UX | A.M_UY | A.M_T | A.M_E, out=None):
+        """Fields of the current state as [Ny, Nx] views of one buffer.  out:
+        an optional C-contiguous float64 array of at least
+        rlbm_moments_size(mask) elements to receive them (page-locked host
+        memory makes the device-to-host copy direct); default a new array."""
         size = self._lib.rlbm_moments_size(self._ctx, mask)
-        out = np.empty(size, dtype=np.float64)
+        if out is None:
+            out = np.empty(size, dtype=np.float64)
+        else:
+            out = np.asarray(out)
+            if out.dtype != np.float64 or not out.flags.c_contiguous or out.size < size:
+                raise ValueError("out must be a C-contiguous float64 array of at least %d elements" % size)
+            out = out.reshape(-1)
         self._chk(self._lib.rlbm_moments(self._ctx, out.ctypes.data_as(C.POINTER(C.c_double)), mask))
         res = {}
         plane = 0
