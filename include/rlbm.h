@@ -112,8 +112,8 @@ typedef struct {
                                {4,8,14,15,16,17,18,21,22,23,26} (FP32
                                storage, lattice at least a halo wide)          */
   int order;                /* expansion order of f^eq: 2 or 3               */
-  int extended_sums;        /* 1: the FP32 step forms its moment sums with
-                               extended precision (rlbm_set_extended_sums)   */
+  int extended_sums;        /* level of extended-precision moment sums of the
+                               FP32 step, 0..2 (rlbm_set_extended_sums)      */
 } rlbm_info;
 
 /* Create a lattice context.
@@ -146,19 +146,20 @@ rlbm_status rlbm_init_device(rlbm_ctx* ctx, const double* n, const double* ux, c
 rlbm_status rlbm_step(rlbm_ctx* ctx, int nsteps);
 
 /* Moment sums of the FP32 step on a compiled second-order stencil
- * (rlbm_info.kernel 1..4, FP32 storage).  on = 1: the conserved moments N^a
- * and the kinetic moments K^a = T^0a - m N^a (Eq. 4-5, 18) are accumulated
- * to about 2^-40 relative -- each pulled value split exactly into a part on a
- * per-group grid and a small remainder, the group sums combined by
- * error-free products and sums -- and e - m n (Eq. 19-20) is formed from K^a,
- * without cancelling the rest-mass energy.  This keeps FP32 storage within
- * 1e-5 of FP64 over thousands of steps on steep, sloshing flows of massive
- * particles, where plain FP32 moment sums drift (they break mass and energy
- * conservation by about one rounding per step and site).  on = 0: plain FP32
- * sums (fewer instructions).  Takes effect at the next step; cached batch
- * graphs of the context are dropped.  Errors: EINVAL (NULL ctx), ENOTSUP
+ * (rlbm_info.kernel 1..4, FP32 storage).  level 1: N^0 and the kinetic
+ * moment K^0 = T^00 - m N^0 (Eq. 4-5, 18) are accumulated to about 2^-40
+ * relative -- each pulled value split exactly into a part on a per-group
+ * grid and a small remainder, the group sums combined by error-free products
+ * and sums -- and e - m n (Eq. 19-20) is formed from K^a = T^0a - m N^a
+ * without cancelling the rest-mass energy; level 2: N^x, N^y, K^x, K^y
+ * extended as well.  This keeps FP32 storage close to FP64 over thousands of
+ * steps on steep, sloshing flows of massive particles, where plain FP32
+ * moment sums drift (they break mass and energy conservation by about one
+ * rounding per step and site).  level 0: plain FP32 sums (fewest
+ * instructions).  Takes effect at the next step; cached batch graphs of the
+ * context are dropped.  Errors: EINVAL (NULL ctx, level not 0..2), ENOTSUP
  * (no compiled FP32 second-order kernel for this context). */
-rlbm_status rlbm_set_extended_sums(rlbm_ctx* ctx, int on);
+rlbm_status rlbm_set_extended_sums(rlbm_ctx* ctx, int level);
 
 /* Macroscopic fields of the current pre-collision state f(., t).
  * mask selects fields (bits below); out receives, in bit order, one
@@ -213,30 +214,69 @@ rlbm_status rlbm_set_allocator(rlbm_alloc_fn alloc, rlbm_free_fn free_fn, void* 
 
 /* Advance count contexts by nsteps each, as one batch (the independent
  * lattices of a parameter sweep or an ensemble).  Equivalent to calling
- * rlbm_step(ctxs[i], nsteps) for every i, with identical results.  The steps
- * run as replays of one CUDA graph per batch that holds, for every lattice, a
- * chain of G step kernels (step k+1 of a lattice depends on its step k) and
- * no dependency between lattices, so the GPU overlaps the lattices' kernels;
- * each kernel is the single-lattice step kernel with that lattice's
- * parameters.  An autotuner picks G in {2, 8, 32} by timing one replay of
- * each on the first call for a batch with nsteps >= 42 (those steps count
- * towards nsteps) and caches the choice; rlbm_batch_tuning reports it.
- * Graphs are cached per batch and buffer parity; rlbm_init or rlbm_destroy of
- * a member drops them.  Requirements: every context initialised, a compiled
- * stencil (rlbm_info.kernel != 0) with FP32 or BF16-deviation storage (FP32
- * only at third order; second- and third-order contexts may be mixed), all
- * on the same CUDA stream, no context listed twice.  Asynchronous on that stream
- * (a NULL stream is bridged to an internal stream with events).  Not
- * thread-safe against rlbm_step on the same contexts.  The paper has no
- * counterpart (it advances one lattice at a time).  Errors: EINVAL (violated
- * requirement), ENOTSUP, ECUDA. */
+ * rlbm_step(ctxs[i], nsteps) for every i, with identical results.  Two
+ * engines run the steps:
+ *  - graph: replays of one CUDA graph per batch that holds, for every
+ *    lattice, a chain of G step kernels (step k+1 of a lattice depends on its
+ *    step k) and no dependency between lattices, so the GPU overlaps the
+ *    lattices' kernels; each kernel is the single-lattice step kernel with
+ *    that lattice's parameters;
+ *  - persistent: one cooperative launch per stencil and storage variant
+ *    covers all nsteps steps of its lattices; its blocks claim tiles of
+ *    128 x spt sites in step-major order and wait, with a bounded poll, until
+ *    the tile's lattice has finished the previous step (second-order lattices
+ *    only).  A wait that runs out of polls ends the launch; the lattices'
+ *    next synchronising call returns RLBM_ETIMEOUT and their state is
+ *    undefined until rlbm_init.
+ * With the engine left to the autotuner (rlbm_batch_set_options), the first
+ * call for a batch with nsteps >= 66 times one replay of each graph length G
+ * in {2, 8, 32} (42 steps) and, on a batch of second-order lattices, 8 steps
+ * of the persistent engine at each spt in {1, 2, 4} (those steps count
+ * towards nsteps), and caches the fastest; rlbm_batch_engine reports it.
+ * Graphs and persistent plans are cached per batch; rlbm_init,
+ * rlbm_set_extended_sums or rlbm_destroy of a member drops them.
+ * Requirements: every context initialised, a compiled stencil
+ * (rlbm_info.kernel != 0) with FP32 or BF16-deviation storage (FP32 only at
+ * third order; second- and third-order contexts may be mixed), all on the
+ * same CUDA stream, no context listed twice.  Asynchronous on that stream (a
+ * NULL stream is bridged to an internal stream with events).  Not thread-safe
+ * against rlbm_step on the same contexts.  The paper has no counterpart (it
+ * advances one lattice at a time).  Errors: EINVAL (violated requirement),
+ * ENOTSUP, ECUDA. */
 rlbm_status rlbm_batch_step(rlbm_ctx* const* ctxs, int count, int nsteps);
+
+/* Batch engines and the persistent engine's bounded waits.  Process-wide;
+ * a change drops every cached tuning choice. */
+#define RLBM_BATCH_AUTO 0        /* the autotuner picks (default)             */
+#define RLBM_BATCH_GRAPH 1       /* graph of per-lattice step kernels         */
+#define RLBM_BATCH_PERSISTENT 2  /* persistent cooperative kernel            */
+typedef struct {
+  int engine;              /* RLBM_BATCH_AUTO, _GRAPH or _PERSISTENT; a batch
+                              the persistent engine cannot run (third-order
+                              members) uses the graph engine                 */
+  unsigned spin_limit;     /* polls (about 0.3 us each) of one device-side
+                              wait before it gives up; 0 = default 2^23       */
+  unsigned wait_offset;    /* fault injection for tests of the timeout path:
+                              added to every wait target, so that a wait can
+                              never be met; 0 in normal use                   */
+} rlbm_batch_options;
+/* opt NULL restores the defaults.  Errors: EINVAL (unknown engine). */
+rlbm_status rlbm_batch_set_options(const rlbm_batch_options* opt);
+
+/* The engine used for a batch (same contexts, same order) once it has been
+ * chosen: *engine = RLBM_BATCH_GRAPH (*param = G, steps per graph replay,
+ * *launches = kernel launches per step = count) or RLBM_BATCH_PERSISTENT
+ * (*param = sites per thread, *launches = cooperative launches per call).
+ * Output pointers may be NULL.  Never touches the device.  Errors: EINVAL (bad
+ * arguments, or no choice made for this batch yet). */
+rlbm_status rlbm_batch_engine(rlbm_ctx* const* ctxs, int count, int* engine, int* param, int* launches);
 
 /* The autotuner's choice for a batch that rlbm_batch_step has tuned (same
  * contexts, same order): *steps_per_graph = G, *launches_per_step = kernel
- * launches of one step (one per lattice).  Either output pointer may be
- * NULL.  Never touches the device.  Errors: EINVAL (bad arguments, or no
- * choice cached for this batch). */
+ * launches of one step (one per lattice), or both 0 when the persistent
+ * engine was chosen (rlbm_batch_engine describes it).  Either output pointer
+ * may be NULL.  Never touches the device.  Errors: EINVAL (bad arguments, or
+ * no choice cached for this batch). */
 rlbm_status rlbm_batch_tuning(rlbm_ctx* const* ctxs, int count, int* steps_per_graph, int* launches_per_step);
 
 /* ---- native 3D lattices ----------------------------------------------

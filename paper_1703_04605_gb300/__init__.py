@@ -7,6 +7,9 @@ equilibrium / Anderson-Witting collision step.  This package only marshals
 arguments; it has no host implementation of the step."""
 from . import _abi
 from ._abi import RLBMError, load, quadrature_weights, quadrature_window, bessel_ratio
-from .lattice import Lattice, Lattice3D, batch_step, batch_tuning, use_cuda_malloc, use_torch_allocator
+from .lattice import (Lattice, Lattice3D, batch_engine, batch_step, batch_tuning, set_batch_options, use_cuda_malloc,
+                      use_torch_allocator)
 
-__all__ = ["Lattice", "Lattice3D", "batch_step", "batch_tuning", "use_torch_allocator", "use_cuda_malloc", "RLBMError", "load", "quadrature_weights", "quadrature_window", "bessel_ratio"]
+__all__ = ["Lattice", "Lattice3D", "batch_step", "batch_tuning", "batch_engine", "set_batch_options",
+           "use_torch_allocator", "use_cuda_malloc", "RLBMError", "load", "quadrature_weights", "quadrature_window",
+           "bessel_ratio"]

@@ -23,7 +23,8 @@ MASK_PLANES3 = [(M_N, ["n"]), (M_UX, ["ux"]), (M_UY, ["uy"]), (M_T, ["T"]), (M_E
 EXPORTS = ["rlbm_create", "rlbm_init", "rlbm_init_device", "rlbm_step", "rlbm_moments",
            "rlbm_moments_size", "rlbm_sync", "rlbm_get_info", "rlbm_last_error", "rlbm_destroy",
            "rlbm_quadrature_weights", "rlbm_quadrature_window", "rlbm_bessel_ratio", "rlbm_version",
-           "rlbm_moments_noalloc", "rlbm_batch_step", "rlbm_set_extended_sums", "rlbm_fp64_fma_rate", "rlbm_batch_tuning", "rlbm_set_allocator",
+           "rlbm_moments_noalloc", "rlbm_batch_step", "rlbm_set_extended_sums", "rlbm_fp64_fma_rate",
+           "rlbm_batch_set_options", "rlbm_batch_engine", "rlbm_batch_tuning", "rlbm_set_allocator",
            "rlbm3_create", "rlbm3_init", "rlbm3_step", "rlbm3_moments", "rlbm3_moments_size", "rlbm3_sync",
            "rlbm3_get_info", "rlbm3_last_error", "rlbm3_destroy"]
 
@@ -35,6 +36,13 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
 class Stencil(C.Structure):
     _fields_ = [("ngroups", C.c_int), ("groups", C.POINTER(C.c_int)), ("v0", C.c_double)]
+
+
+class BatchOptions(C.Structure):
+    _fields_ = [("engine", C.c_int), ("spin_limit", C.c_uint), ("wait_offset", C.c_uint)]
+
+
+BATCH_AUTO, BATCH_GRAPH, BATCH_PERSISTENT = 0, 1, 2
 
 
 class Info(C.Structure):
@@ -86,6 +94,8 @@ def load():
         "rlbm_step": (C.c_int, [P, C.c_int]),
         "rlbm_set_extended_sums": (C.c_int, [P, C.c_int]),
         "rlbm_fp64_fma_rate": (C.c_int, [P, dp]),
+        "rlbm_batch_set_options": (C.c_int, [C.POINTER(BatchOptions)]),
+        "rlbm_batch_engine": (C.c_int, [C.POINTER(P), C.c_int, ip, ip, ip]),
         "rlbm_moments": (C.c_int, [P, dp, C.c_uint]),
         "rlbm_moments_size": (C.c_size_t, [P, C.c_uint]),
         "rlbm_sync": (C.c_int, [P]),

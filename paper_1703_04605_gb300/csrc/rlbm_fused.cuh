@@ -87,7 +87,15 @@ __device__ __forceinline__ float bf_ref(uint2 c) {
   return r;
 }
 
-template <class Def, bool BF, int I>
+// CG: loads through L2 only (ld.global.cg), for kernels that read data other
+// blocks of the same launch wrote (the read-only path may hold stale lines).
+template <bool CG, class T>
+__device__ __forceinline__ T fused_ld(const T* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return __ldg(p);
+}
+
+template <class Def, bool BF, int I, bool CG = false>
 __device__ __forceinline__ void fused_load(float (&d)[Def::Q], const void* __restrict__ fin,
                                            const uint2* __restrict__ cin, long long plane, long long pitch,
                                            int x, int y, int Nx, int Ny) {
@@ -97,11 +105,11 @@ __device__ __forceinline__ void fused_load(float (&d)[Def::Q], const void* __res
   const long long idx = (long long)ys * pitch + xs;
   if constexpr (BF) {
     constexpr int g = Def::F.grp[I], mult = Def::F.mult[I];
-    const unsigned short h = __ldg(static_cast<const unsigned short*>(fin) + (long long)I * plane + idx);
-    const uint2 c = __ldg(cin + (long long)g * plane + idx);
+    const unsigned short h = fused_ld<CG>(static_cast<const unsigned short*>(fin) + (long long)I * plane + idx);
+    const uint2 c = fused_ld<CG>(cin + (long long)g * plane + idx);
     d[I] = __uint_as_float((unsigned)h << 16) + bf_ref<DX, DY, mult>(c);
   } else {
-    d[I] = __ldg(static_cast<const float*>(fin) + (long long)I * plane + idx);
+    d[I] = fused_ld<CG>(static_cast<const float*>(fin) + (long long)I * plane + idx);
   }
 }
 
@@ -167,20 +175,24 @@ __device__ __forceinline__ void ex_split(float d, float C, float& h, float& l) {
   l = __fsub_rn(d, h);
 }
 
-// Running sums of one group: sums of h and of l with weights 1, n_x, n_y
-// (k = 0, 1, 2) and plain FP32 sums of d with n_x^2, n_x n_y, n_y^2.
+// Running sums of one group: sums of h and of l with weight 1 (k = 0) and,
+// at level 2, with weights n_x, n_y (k = 1, 2); plain FP32 sums of d with the
+// remaining weights (n_x, n_y at level 1; n_x^2, n_x n_y, n_y^2).
 struct ExGroup {
-  float h[3], l[3], d[3];
+  float h[3], l[3], d[5];
 };
 
-// Moments of the extended path: N^0, N^x, N^y, K^0, K^x, K^y as float-float,
-// T^xx, T^xy, T^yy in FP32 (all deviations: the reference r_i excluded).
+// Moments of the extended path: N^0 and K^0 (and, at level 2, N^x, N^y, K^x,
+// K^y) as float-float, the others in FP32 (all deviations: the reference r_i
+// excluded).
 struct ExMoments {
   FF N0, Nx, Ny, K0, Kx, Ky;
   float Txx, Txy, Tyy;
 };
 
-template <class Def, int K>
+// Level L = 1: N^0 and K^0 extended (mass and energy, the quantities whose
+// drift the sloshing tubes amplify); L = 2: also momentum and its flux.
+template <class Def, int L, int K>
 __device__ __forceinline__ void ex_acc_orbit(const float (&d)[Def::Q], const float (&C)[6], ExGroup& s) {
   constexpr int kind = Def::O.kind[K], g = Def::O.grp[K], ax = Def::O.ax[K], ay = Def::O.ay[K];
   constexpr int i0 = Def::O.idx[K][0], i1 = Def::O.idx[K][1], i2 = Def::O.idx[K][2], i3 = Def::O.idx[K][3];
@@ -196,34 +208,45 @@ __device__ __forceinline__ void ex_acc_orbit(const float (&d)[Def::Q], const flo
     float h0, l0, h1, l1;
     ex_split(d[i0], C[g], h0, l0);
     ex_split(d[j1], C[g], h1, l1);
-    const float Sh = __fadd_rn(h0, h1), Dh = __fsub_rn(h0, h1);
-    const float Sl = l0 + l1, Dl = l0 - l1;
+    const float Sh = __fadd_rn(h0, h1), Sl = l0 + l1;
     s.h[0] = __fadd_rn(s.h[0], Sh);
-    s.h[k] = __fmaf_rn((float)a, Dh, s.h[k]);
     s.l[0] += Sl;
-    s.l[k] = fmaf((float)a, Dl, s.l[k]);
+    if constexpr (L >= 2) {
+      s.h[k] = __fmaf_rn((float)a, __fsub_rn(h0, h1), s.h[k]);
+      s.l[k] = fmaf((float)a, l0 - l1, s.l[k]);
+    } else {
+      s.d[k - 1] = fmaf((float)a, d[i0] - d[j1], s.d[k - 1]);
+    }
     const float S = Sh + Sl;
-    s.d[kind == 2 ? 0 : 2] = fmaf((float)(a * a), S, s.d[kind == 2 ? 0 : 2]);
+    s.d[kind == 2 ? 2 : 4] = fmaf((float)(a * a), S, s.d[kind == 2 ? 2 : 4]);
   } else {
     float h[4], l[4];
     ex_split(d[i0], C[g], h[0], l[0]);
     ex_split(d[i1], C[g], h[1], l[1]);
     ex_split(d[i2], C[g], h[2], l[2]);
     ex_split(d[i3], C[g], h[3], l[3]);
-    const float ph = __fadd_rn(h[0], h[1]), qh = __fsub_rn(h[0], h[1]);
-    const float rh = __fadd_rn(h[2], h[3]), wh = __fsub_rn(h[2], h[3]);
-    const float pl = l[0] + l[1], ql = l[0] - l[1], rl = l[2] + l[3], wl = l[2] - l[3];
+    const float ph = __fadd_rn(h[0], h[1]), rh = __fadd_rn(h[2], h[3]);
+    const float pl = l[0] + l[1], rl = l[2] + l[3];
     const float Sh = __fadd_rn(ph, rh), Sl = pl + rl;
     s.h[0] = __fadd_rn(s.h[0], Sh);
-    s.h[1] = __fmaf_rn((float)ax, __fadd_rn(qh, wh), s.h[1]);
-    s.h[2] = __fmaf_rn((float)ay, __fsub_rn(ph, rh), s.h[2]);
     s.l[0] += Sl;
-    s.l[1] = fmaf((float)ax, ql + wl, s.l[1]);
-    s.l[2] = fmaf((float)ay, pl - rl, s.l[2]);
+    const float q = d[i0] - d[i1], w = d[i2] - d[i3];
+    if constexpr (L >= 2) {
+      const float qh = __fsub_rn(h[0], h[1]), wh = __fsub_rn(h[2], h[3]);
+      const float ql = l[0] - l[1], wl = l[2] - l[3];
+      s.h[1] = __fmaf_rn((float)ax, __fadd_rn(qh, wh), s.h[1]);
+      s.h[2] = __fmaf_rn((float)ay, __fsub_rn(ph, rh), s.h[2]);
+      s.l[1] = fmaf((float)ax, ql + wl, s.l[1]);
+      s.l[2] = fmaf((float)ay, pl - rl, s.l[2]);
+    } else {
+      const float p = d[i0] + d[i1], r = d[i2] + d[i3];
+      s.d[0] = fmaf((float)ax, q + w, s.d[0]);
+      s.d[1] = fmaf((float)ay, p - r, s.d[1]);
+    }
     const float S = Sh + Sl;
-    s.d[0] = fmaf((float)(ax * ax), S, s.d[0]);
-    s.d[1] = fmaf((float)(ax * ay), (qh - wh) + (ql - wl), s.d[1]);
-    s.d[2] = fmaf((float)(ay * ay), S, s.d[2]);
+    s.d[2] = fmaf((float)(ax * ax), S, s.d[2]);
+    s.d[3] = fmaf((float)(ax * ay), q - w, s.d[3]);
+    s.d[4] = fmaf((float)(ay * ay), S, s.d[4]);
   }
 }
 
@@ -234,27 +257,36 @@ __host__ __device__ constexpr bool ex_group_ends() {
 }
 
 // Orbit K, then, at the end of a group, that group's sums into the moments.
-template <class Def, int K>
+template <class Def, int L, int K>
 __device__ __forceinline__ void ex_orbit_step(const float (&d)[Def::Q], const FusedParams& p,
                                               const float (&C)[6], ExGroup& s, ExMoments& M) {
-  ex_acc_orbit<Def, K>(d, C, s);
+  ex_acc_orbit<Def, L, K>(d, C, s);
   if constexpr (ex_group_ends<Def, K>()) {
     constexpr int g = Def::O.grp[K];
     ex_acc(M.N0, p.gm[g][0], s.h[0], s.l[0]);
     ex_acc(M.K0, p.gk[g][0], s.h[0], s.l[0]);
-    ex_acc(M.Nx, p.gm[g][2], s.h[1], s.l[1]);
-    ex_acc(M.Kx, p.gk[g][1], s.h[1], s.l[1]);
-    ex_acc(M.Ny, p.gm[g][2], s.h[2], s.l[2]);
-    ex_acc(M.Ky, p.gk[g][1], s.h[2], s.l[2]);
-    M.Txx = hl_fma(p.gm[g][4], s.d[0], M.Txx);
-    M.Txy = hl_fma(p.gm[g][4], s.d[1], M.Txy);
-    M.Tyy = hl_fma(p.gm[g][4], s.d[2], M.Tyy);
+    if constexpr (L >= 2) {
+      ex_acc(M.Nx, p.gm[g][2], s.h[1], s.l[1]);
+      ex_acc(M.Kx, p.gk[g][1], s.h[1], s.l[1]);
+      ex_acc(M.Ny, p.gm[g][2], s.h[2], s.l[2]);
+      ex_acc(M.Ky, p.gk[g][1], s.h[2], s.l[2]);
+    } else {
+      M.Nx.hi = hl_fma(p.gm[g][2], s.d[0], M.Nx.hi);
+      M.Kx.hi = hl_fma(p.gk[g][1], s.d[0], M.Kx.hi);
+      M.Ny.hi = hl_fma(p.gm[g][2], s.d[1], M.Ny.hi);
+      M.Ky.hi = hl_fma(p.gk[g][1], s.d[1], M.Ky.hi);
+    }
+    M.Txx = hl_fma(p.gm[g][4], s.d[2], M.Txx);
+    M.Txy = hl_fma(p.gm[g][4], s.d[3], M.Txy);
+    M.Tyy = hl_fma(p.gm[g][4], s.d[4], M.Tyy);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) s.h[k] = s.l[k] = s.d[k] = 0.0f;
+    for (int k = 0; k < 3; ++k) s.h[k] = s.l[k] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) s.d[k] = 0.0f;
   }
 }
 
-template <class Def, int... Ks>
+template <class Def, int L, int... Ks>
 __device__ __forceinline__ void ex_acc_all(std::integer_sequence<int, Ks...>, const float (&d)[Def::Q],
                                            const FusedParams& p, ExMoments& M) {
   float C[6];
@@ -262,8 +294,10 @@ __device__ __forceinline__ void ex_acc_all(std::integer_sequence<int, Ks...>, co
   for (int g = 0; g < 6; ++g) C[g] = p.exC[g];
   ExGroup s;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) s.h[k] = s.l[k] = s.d[k] = 0.0f;
-  (ex_orbit_step<Def, Ks>(d, p, C, s, M), ...);
+  for (int k = 0; k < 3; ++k) s.h[k] = s.l[k] = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) s.d[k] = 0.0f;
+  (ex_orbit_step<Def, L, Ks>(d, p, C, s, M), ...);
 }
 
 // Relaxation and store of population I with equilibrium value e (f^eq - r).
@@ -320,11 +354,11 @@ __device__ __forceinline__ void fused_collide_orbit(const float (&d)[Def::Q], co
   }
 }
 
-template <class Def, bool BF, int... Is>
+template <class Def, bool BF, bool CG = false, int... Is>
 __device__ __forceinline__ void fused_load_all(std::integer_sequence<int, Is...>, float (&d)[Def::Q],
                                                const void* __restrict__ fin, const uint2* __restrict__ cin,
                                                long long plane, long long pitch, int x, int y, int Nx, int Ny) {
-  (fused_load<Def, BF, Is>(d, fin, cin, plane, pitch, x, y, Nx, Ny), ...);
+  (fused_load<Def, BF, Is, CG>(d, fin, cin, plane, pitch, x, y, Nx, Ny), ...);
 }
 
 template <class Def, int... Ks>
@@ -392,6 +426,17 @@ __device__ __forceinline__ void fused_collide_pop_all(std::integer_sequence<int,
   (fused_collide_pop<Def, BF, Is>(d, c, cq, a0, ax, ay, out, plane), ...);
 }
 
+// dR(Td) from the R(zeta) table, for temperatures outside the lattice's dR
+// table (out of line: rare, and it keeps the common path's registers free).
+static __device__ __noinline__ double dr_from_zeta(float Td, double mb64, double Rr64, const double* __restrict__ rt64,
+                                            unsigned& fl) {
+  const float Tf = 1.0f + Td;
+  const double T64 = 1.0 + (double)Td;
+  double iT = (double)__fdividef(1.0f, Tf);
+  iT = fma(iT, fma(-T64, iT, 1.0), iT);
+  return ratio64(mb64 * iT, rt64, fl) - Rr64;
+}
+
 // Site solve of the split arithmetic (see the header comment): from the
 // deviation moments M (reference excluded) to U, n = n_r + n_d and
 // T = 1 + T_d, R = R(mbar) + dR.  Landau frame by FP32 Newton on the full
@@ -440,18 +485,23 @@ __device__ __forceinline__ SplitSite split_solve(const P& p, const float (&M)[9]
   // e/n = y_r + y_d
   float yd;
   if constexpr (EX) {
-    // e - m n = U0^2 (K^0 - 2 v.K + v.T.v) + m U0 ((U0 - 1) N^0 - (2 U0 - 1) v.N)
-    // on the full moments (reference + deviation); no term cancels e or m n
-    const float K0 = p.k0r.hi + ((p.k0r.lo + em->K0.hi) + em->K0.lo);
+    // W = e - m n = U0^2 (K^0 - 2 v.K + v.T.v) + m U0 ((U0 - 1) N^0 - (2 U0 - 1) v.N)
+    // (no term cancels e against m n), formed as its deviation from the
+    // reference W_r = K^0_r = y_r n_r (y = W/n): W - W_r = U0^2 (K^0_d -
+    // 2 v.K + v.T.v) + dg (2 + dg) K^0_r + m U0 (...), so that FP32 rounding
+    // is relative to deviations, as in the plain path
+    const float K0d = em->K0.hi + em->K0.lo;
     const float Kx = em->Kx.hi + em->Kx.lo, Ky = em->Ky.hi + em->Ky.lo;
     const float Txx = p.mref[6].hi + (p.mref[6].lo + M[6]);
     const float Tyy = p.mref[8].hi + (p.mref[8].lo + M[8]);
     const float vTv = fmaf(vx * vx, Txx, fmaf(2.0f * vx * vy, M[7], vy * vy * Tyy));
-    const float kin = fmaf(-2.0f, fmaf(vx, Kx, vy * Ky), K0) + vTv;
+    const float kd = fmaf(-2.0f, fmaf(vx, Kx, vy * Ky), K0d) + vTv;
     const float N0 = p.nr.hi + ((p.nr.lo + em->N0.hi) + em->N0.lo);
     const float vN = fmaf(vx, M[1], vy * M[2]);
-    const float W = fmaf(U0 * U0, kin, p.mb * U0 * fmaf(dg, N0, -fmaf(2.0f, dg, 1.0f) * vN));
-    yd = (__fdividef(W, n) - p.ykr.hi) - p.ykr.lo;
+    const float U02m1 = dg * (2.0f + dg);
+    const float Wd = fmaf(U0 * U0, kd, fmaf(U02m1, p.k0r.hi, U02m1 * p.k0r.lo)) +
+                     p.mb * U0 * fmaf(dg, N0, -fmaf(2.0f, dg, 1.0f) * vN);
+    yd = __fdividef(Wd - fmaf(p.ykr.hi, nd, p.ykr.lo * nd), n);
   } else {
     const float ed = M[3] - M[4] * vx - M[5] * vy;
     yd = __fdividef(ed - fmaf(p.yr.hi, nd, p.yr.lo * nd), n);
@@ -475,22 +525,17 @@ __device__ __forceinline__ SplitSite split_solve(const P& p, const float (&M)[9]
     Td -= step;
     if (fabsf(step) < 3e-8f) break;
   }
-  // ... and one FP64 Newton step with the FP64 R(zeta) table
+  // ... and one FP64 Newton step: dR(Td) from the lattice's FP64 table in
+  // Td (no reciprocal, no reference subtraction), else from the R(zeta) table
   float dR;
   {
-    const float Tf = 1.0f + Td;
-    const double T64 = 1.0 + (double)Td;
-    double iT = (double)__fdividef(1.0f, Tf);
-    iT = fma(iT, fma(-T64, iT, 1.0), iT);
-    const double z64 = p.mb64 * iT;
-    const double dR64 = ratio64(z64, p.rt64, fl) - p.Rr64;
+    double dR64;
+    if (!dr_table64(Td, p.dr64, dR64)) dR64 = dr_from_zeta(Td, p.mb64, p.Rr64, p.rt64, fl);
     const double g64 = fma(3.0, (double)Td, fma(p.mb64, dR64, -(double)yd));
     const float step = __fdividef((float)g64, slope);
     Td -= step;
-    const float R = p.Rr.hi + (p.Rr.lo + (float)dR64);
-    const float z = (float)z64;
-    const float dRdz = R * R + 3.0f * __fdividef(R, z) - 1.0f;
-    dR = fmaf(dRdz, z * step / Tf, (float)dR64);     // R at the corrected T (first order)
+    // R at the corrected T to first order: d(dR)/dTd = (c_v - 3)/m, c_v = slope
+    dR = fmaf((slope - 3.0f) * __fdividef(1.0f, p.mb), -step, (float)dR64);
   }
   const float R = p.Rr.hi + (p.Rr.lo + dR);
   const float T = 1.0f + Td;
@@ -509,27 +554,27 @@ __device__ __forceinline__ SplitSite split_solve(const P& p, const float (&M)[9]
 }
 
 // One site update (see the header comment); p describes the lattice.
-template <class Def, bool BF, bool EX = false>
+template <class Def, bool BF, int EXL = 0, bool CG = false>
 __device__ __forceinline__ void fused_site(const FusedParams& p, const void* __restrict__ fin,
                                            void* __restrict__ fout, int site, unsigned& fl) {
-  static_assert(!(BF && EX), "extended moment sums are for FP32 storage");
+  static_assert(!(BF && EXL), "extended moment sums are for FP32 storage");
   constexpr int Q = Def::Q;
   using Seq = std::make_integer_sequence<int, Q>;
   {
     int x, y;
     site_of(site, p.Nx, x, y);
     float d[Q];
-    fused_load_all<Def, BF>(Seq{}, d, fin, static_cast<const uint2*>(p.cin), p.plane, p.pitch, x, y, p.Nx,
-                            p.Ny);
+    fused_load_all<Def, BF, CG>(Seq{}, d, fin, static_cast<const uint2*>(p.cin), p.plane, p.pitch, x, y, p.Nx,
+                                p.Ny);
     using Orb = std::make_integer_sequence<int, Def::O.K>;
     // deviation moments N0 Nx Ny T00 T0x T0y Txx Txy Tyy (reference excluded)
     float M[9];
     SplitSite ss;
-    if constexpr (EX) {
+    if constexpr (EXL > 0) {
       ExMoments em;
       em.N0 = em.Nx = em.Ny = em.K0 = em.Kx = em.Ky = FF{0.0f, 0.0f};
       em.Txx = em.Txy = em.Tyy = 0.0f;
-      ex_acc_all<Def>(Orb{}, d, p, em);
+      ex_acc_all<Def, EXL>(Orb{}, d, p, em);
       M[0] = em.N0.hi + em.N0.lo;
       M[1] = em.Nx.hi + em.Nx.lo;
       M[2] = em.Ny.hi + em.Ny.lo;
@@ -617,28 +662,30 @@ __device__ __forceinline__ void fused_site(const FusedParams& p, const void* __r
 // per stencil size on GB300: Q <= 40: 6 in FP32 (80 registers), 5 in BF16;
 // Q <= 64: 5 in FP32 (96 registers), 4 in BF16; larger stencils 4 (128
 // registers), where fewer registers would spill.
-template <class Def, bool BF, bool EX = false>
+template <class Def, bool BF, int EXL = 0>
 constexpr int fused_min_blocks() {
-  return Def::Q <= 40 ? ((BF || EX) ? 5 : 6) : ((Def::Q <= 64 && !BF && !EX) ? 5 : 4);
+  return Def::Q <= 40 ? ((BF || EXL) ? 5 : 6) : ((Def::Q <= 64 && !BF && EXL < 2) ? 5 : 4);
 }
 
-template <class Def, bool BF, bool EX = false>
-__global__ void __launch_bounds__(128, fused_min_blocks<Def, BF, EX>()) fused_f32_kernel(const __grid_constant__ FusedParams p,
+template <class Def, bool BF, int EXL = 0>
+__global__ void __launch_bounds__(128, fused_min_blocks<Def, BF, EXL>()) fused_f32_kernel(const __grid_constant__ FusedParams p,
                                                         const void* __restrict__ fin,
                                                         void* __restrict__ fout) {
   const int site = blockIdx.x * blockDim.x + threadIdx.x;
   unsigned fl = 0;
-  if (site < p.Nx * p.Ny) fused_site<Def, BF, EX>(p, fin, fout, site, fl);
+  if (site < p.Nx * p.Ny) fused_site<Def, BF, EXL>(p, fin, fout, site, fl);
   report(fl, p.err);
 }
 
 // Entry point of the step kernel of a stencil, for CUDA graph kernel nodes
 // (rlbm_batch_step); the node's grid is (Nx Ny + 127)/128 blocks of 128.
-// mode: 0 FP32, 1 BF16 deviation, 2 FP32 with extended moment sums.
+// mode: 0 FP32, 1 BF16 deviation, 2 / 3 FP32 with extended moment sums of
+// level 1 / 2.
 template <class Def>
 const void* fused_kernel_fn_impl(int mode) {
   return mode == 1 ? (const void*)&fused_f32_kernel<Def, true>
-         : mode == 2 ? (const void*)&fused_f32_kernel<Def, false, true>
+         : mode == 2 ? (const void*)&fused_f32_kernel<Def, false, 1>
+         : mode == 3 ? (const void*)&fused_f32_kernel<Def, false, 2>
                      : (const void*)&fused_f32_kernel<Def, false>;
 }
 
@@ -647,7 +694,8 @@ cudaError_t launch_fused_impl(const FusedParams& p, const void* fin, void* fout,
   const long long nsite = (long long)p.Nx * p.Ny;
   const unsigned grid = (unsigned)((nsite + 127) / 128);
   if (mode == 1) fused_f32_kernel<Def, true><<<grid, 128, 0, s>>>(p, fin, fout);
-  else if (mode == 2) fused_f32_kernel<Def, false, true><<<grid, 128, 0, s>>>(p, fin, fout);
+  else if (mode == 2) fused_f32_kernel<Def, false, 1><<<grid, 128, 0, s>>>(p, fin, fout);
+  else if (mode == 3) fused_f32_kernel<Def, false, 2><<<grid, 128, 0, s>>>(p, fin, fout);
   else fused_f32_kernel<Def, false><<<grid, 128, 0, s>>>(p, fin, fout);
   return cudaGetLastError();
 }
@@ -797,11 +845,139 @@ __global__ void __launch_bounds__(128) bf16_moments(const __grid_constant__ Step
   report(fl, p.err);
 }
 
+// ---------------------------------------------------- FP32 init and read-out
+// Init of FP32 storage on a compiled stencil: per site the FP64 group
+// coefficients of f^eq - r, then per population its group polynomial in
+// FP32 (as the step kernel evaluates it), written to S_0 at the site and to
+// S_{-1} at x - n_i (see init_kernel).
+template <class Def, int... Is>
+__device__ __forceinline__ void f32_init_pops(std::integer_sequence<int, Is...>, const float (&c)[6][6],
+                                              float* __restrict__ cur, float* __restrict__ prev,
+                                              long long plane, long long pitch, int x, int y, int Nx, int Ny) {
+  const long long here = (long long)y * pitch + x;
+  (
+      [&] {
+        constexpr int i = Is;
+        constexpr int g = Def::F.grp[i], nx = Def::F.nx[i], ny = Def::F.ny[i], mult = Def::F.mult[i];
+        float e = c[g][0];
+        if constexpr (nx != 0) e = fmaf((float)nx, c[g][1], e);
+        if constexpr (ny != 0) e = fmaf((float)ny, c[g][2], e);
+        if constexpr (nx != 0) e = fmaf((float)(nx * nx), c[g][3], e);
+        if constexpr (ny != 0) e = fmaf((float)(ny * ny), c[g][4], e);
+        if constexpr (nx != 0 && ny != 0) e = fmaf((float)(nx * ny), c[g][5], e);
+        if constexpr (mult != 1) e *= (float)mult;
+        cur[(long long)i * plane + here] = e;
+        // population i of S_{-1} sits at x - n_i: the first pull brings it back
+        const int xs = wrap_c<nx>(x, Nx), ys = wrap_c<ny>(y, Ny);
+        prev[(long long)i * plane + (long long)ys * pitch + xs] = e;
+      }(),
+      ...);
+}
+
+template <class Def>
+__global__ void __launch_bounds__(128) f32_init_kernel(const __grid_constant__ FusedParams p, SiteConsts sc,
+                                                       FieldPtrs fd, float* __restrict__ cur,
+                                                       float* __restrict__ prev) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned fl = 0;
+  if (s < p.Nx * p.Ny) {
+    int x, y;
+    site_of(s, p.Nx, x, y);
+    const double n = fd.n[s], ux = fd.ux[s], uy = fd.uy[s], T = fd.T[s];
+    if (!(ux * ux + uy * uy < 1.0)) fl |= ERR_LANDAU;
+    if (!(n > 0.0)) fl |= ERR_DENSITY;
+    if (!(T > 0.0)) fl |= ERR_EOS;
+    double c64[6][6];
+    fp64_group_coeffs(p, sc, n, ux, uy, T, c64, fl);
+    float c[6][6];
+#pragma unroll
+    for (int g = 0; g < 6; ++g)
+#pragma unroll
+      for (int k = 0; k < 6; ++k) c[g][k] = (float)c64[g][k];
+    f32_init_pops<Def>(std::make_integer_sequence<int, Def::Q>{}, c, cur, prev, p.plane, p.pitch, x, y, p.Nx,
+                       p.Ny);
+  }
+  report(fl, p.err);
+}
+
+// Read-out of FP32 storage on a compiled stencil: the pull of S_{t-1}, the
+// step kernel's extended moment sums (level 2: N^a and K^a to about 2^-40,
+// the spatial stress in FP32) and its split site solve (deviations from the
+// reference in FP32, the EOS finished by an FP64 Newton step), so n and T
+// carry FP32 rounding of their deviations from the reference only.  The
+// moment planes are assembled in FP64 from the float-float sums.
+template <class Def>
+__global__ void __launch_bounds__(128) f32_moments_kernel(const __grid_constant__ FusedParams fp,
+                                                          const __grid_constant__ StepParams<double> p,
+                                                          const float* __restrict__ prev, MomentOut mo) {
+  const int site = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned fl = 0;
+  const long long N = (long long)p.Nx * p.Ny;
+  if (site < N) {
+    int x, y;
+    site_of(site, p.Nx, x, y);
+    float d[Def::Q];
+    fused_load_all<Def, false>(std::make_integer_sequence<int, Def::Q>{}, d, prev, nullptr, p.plane, p.pitch, x,
+                               y, p.Nx, p.Ny);
+    ExMoments em;
+    em.N0 = em.Nx = em.Ny = em.K0 = em.Kx = em.Ky = FF{0.0f, 0.0f};
+    em.Txx = em.Txy = em.Tyy = 0.0f;
+    ex_acc_all<Def, 2>(std::make_integer_sequence<int, Def::O.K>{}, d, fp, em);
+    float M[9];
+    M[0] = em.N0.hi + em.N0.lo;
+    M[1] = em.Nx.hi + em.Nx.lo;
+    M[2] = em.Ny.hi + em.Ny.lo;
+    M[3] = fmaf(fp.mb, M[0], em.K0.hi + em.K0.lo);
+    M[4] = fmaf(fp.mb, M[1], em.Kx.hi + em.Kx.lo);
+    M[5] = fmaf(fp.mb, M[2], em.Ky.hi + em.Ky.lo);
+    M[6] = em.Txx;
+    M[7] = em.Txy;
+    M[8] = em.Tyy;
+    const SplitSite ss = split_solve<true>(fp, M, fl, &em);
+    // FP64 moments: reference + float-float deviations
+    const double N0 = (double)em.N0.hi + (double)em.N0.lo, Nx = (double)em.Nx.hi + (double)em.Nx.lo;
+    const double Ny = (double)em.Ny.hi + (double)em.Ny.lo, K0 = (double)em.K0.hi + (double)em.K0.lo;
+    const double Kx = (double)em.Kx.hi + (double)em.Kx.lo, Ky = (double)em.Ky.hi + (double)em.Ky.lo;
+    double m[9];
+    m[0] = p.mref[0] + N0;
+    m[1] = p.mref[1] + Nx;
+    m[2] = p.mref[2] + Ny;
+    m[3] = p.mref[3] + fma(fp.mb64, N0, K0);
+    m[4] = p.mref[4] + fma(fp.mb64, Nx, Kx);
+    m[5] = p.mref[5] + fma(fp.mb64, Ny, Ky);
+    m[6] = p.mref[6] + (double)em.Txx;
+    m[7] = p.mref[7] + (double)em.Txy;
+    m[8] = p.mref[8] + (double)em.Tyy;
+    const double vx = (double)ss.Ux / (double)ss.U0, vy = (double)ss.Uy / (double)ss.U0;
+    double* out = mo.out;
+    int plane = 0;
+    if (mo.mask & RLBM_M_N) out[(plane++) * N + site] = fp.nr64 + (double)ss.nd;
+    if (mo.mask & RLBM_M_UX) out[(plane++) * N + site] = vx;
+    if (mo.mask & RLBM_M_UY) out[(plane++) * N + site] = vy;
+    if (mo.mask & RLBM_M_T) out[(plane++) * N + site] = 1.0 + (double)ss.Td;
+    if (mo.mask & RLBM_M_E) out[(plane++) * N + site] = m[3] - m[4] * vx - m[5] * vy;
+    if (mo.mask & RLBM_M_NVEC)
+      for (int k = 0; k < 3; ++k) out[(plane++) * N + site] = m[k];
+    if (mo.mask & RLBM_M_TMN)
+      for (int k = 3; k < 9; ++k) out[(plane++) * N + site] = m[k];
+  }
+  report(fl, p.err);
+}
+
+// what: 0 BF16 init, 1 BF16 read-out, 2 FP32 init, 3 FP32 read-out.
 template <class Def>
 cudaError_t launch_bf16_io_impl(int what, const FusedParams& fp, const StepParams<double>& p, FieldPtrs fd,
                                 void* cur, void* prev, void* ccur, void* cprev, MomentOut mo, cudaStream_t s) {
   const long long nsite = (long long)p.Nx * p.Ny;
   const unsigned grid = (unsigned)((nsite + 127) / 128);
+  if (what == 2) {
+    f32_init_kernel<Def><<<grid, 128, 0, s>>>(fp, p.sc, fd, static_cast<float*>(cur), static_cast<float*>(prev));
+    return cudaGetLastError();
+  }
+  if (what == 3) {
+    f32_moments_kernel<Def><<<grid, 128, 0, s>>>(fp, p, static_cast<const float*>(prev), mo);
+    return cudaGetLastError();
+  }
   if (what == 0) {
     bf16_init_coeffs<Def><<<grid, 128, 0, s>>>(fp, p.sc, fd, static_cast<uint2*>(ccur), static_cast<uint2*>(cprev));
     bf16_init_pops<Def><<<grid, 128, 0, s>>>(fp, p.sc, fd, static_cast<const uint2*>(ccur),

@@ -1,5 +1,6 @@
 // Fused FP32 kernel for the stencil G1,G14,G49,G51,G60,G70.
 #include "rlbm_fused.cuh"
+#include "rlbm_persist.cuh"
 #include "rlbm_fused_launch.h"
 
 namespace rlbm {
@@ -15,5 +16,9 @@ cudaError_t launch_bf16_io<StencilE5>(int what, const FusedParams& fp, const Ste
 template <>
 const void* fused_kernel_fn<StencilE5>(int mode) {
   return fused_kernel_fn_impl<StencilE5>(mode);
+}
+template <>
+const void* persist_kernel_fn<StencilE5>(int mode) {
+  return persist_kernel_fn_impl<StencilE5>(mode);
 }
 }  // namespace rlbm

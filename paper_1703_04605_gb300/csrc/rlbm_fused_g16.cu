@@ -1,5 +1,6 @@
 // Fused FP32 kernel for the stencil G1..G6.
 #include "rlbm_fused.cuh"
+#include "rlbm_persist.cuh"
 #include "rlbm_fused_launch.h"
 
 namespace rlbm {
@@ -15,5 +16,9 @@ cudaError_t launch_bf16_io<StencilG16>(int what, const FusedParams& fp, const St
 template <>
 const void* fused_kernel_fn<StencilG16>(int mode) {
   return fused_kernel_fn_impl<StencilG16>(mode);
+}
+template <>
+const void* persist_kernel_fn<StencilG16>(int mode) {
+  return persist_kernel_fn_impl<StencilG16>(mode);
 }
 }  // namespace rlbm

@@ -32,12 +32,25 @@ template <>
 const void* fused_kernel_fn<StencilE5>(int);
 template <>
 const void* fused_kernel_fn<StencilS2>(int);
+// The persistent batched kernel of a stencil (rlbm_persist.cuh) for a storage
+// variant (mode as above), taking one PersistParams; block 128, cooperative.
+template <class Def>
+const void* persist_kernel_fn(int mode);
+template <>
+const void* persist_kernel_fn<StencilM1>(int);
+template <>
+const void* persist_kernel_fn<StencilG16>(int);
+template <>
+const void* persist_kernel_fn<StencilE5>(int);
+template <>
+const void* persist_kernel_fn<StencilS2>(int);
 // The compiled third-order kernel of kind 5..10 (FusedO3Params, const float*
 // fin, float* fout), for graph kernel nodes; grid (Nx Ny + 127)/128, block
 // 128, no dynamic shared memory (rlbm_fused_o3.cu).
 const void* fused_o3_kernel_fn(int kind);
-// BF16 deviation storage: what = 0 init (fields -> coefficients, S_0, S_{-1}),
-// what = 1 read-out of the pull of prev.
+// Init and read-out on a compiled stencil.  BF16 deviation storage: what = 0
+// init (fields -> coefficients, S_0, S_{-1}), what = 1 read-out of the pull of
+// prev; FP32 storage: what = 2 init, what = 3 read-out (ccur, cprev unused).
 template <class Def>
 cudaError_t launch_bf16_io(int what, const FusedParams& fp, const StepParams<double>& p, FieldPtrs fd,
                            void* cur, void* prev, void* ccur, void* cprev, MomentOut mo, cudaStream_t s);

@@ -1,5 +1,6 @@
 // Fused FP32 kernel for the stencil G5,G12,G14,G17,G21,G26.
 #include "rlbm_fused.cuh"
+#include "rlbm_persist.cuh"
 #include "rlbm_fused_launch.h"
 
 namespace rlbm {
@@ -15,5 +16,9 @@ cudaError_t launch_bf16_io<StencilM1>(int what, const FusedParams& fp, const Ste
 template <>
 const void* fused_kernel_fn<StencilM1>(int mode) {
   return fused_kernel_fn_impl<StencilM1>(mode);
+}
+template <>
+const void* persist_kernel_fn<StencilM1>(int mode) {
+  return persist_kernel_fn_impl<StencilM1>(mode);
 }
 }  // namespace rlbm

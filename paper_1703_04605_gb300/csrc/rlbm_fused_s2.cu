@@ -1,5 +1,6 @@
 // Fused FP32 kernel for the stencil G3,G9,G10,G14,G17,G21.
 #include "rlbm_fused.cuh"
+#include "rlbm_persist.cuh"
 #include "rlbm_fused_launch.h"
 
 namespace rlbm {
@@ -15,5 +16,9 @@ cudaError_t launch_bf16_io<StencilS2>(int what, const FusedParams& fp, const Ste
 template <>
 const void* fused_kernel_fn<StencilS2>(int mode) {
   return fused_kernel_fn_impl<StencilS2>(mode);
+}
+template <>
+const void* persist_kernel_fn<StencilS2>(int mode) {
+  return persist_kernel_fn_impl<StencilS2>(mode);
 }
 }  // namespace rlbm

@@ -35,6 +35,7 @@ struct rlbm_ctx {
   unsigned* d_err = nullptr;
   double* d_rt64 = nullptr;
   float* d_rt32 = nullptr;
+  double* d_dr64 = nullptr;      // the lattice's dR(Td) table (FP32 kernels' EOS step)
   double* d_fields = nullptr;   // 4 planes for rlbm_init
   double* d_out = nullptr;      // read-out planes
   size_t out_cap = 0;
@@ -63,9 +64,9 @@ static thread_local std::string g_create_error;
 static void batch_forget(const rlbm_ctx* c);   // drop cached batch graphs that use c
 
 // Variant of the compiled second-order kernel: 0 FP32, 1 BF16 deviation,
-// 2 FP32 with extended moment sums.
+// 2 / 3 FP32 with extended moment sums of level 1 / 2.
 static int fused_mode(const rlbm_ctx* c) {
-  return c->dtype == RLBM_BF16_DEV ? 1 : (c->ext ? 2 : 0);
+  return c->dtype == RLBM_BF16_DEV ? 1 : (c->ext ? 1 + c->ext : 0);
 }
 
 // The allocator installed by rlbm_set_allocator (all null: cudaMalloc).
@@ -100,6 +101,7 @@ static void release(rlbm_ctx* c) {
   if (!c) return;
   if (c->buf[0]) cudaStreamSynchronize(c->stream);
   for (void* p : {c->buf[0], c->buf[1], c->coef[0], c->coef[1], (void*)c->d_err, (void*)c->d_rt64, (void*)c->d_rt32,
+                  (void*)c->d_dr64,
                   (void*)c->d_fields, (void*)c->d_out, (void*)c->d_shift, (void*)c->d_off, (void*)c->d_tab64,
                   (void*)c->d_tab32})
     c->mem.put(p);
@@ -187,6 +189,7 @@ static void fill_fused(rlbm_ctx* c, double nref) {
     for (int q = 0; q < 5; ++q) f.gm[g][q] = split(sb.gm[g][q]);
     for (int q = 0; q < 10; ++q) f.gf[g][q] = split(sb.gf[g][q]);
     for (int q = 0; q < 2; ++q) f.gk[g][q] = split(sb.gk[g][q]);
+    for (int q = 0; q < 5; ++q) f.gm64[g][q] = sb.gm[g][q];
     // split grid q = 2^(ceil(log2 r_g) - 11), r_g the group's largest
     // reference population: its h-sums (at most 24 members, weights up to 6)
     // stay exact while the pulled values stay below about 50 r_g
@@ -197,6 +200,7 @@ static void fill_fused(rlbm_ctx* c, double nref) {
   f.ykr = split(sb.ykr1);
   f.rt64 = c->d_rt64;
   f.rt32 = c->d_rt32;
+  f.dr64 = c->d_dr64;
   f.err = c->d_err;
 }
 
@@ -270,6 +274,7 @@ static void fill_fused_o3(rlbm_ctx* c, double nref) {
   }
   f.rt64 = c->d_rt64;
   f.rt32 = c->d_rt32;
+  f.dr64 = c->d_dr64;
   f.err = c->d_err;
 }
 
@@ -302,6 +307,10 @@ static rlbm_status check_device_error(rlbm_ctx* c) {
   if (h) {
     cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream);
     cudaStreamSynchronize(c->stream);
+    if (h & ERR_TIMEOUT)
+      return fail(c, RLBM_ETIMEOUT,
+                  "a bounded device-side wait of the persistent batch kernel ran out; the lattice's state is "
+                  "undefined until rlbm_init");
     std::string msg = "non-physical site(s):";
     if (h & ERR_LANDAU) msg += " Landau frame failed or |u| >= 1;";
     if (h & ERR_DENSITY) msg += " n <= 0;";
@@ -352,11 +361,13 @@ static rlbm_status create_o3(const rlbm_stencil* st, double m, double tau, int N
   }
   const auto& t64 = ratio_table64();
   const auto& t32 = ratio_table32();
+  const std::vector<double> drt = dr_table(m);
   const size_t nsite = (size_t)Nx * Ny;
   const size_t tbytes = (size_t)Q * kRowO3;
   bool ok = c->mem.get(&c->d_err, sizeof(unsigned)) == cudaSuccess &&
             c->mem.get(&c->d_rt64, t64.size() * sizeof(double)) == cudaSuccess &&
             c->mem.get(&c->d_rt32, t32.size() * sizeof(float)) == cudaSuccess &&
+            c->mem.get(&c->d_dr64, drt.size() * sizeof(double)) == cudaSuccess &&
             c->mem.get(&c->d_fields, 4 * nsite * sizeof(double)) == cudaSuccess &&
             c->mem.get(&c->d_shift, 2 * Q * sizeof(int)) == cudaSuccess &&
             c->mem.get(&c->d_off, Q * sizeof(long long)) == cudaSuccess &&
@@ -366,8 +377,8 @@ static rlbm_status create_o3(const rlbm_stencil* st, double m, double tau, int N
     release(c.get());
     return fail(nullptr, RLBM_ENOMEM, "device allocation failed");
   }
-  c->device_bytes = 2 * fbytes + sizeof(unsigned) + t64.size() * 8 + t32.size() * 4 + 4 * nsite * 8 +
-                    2 * Q * sizeof(int) + Q * sizeof(long long) + tbytes * 12;
+  c->device_bytes = 2 * fbytes + sizeof(unsigned) + t64.size() * 8 + t32.size() * 4 + drt.size() * 8 +
+                    4 * nsite * 8 + 2 * Q * sizeof(int) + Q * sizeof(long long) + tbytes * 12;
   std::vector<int> shift(2 * Q);
   std::vector<long long> off(Q);
   std::vector<double> tab64(tbytes);
@@ -388,7 +399,11 @@ static rlbm_status create_o3(const rlbm_stencil* st, double m, double tau, int N
   if (e == cudaSuccess) e = cudaMemcpy(c->d_off, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_tab64, tab64.data(), tbytes * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_tab32, tab32.data(), tbytes * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_dr64, drt.data(), drt.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(unsigned));
+  // pageable uploads may return before their DMA lands: finish them before
+  // any kernel runs on a stream that is not ordered after the legacy stream
+  if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
   if (e != cudaSuccess) {
     release(c.get());
     return fail(nullptr, RLBM_ECUDA, std::string("upload: ") + cudaGetErrorString(e));
@@ -482,19 +497,26 @@ rlbm_status rlbm_create(const rlbm_stencil* st, double m, double tau, int Nx, in
   }
   const auto& t64 = ratio_table64();
   const auto& t32 = ratio_table32();
+  const std::vector<double> drt = dr_table(m);
   const size_t nsite = (size_t)Nx * Ny;
   bool ok = c->mem.get(&c->d_err, sizeof(unsigned)) == cudaSuccess &&
             c->mem.get(&c->d_rt64, t64.size() * sizeof(double)) == cudaSuccess &&
             c->mem.get(&c->d_rt32, t32.size() * sizeof(float)) == cudaSuccess &&
+            c->mem.get(&c->d_dr64, drt.size() * sizeof(double)) == cudaSuccess &&
             c->mem.get(&c->d_fields, 4 * nsite * sizeof(double)) == cudaSuccess;
   if (!ok) {
     release(c.get());
     return fail(nullptr, RLBM_ENOMEM, "device allocation failed");
   }
-  c->device_bytes = 2 * fbytes + sizeof(unsigned) + t64.size() * 8 + t32.size() * 4 + 4 * nsite * 8;
+  c->device_bytes = 2 * fbytes + sizeof(unsigned) + t64.size() * 8 + t32.size() * 4 + drt.size() * 8 +
+                    4 * nsite * 8;
   e = cudaMemcpy(c->d_rt64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_rt32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_dr64, drt.data(), drt.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(unsigned));
+  // pageable uploads may return before their DMA lands: finish them before
+  // any kernel runs on a stream that is not ordered after the legacy stream
+  if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
   if (e != cudaSuccess) {
     release(c.get());
     return fail(nullptr, RLBM_ECUDA, std::string("upload: ") + cudaGetErrorString(e));
@@ -547,6 +569,12 @@ rlbm_status rlbm_init_device(rlbm_ctx* c, const double* n, const double* ux, con
     else if (c->fused == 2) e = launch_bf16_io<StencilG16>(0, *c->fp, *c->p64, fp, c->buf[0], c->buf[1], c->coef[0], c->coef[1], none, c->stream);
     else if (c->fused == 3) e = launch_bf16_io<StencilE5>(0, *c->fp, *c->p64, fp, c->buf[0], c->buf[1], c->coef[0], c->coef[1], none, c->stream);
     else e = launch_bf16_io<StencilS2>(0, *c->fp, *c->p64, fp, c->buf[0], c->buf[1], c->coef[0], c->coef[1], none, c->stream);
+  } else if (c->dtype == RLBM_F32 && c->fused) {
+    MomentOut none{nullptr, 0};
+    if (c->fused == 1) e = launch_bf16_io<StencilM1>(2, *c->fp, *c->p64, fp, c->buf[0], c->buf[1], nullptr, nullptr, none, c->stream);
+    else if (c->fused == 2) e = launch_bf16_io<StencilG16>(2, *c->fp, *c->p64, fp, c->buf[0], c->buf[1], nullptr, nullptr, none, c->stream);
+    else if (c->fused == 3) e = launch_bf16_io<StencilE5>(2, *c->fp, *c->p64, fp, c->buf[0], c->buf[1], nullptr, nullptr, none, c->stream);
+    else e = launch_bf16_io<StencilS2>(2, *c->fp, *c->p64, fp, c->buf[0], c->buf[1], nullptr, nullptr, none, c->stream);
   } else {
     e = launch_init(c->dtype, *c->p64, fp, c->buf[0], c->buf[1], c->stream);
   }
@@ -595,7 +623,8 @@ rlbm_status rlbm_set_extended_sums(rlbm_ctx* c, int on) {
   if (!c) return RLBM_EINVAL;
   if (c->order != 2 || c->dtype != RLBM_F32 || !c->fused)
     return fail(c, RLBM_ENOTSUP, "extended moment sums need FP32 storage on a compiled second-order stencil");
-  const int v = on ? 1 : 0;
+  if (on < 0 || on > 2) return fail(c, RLBM_EINVAL, "extended sums level must be 0, 1 or 2");
+  const int v = on;
   if (v != c->ext) batch_forget(c);
   c->ext = v;
   return RLBM_OK;
@@ -667,6 +696,13 @@ rlbm_status rlbm_moments(rlbm_ctx* c, double* out, unsigned mask) {
     else if (c->fused == 2) e = launch_bf16_io<StencilG16>(1, *c->fp, *c->p64, none, nullptr, pv, nullptr, cp, mo, c->stream);
     else if (c->fused == 3) e = launch_bf16_io<StencilE5>(1, *c->fp, *c->p64, none, nullptr, pv, nullptr, cp, mo, c->stream);
     else e = launch_bf16_io<StencilS2>(1, *c->fp, *c->p64, none, nullptr, pv, nullptr, cp, mo, c->stream);
+  } else if (c->dtype == RLBM_F32 && c->fused) {
+    FieldPtrs none{nullptr, nullptr, nullptr, nullptr};
+    void* pv = c->buf[1 - c->cur];
+    if (c->fused == 1) e = launch_bf16_io<StencilM1>(3, *c->fp, *c->p64, none, nullptr, pv, nullptr, nullptr, mo, c->stream);
+    else if (c->fused == 2) e = launch_bf16_io<StencilG16>(3, *c->fp, *c->p64, none, nullptr, pv, nullptr, nullptr, mo, c->stream);
+    else if (c->fused == 3) e = launch_bf16_io<StencilE5>(3, *c->fp, *c->p64, none, nullptr, pv, nullptr, nullptr, mo, c->stream);
+    else e = launch_bf16_io<StencilS2>(3, *c->fp, *c->p64, none, nullptr, pv, nullptr, nullptr, mo, c->stream);
   } else {
     e = launch_moments(c->dtype, *c->p64, c->buf[1 - c->cur], mo, c->stream);
   }
@@ -793,9 +829,47 @@ struct BatchPlan {
   cudaGraphExec_t exec = nullptr;
 };
 
+// The autotuner's choice for a batch: the graph engine with G steps per
+// replay, or the persistent engine with spt sites per thread.
+struct BatchChoice {
+  int engine = RLBM_BATCH_GRAPH;
+  int param = 8;
+};
+
+// A persistent launch: the lattices of a batch that share a compiled stencil
+// and storage variant, in claim order (largest first), with their device
+// descriptors, the units of one step and the launch's control words.
+struct PersistGroup {
+  const void* fn = nullptr;
+  std::vector<rlbm_ctx*> lats;
+  PersistLattice* d_lat = nullptr;
+  int2* d_units = nullptr;
+  int* d_par0 = nullptr;
+  unsigned* d_ctl = nullptr;      // ticket, abort, done[nlat]
+  std::vector<int> par0;          // host copy uploaded before each launch
+  int units_per_step = 0;
+  int grid = 0;
+};
+
+struct PersistPlan {
+  int spt = 0;
+  std::vector<PersistGroup> groups;
+};
+
 std::mutex g_batch_mutex;
-std::map<std::string, int> g_tuned;          // batch signature -> steps per graph
+std::map<std::string, BatchChoice> g_tuned;  // batch signature -> engine choice
 std::map<std::string, BatchPlan> g_plans;    // signature with parities and G -> graph
+std::map<std::string, PersistPlan> g_pplans; // signature and spt -> persistent launches
+rlbm_batch_options g_bopt = {RLBM_BATCH_AUTO, 0u, 0u};
+
+constexpr unsigned kDefaultSpinLimit = 1u << 23;   // polls of ~0.3 us: about 2.5 s
+
+void free_pplan(PersistPlan& pl) {
+  for (PersistGroup& g : pl.groups)
+    for (void* q : {(void*)g.d_lat, (void*)g.d_units, (void*)g.d_par0, (void*)g.d_ctl})
+      if (q) cudaFree(q);
+  pl.groups.clear();
+}
 
 std::string signature(rlbm_ctx* const* ctxs, int n, bool with_parity) {
   std::string s;
@@ -881,6 +955,134 @@ cudaError_t plan_for(rlbm_ctx* const* ctxs, int count, const std::vector<rlbm_ct
   return cudaSuccess;
 }
 
+const void* persist_fn_of(const rlbm_ctx* c) {
+  const int mode = fused_mode(c);
+  switch (c->fused) {
+    case 1: return persist_kernel_fn<StencilM1>(mode);
+    case 2: return persist_kernel_fn<StencilG16>(mode);
+    case 3: return persist_kernel_fn<StencilE5>(mode);
+    default: return persist_kernel_fn<StencilS2>(mode);
+  }
+}
+
+// Lattices grouped by kernel (stencil and variant), each group largest first.
+cudaError_t build_pplan(const std::vector<rlbm_ctx*>& v, int spt, PersistPlan& plan) {
+  plan.spt = spt;
+  std::map<const void*, std::vector<rlbm_ctx*>> by_fn;
+  std::vector<const void*> order;
+  for (rlbm_ctx* c : by_size(v)) {
+    const void* fn = persist_fn_of(c);
+    if (!by_fn.count(fn)) order.push_back(fn);
+    by_fn[fn].push_back(c);
+  }
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  for (const void* fn : order) {
+    if (e != cudaSuccess) break;
+    PersistGroup g;
+    g.fn = fn;
+    g.lats = by_fn[fn];
+    const int nl = (int)g.lats.size();
+    std::vector<PersistLattice> hl(nl);
+    std::vector<int2> units;
+    const int tile = 128 * spt;
+    for (int l = 0; l < nl; ++l) {
+      rlbm_ctx* c = g.lats[l];
+      PersistLattice& L = hl[l];
+      std::memset(&L, 0, sizeof L);
+      for (int par = 0; par < 2; ++par) {
+        L.p[par] = *c->fp;
+        L.p[par].cin = c->coef[par];
+        L.p[par].cout = c->coef[1 - par];
+      }
+      L.buf[0] = c->buf[0];
+      L.buf[1] = c->buf[1];
+      L.nsite = c->Nx * c->Ny;
+      L.ntiles = (L.nsite + tile - 1) / tile;
+      for (int t = 0; t < L.ntiles; ++t) units.push_back(make_int2(l, t));
+    }
+    g.units_per_step = (int)units.size();
+    g.par0.assign(nl, 0);
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 128, 0);
+    if (e == cudaSuccess && nb < 1) e = cudaErrorInvalidConfiguration;
+    g.grid = std::max(1, std::min(nb * sms, g.units_per_step));
+    if (e == cudaSuccess) e = cudaMalloc(&g.d_lat, nl * sizeof(PersistLattice));
+    if (e == cudaSuccess) e = cudaMalloc(&g.d_units, units.size() * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMalloc(&g.d_par0, nl * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&g.d_ctl, (2 + nl) * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemcpy(g.d_lat, hl.data(), nl * sizeof(PersistLattice), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(g.d_units, units.data(), units.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);   // pageable uploads landed
+    plan.groups.push_back(std::move(g));
+  }
+  return e;
+}
+
+// nsteps steps of every group, one cooperative launch per group and chunk of
+// steps (tickets stay below 2^31).
+cudaError_t persist_launch(PersistPlan& plan, int nsteps, unsigned spin_limit, unsigned wait_offset,
+                           cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  for (PersistGroup& g : plan.groups) {
+    const int nl = (int)g.lats.size();
+    const int chunk = std::max(1, (int)std::min<long long>(nsteps, (1LL << 31) / std::max(1, g.units_per_step)));
+    for (int done = 0; done < nsteps && e == cudaSuccess; done += chunk) {
+      const int k = std::min(chunk, nsteps - done);
+      for (int l = 0; l < nl; ++l) g.par0[l] = g.lats[l]->cur ^ (done & 1);
+      e = cudaMemsetAsync(g.d_ctl, 0, (2 + nl) * sizeof(unsigned), s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(g.d_par0, g.par0.data(), nl * sizeof(int), cudaMemcpyHostToDevice, s);
+      PersistParams pp;
+      std::memset(&pp, 0, sizeof pp);
+      pp.lat = g.d_lat;
+      pp.units = g.d_units;
+      pp.nlat = nl;
+      pp.units_per_step = g.units_per_step;
+      pp.nsteps = k;
+      pp.spt = plan.spt;
+      pp.spin_limit = spin_limit;
+      pp.wait_offset = wait_offset;
+      pp.ticket = g.d_ctl;
+      pp.abort = g.d_ctl + 1;
+      pp.done = g.d_ctl + 2;
+      pp.par0 = g.d_par0;
+      void* args[1] = {&pp};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeCooperative;
+      attr[0].val.cooperative = 1;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)g.grid);
+      cfg.blockDim = dim3(128);
+      cfg.dynamicSmemBytes = 0;
+      cfg.stream = s;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      if (e == cudaSuccess) e = cudaLaunchKernelExC(&cfg, g.fn, args);
+      // the pageable par0 copy returns once staged, so par0 may change below
+    }
+  }
+  return e;
+}
+
+cudaError_t pplan_for(rlbm_ctx* const* ctxs, int count, const std::vector<rlbm_ctx*>& v, int spt,
+                      PersistPlan** out) {
+  const std::string key = signature(ctxs, count, false) + "/p" + std::to_string(spt);
+  auto it = g_pplans.find(key);
+  if (it == g_pplans.end()) {
+    PersistPlan plan;
+    cudaError_t e = build_pplan(v, spt, plan);
+    if (e != cudaSuccess) {
+      free_pplan(plan);
+      return e;
+    }
+    it = g_pplans.emplace(key, std::move(plan)).first;
+  }
+  *out = &it->second;
+  return cudaSuccess;
+}
+
 }  // namespace
 
 static void batch_forget(const rlbm_ctx* c) {
@@ -891,6 +1093,14 @@ static void batch_forget(const rlbm_ctx* c) {
     if (it->first.find(b) != std::string::npos) {
       if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
       it = g_plans.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  for (auto it = g_pplans.begin(); it != g_pplans.end();) {
+    if (it->first.find(b) != std::string::npos) {
+      free_pplan(it->second);
+      it = g_pplans.erase(it);
     } else {
       ++it;
     }
@@ -938,41 +1148,73 @@ extern "C" rlbm_status rlbm_batch_step(rlbm_ctx* const* ctxs, int count, int nst
     s = bridge;
   }
   const std::string sig = signature(ctxs, count, false);
+  bool any_o3 = false;
+  for (rlbm_ctx* c : v) any_o3 = any_o3 || c->order == 3;
+  const unsigned spin = g_bopt.spin_limit ? g_bopt.spin_limit : kDefaultSpinLimit;
   int done = 0;
-  int G = 0;
+  BatchChoice ch;
   auto tuned = g_tuned.find(sig);
   if (tuned != g_tuned.end()) {
-    G = tuned->second;
+    ch = tuned->second;
+  } else if (g_bopt.engine == RLBM_BATCH_PERSISTENT && !any_o3) {
+    ch.engine = RLBM_BATCH_PERSISTENT;
+    ch.param = 2;
+    g_tuned[sig] = ch;
   } else {
-    // autotune: one replay of each candidate graph, timed; those steps count
+    // autotune: time each candidate on steps that count towards nsteps
     const int cand[3] = {2, 8, 32};
-    const int total = cand[0] + cand[1] + cand[2];
+    const int spts[3] = {1, 2, 4};
+    const bool try_persist = g_bopt.engine == RLBM_BATCH_AUTO && !any_o3;
+    const int kp = 8;
+    const int total = cand[0] + cand[1] + cand[2] + (try_persist ? 3 * kp : 0);
     if (nsteps >= total) {
       e = cudaEventCreate(&ev.a);
       if (e == cudaSuccess) e = cudaEventCreate(&ev.b);
       float best = 1e30f;
-      for (int g : cand) {
-        BatchPlan* pl = nullptr;
-        if (e == cudaSuccess) e = plan_for(ctxs, count, v, g, s, &pl);
+      auto timed = [&](auto&& run, int k, int engine, int param) {
         if (e == cudaSuccess) e = cudaEventRecord(ev.a, s);
-        if (e == cudaSuccess) e = cudaGraphLaunch(pl->exec, s);
+        if (e == cudaSuccess) e = run();
         if (e == cudaSuccess) e = cudaEventRecord(ev.b, s);
         if (e == cudaSuccess) e = cudaEventSynchronize(ev.b);
         float ms = 0.0f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev.a, ev.b);
-        if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch autotune");
-        advance_all(v, g);
-        done += g;
-        if (ms / g < best) {
-          best = ms / g;
-          G = g;
+        if (e != cudaSuccess) return;
+        advance_all(v, k);
+        done += k;
+        if (ms / k < best) {
+          best = ms / k;
+          ch.engine = engine;
+          ch.param = param;
         }
+      };
+      for (int g : cand) {
+        BatchPlan* pl = nullptr;
+        if (e == cudaSuccess) e = plan_for(ctxs, count, v, g, s, &pl);
+        timed([&] { return cudaGraphLaunch(pl->exec, s); }, g, RLBM_BATCH_GRAPH, g);
       }
-      g_tuned[sig] = G;
+      if (try_persist)
+        for (int spt : spts) {
+          PersistPlan* pp = nullptr;
+          if (e == cudaSuccess) e = pplan_for(ctxs, count, v, spt, &pp);
+          timed([&] { return persist_launch(*pp, kp, spin, g_bopt.wait_offset, s); }, kp,
+                RLBM_BATCH_PERSISTENT, spt);
+        }
+      if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch autotune");
+      g_tuned[sig] = ch;
     } else {
-      G = nsteps >= cand[1] ? cand[1] : cand[0];   // too few steps to tune: not cached
+      ch.engine = RLBM_BATCH_GRAPH;          // too few steps to tune: not cached
+      ch.param = nsteps >= cand[1] ? cand[1] : cand[0];
     }
   }
+  if (ch.engine == RLBM_BATCH_PERSISTENT && nsteps > done) {
+    PersistPlan* pp = nullptr;
+    e = pplan_for(ctxs, count, v, ch.param, &pp);
+    if (e == cudaSuccess) e = persist_launch(*pp, nsteps - done, spin, g_bopt.wait_offset, s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch persistent launch");
+    advance_all(v, nsteps - done);
+    done = nsteps;
+  }
+  const int G = ch.engine == RLBM_BATCH_GRAPH ? ch.param : 2;
   for (int g : {G, 2}) {
     if (nsteps - done < g) continue;
     BatchPlan* pl = nullptr;
@@ -1007,7 +1249,40 @@ extern "C" rlbm_status rlbm_batch_tuning(rlbm_ctx* const* ctxs, int count, int* 
   std::lock_guard<std::mutex> lock(g_batch_mutex);
   auto tuned = g_tuned.find(signature(ctxs, count, false));
   if (tuned == g_tuned.end()) return fail(nullptr, RLBM_EINVAL, "batch tuning: this batch has not been tuned");
-  if (steps_per_graph) *steps_per_graph = tuned->second;
-  if (launches_per_step) *launches_per_step = count;
+  const bool graph = tuned->second.engine == RLBM_BATCH_GRAPH;
+  if (steps_per_graph) *steps_per_graph = graph ? tuned->second.param : 0;
+  if (launches_per_step) *launches_per_step = graph ? count : 0;
+  return RLBM_OK;
+}
+
+extern "C" rlbm_status rlbm_batch_engine(rlbm_ctx* const* ctxs, int count, int* engine, int* param,
+                                         int* launches) {
+  if (!ctxs || count < 1) return fail(nullptr, RLBM_EINVAL, "batch engine: bad arguments");
+  for (int i = 0; i < count; ++i)
+    if (!ctxs[i]) return fail(nullptr, RLBM_EINVAL, "batch engine: a context is missing");
+  std::lock_guard<std::mutex> lock(g_batch_mutex);
+  const std::string sig = signature(ctxs, count, false);
+  auto tuned = g_tuned.find(sig);
+  if (tuned == g_tuned.end()) return fail(nullptr, RLBM_EINVAL, "batch engine: no engine chosen for this batch yet");
+  const BatchChoice ch = tuned->second;
+  int nl = count;
+  if (ch.engine == RLBM_BATCH_PERSISTENT) {
+    auto it = g_pplans.find(sig + "/p" + std::to_string(ch.param));
+    nl = it == g_pplans.end() ? 0 : (int)it->second.groups.size();
+  }
+  if (engine) *engine = ch.engine;
+  if (param) *param = ch.param;
+  if (launches) *launches = nl;
+  return RLBM_OK;
+}
+
+extern "C" rlbm_status rlbm_batch_set_options(const rlbm_batch_options* opt) {
+  rlbm_batch_options o = {RLBM_BATCH_AUTO, 0u, 0u};
+  if (opt) o = *opt;
+  if (o.engine < RLBM_BATCH_AUTO || o.engine > RLBM_BATCH_PERSISTENT)
+    return fail(nullptr, RLBM_EINVAL, "batch options: unknown engine");
+  std::lock_guard<std::mutex> lock(g_batch_mutex);
+  g_bopt = o;
+  g_tuned.clear();
   return RLBM_OK;
 }

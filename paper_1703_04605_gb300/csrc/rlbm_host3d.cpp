@@ -275,6 +275,9 @@ rlbm_status rlbm3_create(const rlbm_stencil* st, double m, double tau, int Nx, i
     c->device_bytes += w64.size() * 12;
   }
   if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(unsigned));
+  // pageable uploads may return before their DMA lands: finish them before
+  // any kernel runs on a stream that is not ordered after the legacy stream
+  if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
   if (e != cudaSuccess) {
     release3(c.get());
     return fail3(nullptr, RLBM_ECUDA, std::string("upload: ") + cudaGetErrorString(e));

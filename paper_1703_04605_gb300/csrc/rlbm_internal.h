@@ -92,6 +92,18 @@ struct StepParams {
   PopTable<CT> pt;
 };
 
+// Per-lattice table of dR(Td) = R(mbar/(1 + Td)) - R(mbar) (T = 1 + Td in
+// units of T_R) for the final FP64 Newton step of the FP32 kernels' EOS: one
+// polynomial of degree DR_NC - 1 per slice of width 1/64 in Td, in the local
+// variable x = 64 Td - trunc(64 Td) (in [0, 1) for Td >= 0, (-1, 0] below),
+// which FP32 forms exactly.  Slices DR_NNEG - 1 - j cover Td in
+// (-(j+1)/64, -j/64], slices DR_NNEG + k cover [k/64, (k+1)/64); outside
+// (-DR_NNEG/64, DR_NPOS/64) the kernels use the R(zeta) table.
+constexpr int DR_NNEG = 48;      // T > 1/4 T_R
+constexpr int DR_NPOS = 192;     // T < 4 T_R
+constexpr int DR_NC = 7;         // degree 6
+constexpr int DR_NSEG = DR_NNEG + DR_NPOS;
+
 // Parameters of the stencil-specialised FP32 kernels (rlbm_fused.cuh).
 // A constant as the sum of two FP32 numbers (about 48 significant bits).
 struct HL {
@@ -118,13 +130,38 @@ struct FusedParams {
   HL gk[6][2];
   HL k0r, ykr;
   float exC[6];
+  double gm64[6][5];   // gm in FP64 (read-out kernel)
   const double* rt64;
   const float* rt32;
+  const double* dr64;  // DR_NSEG * DR_NC (the lattice's dR(Td) table)
   unsigned* err;
   // BF16 deviation storage only: per-site equilibrium reference coefficients,
   // six planes (one per group) of uint2 = 4 bf16 (alpha, beta_x, beta_y, q)
   const void* cin;
   void* cout;
+};
+
+// One lattice of a persistent batch launch (device memory; rlbm_persist.cuh).
+struct PersistLattice {
+  FusedParams p[2];       // step parameters for S_t in buf[0] / buf[1] (BF16 coefficient planes set)
+  const void* buf[2];     // population buffers
+  int nsite;              // Nx Ny
+  int ntiles;             // tiles of 128 spt sites
+};
+
+struct PersistParams {
+  const PersistLattice* lat;
+  const int2* units;      // the units of one step in claim order: (lattice, tile)
+  int nlat;
+  int units_per_step;
+  int nsteps;
+  int spt;                // sites per thread
+  unsigned spin_limit;    // polls of one wait before it gives up
+  unsigned wait_offset;   // added to every wait target (testing the timeout path only)
+  unsigned* ticket;       // claim counter, zero at launch
+  unsigned* abort;        // nonzero: stop claiming
+  unsigned* done;         // per lattice: units completed in this launch, zero at launch
+  const int* par0;        // per lattice: buffer holding S_t at launch (0 or 1)
 };
 
 // Device error bits (OR-ed into *err).
@@ -133,6 +170,7 @@ enum : unsigned {
   ERR_DENSITY = 2u,  // n <= 0 or non-finite
   ERR_EOS = 4u,      // e/n <= m or T <= 0 or non-finite
   ERR_ZETA = 8u,     // zeta outside the tabulated range
+  ERR_TIMEOUT = 16u, // a bounded device-side wait ran out (persistent batch)
 };
 
 // Fields read by the init kernel and written by the moments kernel.
@@ -193,6 +231,7 @@ struct FusedO3Params {
   HL ow[kMaxOrbO3][21];
   const double* rt64;
   const float* rt32;
+  const double* dr64;  // DR_NSEG * DR_NC (the lattice's dR(Td) table)
   unsigned* err;
 };
 

@@ -57,6 +57,33 @@ __device__ __forceinline__ double ratio64(double z, const double* __restrict__ t
   return r;
 }
 
+// dR(Td) = R(mbar/(1 + Td)) - R(mbar) from the lattice's table (layout in
+// rlbm_internal.h); false outside the tabulated range (or for NaN).  The
+// local variable is formed exactly in FP32: 64 Td is an exact scaling and
+// 64 Td - trunc(64 Td) an exact difference (the operands agree in sign and
+// are within a factor of two, or the truncation is zero).
+__device__ __forceinline__ bool dr_table64(float Td, const double* __restrict__ tab, double& dR) {
+  if (!(fabsf(Td) < 3.5f)) return false;
+  const float s = Td * 64.0f;
+  const float k = truncf(s);
+  const int ki = (int)k;
+  int idx;
+  if (Td >= 0.0f) {
+    if (ki >= DR_NPOS) return false;
+    idx = DR_NNEG + ki;
+  } else {
+    if (ki <= -DR_NNEG) return false;
+    idx = DR_NNEG - 1 + ki;
+  }
+  const double x = (double)(s - k);
+  const double* c = tab + idx * DR_NC;
+  double r = __ldg(c + DR_NC - 1);
+#pragma unroll
+  for (int q = DR_NC - 2; q >= 0; --q) r = fma(r, x, __ldg(c + q));
+  dR = r;
+  return true;
+}
+
 __device__ __forceinline__ float ratio32(float z, const float* __restrict__ tab, unsigned& fl) {
   if (!(z > 0.0f) || !isfinite(z)) {
     fl |= ERR_ZETA;
@@ -196,18 +223,13 @@ __device__ __forceinline__ Macro<double> solve_site_f64(const double* m, const S
 // (the FP32 Jacobian inverse is enough: the step squares an error that is
 // already ~1e-7).  EOS: FP32 Newton, then one FP64 Newton step with the FP64
 // R(zeta) table.  Returns FP64 macros; the caller rounds what it needs.
-__device__ __forceinline__ Macro<double> solve_site_mixed(const float* mpart, const double* mref,
-                                                         const SiteConsts& sc,
-                                                         const double* __restrict__ rt64,
-                                                         const float* __restrict__ rt32, unsigned& fl) {
-  // full moments: FP32 partial sums of the stored deviations + FP64 reference
-  double m[9];
+// m: the full moments in FP64.
+__device__ __forceinline__ Macro<double> solve_site_mixed_m(const double (&m)[9], const SiteConsts& sc,
+                                                           const double* __restrict__ rt64,
+                                                           const float* __restrict__ rt32, unsigned& fl) {
   float mf[9];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    m[k] = (double)mpart[k] + mref[k];
-    mf[k] = (float)m[k];
-  }
+  for (int k = 0; k < 9; ++k) mf[k] = (float)m[k];
   float vx, vy;
   float J11, J12, J21, J22;
   {
@@ -296,6 +318,17 @@ __device__ __forceinline__ Macro<double> solve_site_mixed(const float* mpart, co
   o.F = sc.mY * o.dR + 3.0 * (T - 1.0);
   o.G = mb * o.dR + 4.0 * (T - 1.0);
   return o;
+}
+
+// Full moments = FP32 partial sums of the stored deviations + FP64 reference.
+__device__ __forceinline__ Macro<double> solve_site_mixed(const float* mpart, const double* mref,
+                                                         const SiteConsts& sc,
+                                                         const double* __restrict__ rt64,
+                                                         const float* __restrict__ rt32, unsigned& fl) {
+  double m[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) m[k] = (double)mpart[k] + mref[k];
+  return solve_site_mixed_m(m, sc, rt64, rt32, fl);
 }
 
 // n times the ten projections b^(k) (App. B), in the order of PopTable::cj.

@@ -1058,4 +1058,66 @@ double ratio_eval_host(double z, int precision) {
   return r;
 }
 
+// dR(Td) per slice: Chebyshev interpolation at 16 nodes of the slice (R from
+// the FP64 table, differences in extended precision), truncated to degree
+// DR_NC - 1 and rewritten as monomials in the kernels' local variable x.
+std::vector<double> dr_table(double mbar) {
+  using ld = long double;
+  std::vector<double> tab((size_t)DR_NSEG * DR_NC, 0.0);
+  const ld Rm = (ld)ratio_eval_host(mbar, 64);
+  const int N = 16;
+  const ld pi = 3.141592653589793238462643383279502884L;
+  for (int seg = 0; seg < DR_NSEG; ++seg) {
+    // slice [a, a + 1/64) in Td, x = 64 (Td - c) with c the end nearest 0
+    const bool pos = seg >= DR_NNEG;
+    const int k = pos ? seg - DR_NNEG : -(DR_NNEG - 1 - seg);   // c = k/64 (k <= 0 below)
+    const ld c = (ld)k / 64;
+    // t in [-1, 1] -> x = (t + 1)/2 (pos) or (t - 1)/2 (neg)
+    ld f[N], ts[N];
+    for (int q = 0; q < N; ++q) {
+      ts[q] = std::cos(pi * ((ld)q + 0.5L) / N);
+      const ld x = pos ? (ts[q] + 1) / 2 : (ts[q] - 1) / 2;
+      const ld T = 1 + c + x / 64;
+      f[q] = (ld)ratio_eval_host((double)((ld)mbar / T), 64) - Rm;
+    }
+    ld ch[DR_NC];
+    for (int n = 0; n < DR_NC; ++n) {
+      ld acc = 0;
+      for (int q = 0; q < N; ++q) acc += f[q] * std::cos((ld)n * pi * ((ld)q + 0.5L) / N);
+      ch[n] = acc * 2 / N;
+    }
+    ch[0] /= 2;
+    // Chebyshev -> monomials in t
+    ld mt[DR_NC] = {}, Tm2[DR_NC] = {}, Tm1[DR_NC] = {}, Tn[DR_NC] = {};
+    Tm2[0] = 1;
+    mt[0] += ch[0];
+    Tm1[1] = 1;
+    mt[1] += ch[1];
+    for (int n = 2; n < DR_NC; ++n) {
+      for (int q = 0; q < DR_NC; ++q) Tn[q] = -Tm2[q] + (q > 0 ? 2 * Tm1[q - 1] : 0);
+      for (int q = 0; q < DR_NC; ++q) mt[q] += ch[n] * Tn[q];
+      for (int q = 0; q < DR_NC; ++q) {
+        Tm2[q] = Tm1[q];
+        Tm1[q] = Tn[q];
+      }
+    }
+    // t = 2x - 1 (pos) or 2x + 1 (neg): expand sum mt[n] t^n in x
+    const ld b = pos ? -1 : 1;
+    ld mx[DR_NC] = {};
+    ld pw[DR_NC] = {};   // coefficients of (2x + b)^n
+    pw[0] = 1;
+    for (int n = 0; n < DR_NC; ++n) {
+      for (int q = 0; q <= n; ++q) mx[q] += mt[n] * pw[q];
+      ld nx[DR_NC] = {};
+      for (int q = 0; q <= n && q + 1 < DR_NC; ++q) {
+        nx[q + 1] += 2 * pw[q];
+        nx[q] += b * pw[q];
+      }
+      for (int q = 0; q < DR_NC; ++q) pw[q] = nx[q];
+    }
+    for (int q = 0; q < DR_NC; ++q) tab[(size_t)seg * DR_NC + q] = (double)mx[q];
+  }
+  return tab;
+}
+
 }  // namespace rlbm

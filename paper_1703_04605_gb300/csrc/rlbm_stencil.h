@@ -143,6 +143,9 @@ void fill_pop_table(const StencilBuild& sb, int Nx, int Ny, PopTable<CT>* pt);
 const std::vector<double>& ratio_table64();
 const std::vector<float>& ratio_table32();
 double ratio_eval_host(double z, int precision);
+// The lattice's dR(Td) table (layout in rlbm_internal.h), fitted from the
+// FP64 R(zeta) table.
+std::vector<double> dr_table(double mbar);
 
 // Message returned by rlbm_last_error(NULL) (defined with the C ABI).
 void set_global_error(const std::string& msg);

@@ -85,10 +85,11 @@ class Lattice:
                 raise ValueError("device fields must be contiguous CUDA tensors of Nx*Ny float64")
         self._chk(self._lib.rlbm_init_device(self._ctx, *[C.c_void_p(t.data_ptr()) for t in (n, ux, uy, T)]))
 
-    def set_extended_sums(self, on=True):
+    def set_extended_sums(self, level=1):
         """FP32 storage on a compiled stencil: moment sums in extended
-        precision (rlbm_set_extended_sums)."""
-        self._chk(self._lib.rlbm_set_extended_sums(self._ctx, 1 if on else 0))
+        precision (rlbm_set_extended_sums; level 0 off, 1 mass and energy,
+        2 also momentum; True means 1)."""
+        self._chk(self._lib.rlbm_set_extended_sums(self._ctx, int(level)))
 
     def step(self, k=1):
         self._chk(self._lib.rlbm_step(self._ctx, int(k)))
@@ -171,6 +172,28 @@ def batch_step(lattices, k=1):
     L = A.load()
     arr = (C.c_void_p * len(lattices))(*[lat._ctx.value for lat in lattices])
     A.check(L.rlbm_batch_step(arr, len(lattices), int(k)))
+
+
+def set_batch_options(engine="auto", spin_limit=0, wait_offset=0):
+    """Process-wide batch engine choice ('auto', 'graph' or 'persistent') and
+    the persistent engine's bounded waits (rlbm_batch_set_options);
+    wait_offset > 0 makes every wait unmeetable (testing the timeout path)."""
+    codes = {"auto": A.BATCH_AUTO, "graph": A.BATCH_GRAPH, "persistent": A.BATCH_PERSISTENT}
+    if engine not in codes:
+        raise ValueError("engine must be one of %s" % ", ".join(sorted(codes)))
+    opt = A.BatchOptions(codes[engine], int(spin_limit), int(wait_offset))
+    A.check(A.load().rlbm_batch_set_options(C.byref(opt)))
+
+
+def batch_engine(lattices):
+    """The engine chosen for a batch: dict(engine='graph'|'persistent',
+    param=G or sites per thread, launches=per step (graph) or per call)."""
+    L = A.load()
+    arr = (C.c_void_p * len(lattices))(*[lat._ctx.value for lat in lattices])
+    out = [C.c_int(0) for _ in range(3)]
+    A.check(L.rlbm_batch_engine(arr, len(lattices), *[C.byref(o) for o in out]))
+    return dict(engine={A.BATCH_GRAPH: "graph", A.BATCH_PERSISTENT: "persistent"}.get(out[0].value, "?"),
+                param=out[1].value, launches=out[2].value)
 
 
 def batch_tuning(lattices):

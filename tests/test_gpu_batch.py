@@ -39,7 +39,7 @@ def test_batch_equals_single_lattices():
     assert sorted({b.info()["kernel"] for b in batch}) == [1, 2, 3, 4]
     batch_step(batch, 20)        # too few steps to tune: graphs of 8 and 2 steps
     batch_step(batch, 5)         # graph of 2 steps and one single step (parity flips)
-    batch_step(batch, 45)        # autotune (42 steps), then the chosen graph / single step
+    batch_step(batch, 45)        # below the 66 tuning steps: graphs of 8 and 2, one single step
     for lat in alone:
         lat.step(70)
     for b, a in zip(batch, alone):
@@ -92,7 +92,7 @@ def test_batch_third_order_equals_single_lattices():
     alone = [_make(s[:4], 300 + i, order=s[4]) for i, s in enumerate(specs)]
     assert [b.info()["kernel"] for b in batch[:5]] == [8, 9, 5, 6, 7]
     batch_step(batch, 9)         # graph of 8 steps and one single step
-    batch_step(batch, 45)        # autotune (42 steps), then a graph of 2 and one single step
+    batch_step(batch, 45)        # below the 66 tuning steps: graphs of 8 and 2, one single step
     for lat in alone:
         lat.step(54)
     for b, a in zip(batch, alone):
@@ -134,12 +134,18 @@ def test_batch_workload_sample():
             lat = Lattice(groups, mu, s["tau"], s["L"], s["L"], dtype="f32", v0=0.0)
             lat.init(f["n"], f["ux"], f["uy"], f["T"])
             group.append(lat)
-    batch_step(batch, 48)
-    from paper_1703_04605_gb300 import batch_tuning
+    batch_step(batch, 72)        # >= 66: the autotuner times both engines
+    from paper_1703_04605_gb300 import batch_engine, batch_tuning
+    eng = batch_engine(batch)
     tune = batch_tuning(batch)
-    assert tune["steps_per_graph"] in (2, 8, 32) and tune["launches_per_step"] == len(batch)
+    if eng["engine"] == "graph":
+        assert eng["param"] in (2, 8, 32) and eng["launches"] == len(batch)
+        assert tune["steps_per_graph"] == eng["param"] and tune["launches_per_step"] == len(batch)
+    else:
+        assert eng["engine"] == "persistent" and eng["param"] in (1, 2, 4) and 1 <= eng["launches"] <= 4
+        assert tune["steps_per_graph"] == 0 and tune["launches_per_step"] == 0
     for lat in alone:
-        lat.step(48)
+        lat.step(72)
     for b, a in zip(batch, alone):
         e = errors(b.moments(), a.moments())
         assert max(e.values()) < 1e-12, e

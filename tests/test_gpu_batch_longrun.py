@@ -1,0 +1,91 @@
+"""The batch workload's hardest lattices for its full length: FP32 storage
+through the batch path (rlbm_batch_step) against the FP64 path (parity-tested
+against the oracle) after 48 + 2000 steps, in n, T and u (u against the
+larger of the flow's largest FP64 velocity and its initial scale).
+
+These are the Sod tubes of the 256-lattice workload that drift furthest:
+massive (m/T_R 4.2 - 9.9), low viscosity (tau 0.61 - 0.81), y-invariant and
+sloshing in a periodic box, where every row and every period rounds alike.
+Measured (one GB300): plain FP32 moment sums reach 5e-4 in n and 2.8e-3 in
+u; extended sums (level 1) cut that about threefold; an experimental kernel
+with the whole site solve and equilibrium in FP64 still left 2e-5 - 6e-5,
+the floor of FP32 storage of f - r for these flows.  The tests pin what is
+delivered: the extended sums improve every one of these lattices and stay
+within the measured bounds; the 1e-5 target on them is recorded as an
+expected failure (strict: it would report if it started to pass).  The
+tubes are y-invariant, so they run on 8 identical rows (bit-identical to the
+full square lattice)."""
+import numpy as np
+import pytest
+
+from paper_1703_04605_gb300 import stencils, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+WORST = [32, 120, 250, 204]
+STEPS = 48 + 2000
+
+
+@pytest.fixture(scope="module")
+def results():
+    from paper_1703_04605_gb300 import Lattice, batch_step, build, set_batch_options
+    build.build()
+    set_batch_options("auto")
+    specs = W.batch_specs(256)
+    fields, ctxs = {}, {}
+    for i in WORST:
+        s = specs[i]
+        f = W.batch_fields(s)
+        fields[i] = {k: np.ascontiguousarray(v[:8]) for k, v in f.items()}
+    out = {}
+    for level in (0, 1):
+        lats = []
+        for i in WORST:
+            s = specs[i]
+            groups, mu = stencils.choose(s["m"])
+            lat = Lattice(groups, mu, s["tau"], s["L"], 8, dtype="f32", v0=0.0)
+            lat.set_extended_sums(level)
+            f = fields[i]
+            lat.init(f["n"], f["ux"], f["uy"], f["T"])
+            lats.append(lat)
+        batch_step(lats, STEPS)
+        out[level] = [lat.moments() for lat in lats]
+        for lat in lats:
+            lat.close()
+    ref = []
+    for i in WORST:
+        s = specs[i]
+        groups, mu = stencils.choose(s["m"])
+        with Lattice(groups, mu, s["tau"], s["L"], 8, dtype="f64", v0=0.0) as lat:
+            f = fields[i]
+            lat.init(f["n"], f["ux"], f["uy"], f["T"])
+            lat.step(STEPS)
+            ref.append(lat.moments())
+    errs = {}
+    for level in (0, 1):
+        errs[level] = []
+        for i, got, rm in zip(WORST, out[level], ref):
+            scale = max(np.abs(rm["ux"]).max(), np.abs(rm["uy"]).max(), 0.05)
+            errs[level].append(dict(
+                n=float(np.max(np.abs(got["n"] / rm["n"] - 1))), T=float(np.max(np.abs(got["T"] / rm["T"] - 1))),
+                u=float(max(np.abs(got["ux"] - rm["ux"]).max(), np.abs(got["uy"] - rm["uy"]).max()) / scale)))
+    return errs
+
+
+def test_extended_sums_improve_every_hard_lattice(results):
+    for e0, e1 in zip(results[0], results[1]):
+        assert max(e1.values()) < max(e0.values()), (e0, e1)
+
+
+def test_hard_lattices_within_measured_bounds(results):
+    for e in results[0]:
+        assert e["n"] < 1e-3 and e["T"] < 5e-4 and e["u"] < 5e-3, e
+    for e in results[1]:
+        assert e["n"] < 5e-4 and e["T"] < 2e-4 and e["u"] < 2e-3, e
+
+
+@pytest.mark.xfail(strict=True, reason="FP32 storage of f - r drifts past 1e-5 on these tubes after 2000 steps "
+                                        "(floor 2e-5 - 6e-5 even with an all-FP64 site solve)")
+def test_hard_lattices_meet_fp32_target(results):
+    for e in results[1]:
+        assert max(e.values()) <= 1e-5, e

@@ -66,9 +66,11 @@ def test_riemann_crop_against_oracle(m):
 
 
 def test_sound_pulse_crop_against_oracle():
+    """A 5 % density pulse (velocities up to ~3 % of c): the FP64 round-off of
+    u stays well below 1e-12 of the flow's velocity scale."""
     st = _stencil(1.0)
-    f = W.sound_pulse(128, 8, amp=1e-2, sigma=8.0)
-    _check(st, 0.55, f, 20, u_scale=1e-3)
+    f = W.sound_pulse(128, 8, amp=5e-2, sigma=8.0)
+    _check(st, 0.55, f, 20, u_scale=1e-2)
 
 
 def test_taylor_dispersion_crop_against_oracle():
