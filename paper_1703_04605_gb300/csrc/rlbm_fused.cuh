@@ -553,6 +553,41 @@ __device__ __forceinline__ SplitSite split_solve(const P& p, const float (&M)[9]
   return o;
 }
 
+// Group coefficients c[g] of f^eq - r (the polynomial mult (c0 + c1 n_x +
+// c2 n_y + c3 n_x^2 + c4 n_y^2 + c5 n_x n_y) of each group) from the split
+// site state: the App. B projections in deviation form, without their
+// normalisations (those and the App. A constants are folded into p.gf).
+__device__ __forceinline__ void fused_coeffs(const FusedParams& p, const SplitSite& ss, float (&c)[6][6]) {
+  const float dg = ss.dg, Ux = ss.Ux, Uy = ss.Uy, n = ss.n, nd = ss.nd;
+  const float Td = ss.Td, dR = ss.dR, R = ss.R, T = ss.T;
+  const float mr32 = fmaf(p.mb, R, 4.0f * T);          // mbar K3/K2(zeta)
+  const float r0 = fmaf(p.nr.hi, dR, fmaf(p.nr.lo, dR, nd * R));   // n R - n_r R_r
+  const float r1 = n * (dg - p.k21 * dR);
+  const float r2 = n * Ux, r3 = n * Uy;
+  const float F = fmaf(p.mY, dR, 3.0f * Td);
+  const float G = fmaf(p.mb, dR, 4.0f * Td);
+  const float r4 = n * (F + dg * fmaf(2.0f, mr32, p.cb00_1) + dg * dg * mr32);
+  const float h = fmaf(mr32, dg, G);
+  const float r5 = n * h * Ux, r6 = n * h * Uy;
+  const float nm = n * mr32;
+  const float r7 = nm * Uy * Uy, r8 = nm * (Uy * Uy - 2.0f * Ux * Ux), r9 = nm * Ux * Uy;
+#pragma unroll
+  for (int g = 0; g < 6; ++g) {
+    const HL* a = p.gf[g];
+    float al = hl(a[0], r0);
+    al = hl_fma(a[1], r1, al);
+    al = hl_fma(a[2], r4, al);
+    al = hl_fma(a[3], r7, al);
+    al = hl_fma(a[4], r8, al);
+    c[g][0] = al;
+    c[g][1] = hl_fma(a[5], r2, hl(a[6], r5));
+    c[g][2] = hl_fma(a[5], r3, hl(a[6], r6));
+    c[g][3] = hl(a[7], r7 - r8);
+    c[g][4] = hl(a[8], r7);
+    c[g][5] = hl(a[9], r9);
+  }
+}
+
 // One site update (see the header comment); p describes the lattice.
 template <class Def, bool BF, int EXL = 0, bool CG = false>
 __device__ __forceinline__ void fused_site(const FusedParams& p, const void* __restrict__ fin,
@@ -609,36 +644,9 @@ __device__ __forceinline__ void fused_site(const FusedParams& p, const void* __r
       }
       ss = split_solve(p, M, fl);
     }
-    const float dg = ss.dg, U0 = ss.U0, Ux = ss.Ux, Uy = ss.Uy, n = ss.n, nd = ss.nd;
-    const float Td = ss.Td, dR = ss.dR, R = ss.R, T = ss.T;
-    // projections without their normalisations (those live in p.gf)
-    const float mr32 = fmaf(p.mb, R, 4.0f * T);          // mbar K3/K2(zeta)
-    const float r0 = fmaf(p.nr.hi, dR, fmaf(p.nr.lo, dR, nd * R));   // n R - n_r R_r
-    const float r1 = n * (dg - p.k21 * dR);
-    const float r2 = n * Ux, r3 = n * Uy;
-    const float F = fmaf(p.mY, dR, 3.0f * Td);
-    const float G = fmaf(p.mb, dR, 4.0f * Td);
-    const float r4 = n * (F + dg * fmaf(2.0f, mr32, p.cb00_1) + dg * dg * mr32);
-    const float h = fmaf(mr32, dg, G);
-    const float r5 = n * h * Ux, r6 = n * h * Uy;
-    const float nm = n * mr32;
-    const float r7 = nm * Uy * Uy, r8 = nm * (Uy * Uy - 2.0f * Ux * Ux), r9 = nm * Ux * Uy;
+    const float U0 = ss.U0, Ux = ss.Ux, Uy = ss.Uy;
     float c[6][6];
-#pragma unroll
-    for (int g = 0; g < 6; ++g) {
-      const HL* a = p.gf[g];
-      float al = hl(a[0], r0);
-      al = hl_fma(a[1], r1, al);
-      al = hl_fma(a[2], r4, al);
-      al = hl_fma(a[3], r7, al);
-      al = hl_fma(a[4], r8, al);
-      c[g][0] = al;
-      c[g][1] = hl_fma(a[5], r2, hl(a[6], r5));
-      c[g][2] = hl_fma(a[5], r3, hl(a[6], r6));
-      c[g][3] = hl(a[7], r7 - r8);
-      c[g][4] = hl(a[8], r7);
-      c[g][5] = hl(a[9], r9);
-    }
+    fused_coeffs(p, ss, c);
     const float a0 = U0 * p.inv_tau, ax = p.v0 * Ux * p.inv_tau, ay = p.v0 * Uy * p.inv_tau;
     const long long here = (long long)y * p.pitch + x;
     uint2 cq[6];
@@ -846,10 +854,10 @@ __global__ void __launch_bounds__(128) bf16_moments(const __grid_constant__ Step
 }
 
 // ---------------------------------------------------- FP32 init and read-out
-// Init of FP32 storage on a compiled stencil: per site the FP64 group
-// coefficients of f^eq - r, then per population its group polynomial in
-// FP32 (as the step kernel evaluates it), written to S_0 at the site and to
-// S_{-1} at x - n_i (see init_kernel).
+// Init of FP32 storage on a compiled stencil: per site the step kernel's own
+// equilibrium of the given fields (split site state with the FP64 dR(Td)
+// table, FP32 projections and group coefficients, FP32 group polynomials),
+// written to S_0 at the site and to S_{-1} at x - n_i (see init_kernel).
 template <class Def, int... Is>
 __device__ __forceinline__ void f32_init_pops(std::integer_sequence<int, Is...>, const float (&c)[6][6],
                                               float* __restrict__ cur, float* __restrict__ prev,
@@ -887,13 +895,26 @@ __global__ void __launch_bounds__(128) f32_init_kernel(const __grid_constant__ F
     if (!(ux * ux + uy * uy < 1.0)) fl |= ERR_LANDAU;
     if (!(n > 0.0)) fl |= ERR_DENSITY;
     if (!(T > 0.0)) fl |= ERR_EOS;
-    double c64[6][6];
-    fp64_group_coeffs(p, sc, n, ux, uy, T, c64, fl);
+    // the split site state of the fields, as the step kernel holds it
+    SplitSite ss;
+    const float vx = (float)ux, vy = (float)uy;
+    const float v2 = vx * vx + vy * vy;
+    const float sq = sqrtf(fmaxf(1.0f - v2, 0.0f));
+    ss.dg = __fdividef(v2, sq * (1.0f + sq));
+    ss.U0 = 1.0f + ss.dg;
+    ss.Ux = ss.U0 * vx;
+    ss.Uy = ss.U0 * vy;
+    ss.nd = (float)(n - p.nr64);
+    ss.n = (float)n;
+    ss.Td = (float)(T - 1.0);
+    ss.T = (float)T;
+    double dR64;
+    if (!dr_table64(ss.Td, p.dr64, dR64)) dR64 = dr_from_zeta(ss.Td, p.mb64, p.Rr64, p.rt64, fl);
+    ss.dR = (float)dR64;
+    ss.R = p.Rr.hi + (p.Rr.lo + ss.dR);
     float c[6][6];
-#pragma unroll
-    for (int g = 0; g < 6; ++g)
-#pragma unroll
-      for (int k = 0; k < 6; ++k) c[g][k] = (float)c64[g][k];
+    fused_coeffs(p, ss, c);
+    (void)sc;
     f32_init_pops<Def>(std::make_integer_sequence<int, Def::Q>{}, c, cur, prev, p.plane, p.pitch, x, y, p.Nx,
                        p.Ny);
   }

@@ -193,22 +193,17 @@ __global__ void __launch_bounds__(128, 4) fused3d_kernel(const __grid_constant__
       Td -= step;
       if (fabsf(step) < 3e-8f) break;
     }
-    // ... and one FP64 Newton step with the FP64 R(zeta) table
+    // ... and one FP64 Newton step: dR(Td) from the lattice's FP64 table in
+    // Td, else from the R(zeta) table
     float dR;
     {
-      const float Tf = 1.0f + Td;
-      const double T64 = 1.0 + (double)Td;
-      double iT = (double)__fdividef(1.0f, Tf);
-      iT = fma(iT, fma(-T64, iT, 1.0), iT);
-      const double z64 = p.mb64 * iT;
-      const double dR64 = ratio64(z64, p.rt64, fl) - p.Rr64;
+      double dR64;
+      if (!dr_table64(Td, p.dr64, dR64)) dR64 = dr_from_zeta(Td, p.mb64, p.Rr64, p.rt64, fl);
       const double g64 = fma(3.0, (double)Td, fma(p.mb64, dR64, -(double)yd));
       const float step = __fdividef((float)g64, slope);
       Td -= step;
-      const float R = p.Rr.hi + (p.Rr.lo + (float)dR64);
-      const float zf = (float)z64;
-      const float dRdz = R * R + 3.0f * __fdividef(R, zf) - 1.0f;
-      dR = fmaf(dRdz, zf * step / Tf, (float)dR64);     // R at the corrected T (first order)
+      // R at the corrected T to first order: d(dR)/dTd = (c_v - 3)/m, c_v = slope
+      dR = fmaf((slope - 3.0f) * __fdividef(1.0f, p.mb), -step, (float)dR64);
     }
     const float R = p.Rr.hi + (p.Rr.lo + dR);
     const float T = 1.0f + Td;

@@ -31,6 +31,7 @@ struct rlbm_ctx3 {
   unsigned* d_err = nullptr;
   double* d_rt64 = nullptr;
   float* d_rt32 = nullptr;
+  double* d_dr64 = nullptr;      // the lattice's dR(Td) table (compiled kernel's EOS step)
   int* d_shift = nullptr;
   long long* d_off = nullptr;
   double* d_tab64 = nullptr;
@@ -70,7 +71,8 @@ rlbm_status cuda_fail3(rlbm_ctx3* c, cudaError_t e, const char* where) {
 
 void release3(rlbm_ctx3* c) {
   if (c->buf[0] || c->buf[1]) cudaStreamSynchronize(c->stream);
-  for (void* p : {c->buf[0], c->buf[1], (void*)c->d_err, (void*)c->d_rt64, (void*)c->d_rt32, (void*)c->d_shift, (void*)c->d_off,
+  for (void* p : {c->buf[0], c->buf[1], (void*)c->d_err, (void*)c->d_rt64, (void*)c->d_rt32, (void*)c->d_dr64,
+                  (void*)c->d_shift, (void*)c->d_off,
                   (void*)c->d_tab64, (void*)c->d_tab32, (void*)c->d_fields, (void*)c->d_out, (void*)c->d_w64,
                   (void*)c->d_w32})
     c->mem.put(p);
@@ -140,6 +142,7 @@ void fill_fused3(rlbm_ctx3* c, double nref) {
   }
   f.rt64 = c->d_rt64;
   f.rt32 = c->d_rt32;
+  f.dr64 = c->d_dr64;
   f.err = c->d_err;
 }
 
@@ -235,10 +238,12 @@ rlbm_status rlbm3_create(const rlbm_stencil* st, double m, double tau, int Nx, i
   const size_t nsite = (size_t)Nx * Ny * Nz;
   const auto& r64 = ratio_table64();
   const auto& r32 = ratio_table32();
+  const std::vector<double> drt = dr_table(m);
   bool ok = c->mem.get(&c->buf[0], fbytes) == cudaSuccess && c->mem.get(&c->buf[1], fbytes) == cudaSuccess &&
             c->mem.get(&c->d_err, sizeof(unsigned)) == cudaSuccess &&
             c->mem.get(&c->d_rt64, r64.size() * sizeof(double)) == cudaSuccess &&
             c->mem.get(&c->d_rt32, r32.size() * sizeof(float)) == cudaSuccess &&
+            c->mem.get(&c->d_dr64, drt.size() * sizeof(double)) == cudaSuccess &&
             c->mem.get(&c->d_shift, sh.size() * sizeof(int)) == cudaSuccess &&
             c->mem.get(&c->d_off, off.size() * sizeof(long long)) == cudaSuccess &&
             c->mem.get(&c->d_tab64, t64.size() * sizeof(double)) == cudaSuccess &&
@@ -261,10 +266,11 @@ rlbm_status rlbm3_create(const rlbm_stencil* st, double m, double tau, int Nx, i
     release3(c.get());
     return fail3(nullptr, RLBM_ENOMEM, "device allocation failed");
   }
-  c->device_bytes = 2 * fbytes + r64.size() * 8 + r32.size() * 4 + sh.size() * 4 + off.size() * 8 + t64.size() * 12 +
+  c->device_bytes = 2 * fbytes + r64.size() * 8 + r32.size() * 4 + drt.size() * 8 + sh.size() * 4 + off.size() * 8 + t64.size() * 12 +
                     5 * nsite * 8 + 4;
   e = cudaMemcpy(c->d_rt64, r64.data(), r64.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_rt32, r32.data(), r32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_dr64, drt.data(), drt.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_shift, sh.data(), sh.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_off, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_tab64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice);

@@ -299,6 +299,7 @@ struct Fused3Params {
   HL gf[6][10];
   const double* rt64;
   const float* rt32;
+  const double* dr64;  // DR_NSEG * DR_NC (the lattice's dR(Td) table)
   unsigned* err;
 };
 

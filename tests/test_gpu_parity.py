@@ -128,7 +128,7 @@ def test_f32_generic_kernel_tiny_lattice():
     assert info["kernel"] == 0
     ref = run_oracle(st, 0.8, f, 20)
     e = errors(got, ref)
-    assert e["n"] < 1e-5 and e["T"] < 1e-5, e
+    assert max(e.values()) < TOL["f32"], e
 
 
 @pytest.mark.parametrize("name", ["M1", "G16", "E5", "S2"])
@@ -161,7 +161,7 @@ def test_bf16dev_blast_crop():
     got, _ = run_gpu(st, 0.7, f, "bf16dev", 60)
     ref = run_oracle(st, 0.7, f, 60)
     e = errors(got, ref)
-    assert e["n"] < TOL["bf16dev"] and e["T"] < TOL["bf16dev"] and e["u"] < 1e-2, e
+    assert max(e.values()) < TOL["bf16dev"], e
 
 
 def test_bf16dev_unsupported_stencil_is_an_error():
