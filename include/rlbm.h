@@ -234,7 +234,10 @@ rlbm_status rlbm_set_allocator(rlbm_alloc_fn alloc, rlbm_free_fn free_fn, void* 
  * of the persistent engine at each spt in {1, 2, 4} (those steps count
  * towards nsteps), and caches the fastest; rlbm_batch_engine reports it.
  * Graphs and persistent plans are cached per batch; rlbm_init,
- * rlbm_set_extended_sums or rlbm_destroy of a member drops them.
+ * rlbm_set_extended_sums or rlbm_destroy of a member drops them.  A
+ * persistent plan holds a few small device descriptors of its own (about
+ * 3 KB per lattice, taken with cudaMalloc, not from rlbm_set_allocator's
+ * allocator, which serves the contexts' buffers).
  * Requirements: every context initialised, a compiled stencil
  * (rlbm_info.kernel != 0) with FP32 or BF16-deviation storage (FP32 only at
  * third order; second- and third-order contexts may be mixed), all on the
