@@ -229,10 +229,12 @@ rlbm_status rlbm_set_allocator(rlbm_alloc_fn alloc, rlbm_free_fn free_fn, void* 
  *    next synchronising call returns RLBM_ETIMEOUT and their state is
  *    undefined until rlbm_init.
  * With the engine left to the autotuner (rlbm_batch_set_options), the first
- * call for a batch with nsteps >= 66 times one replay of each graph length G
+ * call for a batch with enough steps times one replay of each graph length G
  * in {2, 8, 32} (42 steps) and, on a batch of second-order lattices, 8 steps
- * of the persistent engine at each spt in {1, 2, 4} (those steps count
- * towards nsteps), and caches the fastest; rlbm_batch_engine reports it.
+ * of the persistent engine at each spt in {1, 2, 4} (24 more steps; so
+ * nsteps >= 66, or >= 42 with third-order members), those steps counting
+ * towards nsteps, and caches the fastest; rlbm_batch_engine reports it.
+ * Shorter calls run the graph engine untuned.
  * Graphs and persistent plans are cached per batch; rlbm_init,
  * rlbm_set_extended_sums or rlbm_destroy of a member drops them.  A
  * persistent plan holds a few small device descriptors of its own (about
