@@ -45,6 +45,15 @@
 // reader rebuilds f_i - r_i = d_i + ref_i(source site) from the same stored
 // numbers, so encoding and decoding agree exactly; the rest of the step is the
 // FP32 path above.
+//
+// Instruction economy (the BF16 kernel is issue-bound, the FP32 kernel
+// close to it): element indices are 32-bit (a plane holds fewer than 2^32
+// elements); a BF16 site whose sources need no wrapping pulls through fixed
+// per-population offsets from its own element; the bfloat16 factors of the
+// reference polynomial enter the sm_100+ mixed-precision FMA straight from
+// their packed words; and the moment sums run as packed FP32 pairs
+// (fma.rn.f32x2), each lane doing the scalar code's operations, so the
+// results are those of the scalar forms bit for bit.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -76,13 +85,45 @@ __device__ __forceinline__ unsigned bf_pack(float lo, float hi) {
          ((unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
 }
 
-// reference of a population from its group's packed coefficients
+// bfloat16 bits of a small integer (|k| < 256, exact in bfloat16)
+__host__ __device__ constexpr unsigned short bf_int_bits(int k) {
+  const unsigned a = k < 0 ? -k : k;
+  int e = 0;
+  while ((a >> (e + 1)) != 0) ++e;
+  return (unsigned short)(((k < 0) ? 0x8000u : 0u) | ((unsigned)(e + 127) << 7) | ((a << (7 - e)) & 0x7fu));
+}
+
+// acc + K b with b the bfloat16 in the high (HI) or low half of w: the
+// mixed-precision FMA of sm_100+ takes both bfloat16 factors straight from
+// the packed word (no unpacking); K b is exact, so the result is the FP32
+// fmaf(K, b, acc) bit for bit
+template <int K, bool HI>
+__device__ __forceinline__ float fma_kbf(unsigned w, float acc) {
+  float r;
+  if constexpr (HI)
+    asm("{ .reg .b16 lo, hi, k; mov.b32 {lo, hi}, %1; mov.b16 k, %2; fma.rn.f32.bf16 %0, k, hi, %3; }"
+        : "=f"(r) : "r"(w), "n"((int)bf_int_bits(K)), "f"(acc));
+  else
+    asm("{ .reg .b16 lo, hi, k; mov.b32 {lo, hi}, %1; mov.b16 k, %2; fma.rn.f32.bf16 %0, k, lo, %3; }"
+        : "=f"(r) : "r"(w), "n"((int)bf_int_bits(K)), "f"(acc));
+  return r;
+}
+
+// bfloat16 h + FP32 acc, one rounding (the FP32 sum of the widened h)
+__device__ __forceinline__ float add_bf(unsigned short h, float acc) {
+  float r;
+  asm("add.rn.f32.bf16 %0, %1, %2;" : "=f"(r) : "h"(h), "f"(acc));
+  return r;
+}
+
+// reference of a population from its group's packed coefficients:
+// mult (alpha + n_x beta_x + n_y beta_y + |n|^2 q), in this order
 template <int nx, int ny, int mult>
 __device__ __forceinline__ float bf_ref(uint2 c) {
   float r = bf_lo(c.x);
-  if constexpr (nx != 0) r = fmaf((float)nx, bf_hi(c.x), r);
-  if constexpr (ny != 0) r = fmaf((float)ny, bf_lo(c.y), r);
-  if constexpr (nx * nx + ny * ny != 0) r = fmaf((float)(nx * nx + ny * ny), bf_hi(c.y), r);
+  if constexpr (nx != 0) r = fma_kbf<nx, true>(c.x, r);
+  if constexpr (ny != 0) r = fma_kbf<ny, false>(c.y, r);
+  if constexpr (nx * nx + ny * ny != 0) r = fma_kbf<nx * nx + ny * ny, true>(c.y, r);
   if constexpr (mult != 1) r *= (float)mult;
   return r;
 }
@@ -95,6 +136,11 @@ __device__ __forceinline__ T fused_ld(const T* p) {
   else return __ldg(p);
 }
 
+// Element indices: a plane holds fewer than 2^32 elements (checked when the
+// lattice is created), so the index of a pulled value, y_s pitch + x_s, and
+// a plane offset I plane are formed in 32-bit arithmetic; the address is then
+// one wide multiply-add from the base, where 64-bit index arithmetic costs
+// several integer instructions a population.
 template <class Def, bool BF, int I, bool CG = false>
 __device__ __forceinline__ void fused_load(float (&d)[Def::Q], const void* __restrict__ fin,
                                            const uint2* __restrict__ cin, long long plane, long long pitch,
@@ -102,15 +148,28 @@ __device__ __forceinline__ void fused_load(float (&d)[Def::Q], const void* __res
   constexpr int DX = Def::F.nx[I], DY = Def::F.ny[I];
   const int xs = wrap_c<DX>(x, Nx);
   const int ys = wrap_c<DY>(y, Ny);
-  const long long idx = (long long)ys * pitch + xs;
+  const unsigned idx = (unsigned)ys * (unsigned)pitch + (unsigned)xs;
+  const size_t pl = (unsigned)plane;
   if constexpr (BF) {
     constexpr int g = Def::F.grp[I], mult = Def::F.mult[I];
-    const unsigned short h = fused_ld<CG>(static_cast<const unsigned short*>(fin) + (long long)I * plane + idx);
-    const uint2 c = fused_ld<CG>(cin + (long long)g * plane + idx);
-    d[I] = __uint_as_float((unsigned)h << 16) + bf_ref<DX, DY, mult>(c);
+    const unsigned short h = fused_ld<CG>(static_cast<const unsigned short*>(fin) + idx + pl * I);
+    const uint2 c = fused_ld<CG>(cin + idx + pl * g);
+    d[I] = add_bf(h, bf_ref<DX, DY, mult>(c));
   } else {
-    d[I] = fused_ld<CG>(static_cast<const float*>(fin) + (long long)I * plane + idx);
+    d[I] = fused_ld<CG>(static_cast<const float*>(fin) + idx + pl * I);
   }
+}
+
+// The same pull for a site whose sources need no wrapping (BF16 storage):
+// the value and its coefficient word sit at fixed offsets from the site's
+// own element (fh, ch), which takes the index arithmetic off the path.
+template <class Def, int I, bool CG = false>
+__device__ __forceinline__ void fused_load_inner(float (&d)[Def::Q], const unsigned short* __restrict__ fh,
+                                                 const uint2* __restrict__ ch, const FusedParams& p) {
+  constexpr int DX = Def::F.nx[I], DY = Def::F.ny[I], mult = Def::F.mult[I];
+  const unsigned short h = fused_ld<CG>(fh + p.doff[I]);
+  const uint2 c = fused_ld<CG>(ch + p.dcoff[I]);
+  d[I] = add_bf(h, bf_ref<DX, DY, mult>(c));
 }
 
 // Group sums of one reflection orbit (members (+,+), (-,+), (+,-), (-,-) of
@@ -311,12 +370,12 @@ __device__ __forceinline__ void fused_relax(const float (&d)[Def::Q], float e, c
   if constexpr (ny != 0) om = fmaf(-(float)ny, ay, om);
   const float v = d[I];
   const float vn = fmaf(om, e - v, v);
+  const size_t pl = (unsigned)plane;
   if constexpr (BF) {
     const float dv = vn - bf_ref<nx, ny, mult>(cq[g]);
-    __stcs(static_cast<unsigned short*>(out) + (long long)I * plane,
-           __bfloat16_as_ushort(__float2bfloat16_rn(dv)));
+    __stcs(static_cast<unsigned short*>(out) + pl * I, __bfloat16_as_ushort(__float2bfloat16_rn(dv)));
   } else {
-    __stcs(static_cast<float*>(out) + (long long)I * plane, vn);
+    __stcs(static_cast<float*>(out) + pl * I, vn);
   }
 }
 
@@ -352,6 +411,14 @@ __device__ __forceinline__ void fused_collide_orbit(const float (&d)[Def::Q], co
     fused_relax<Def, BF, i2>(d, EM + XM, cq, a0, ax_, ay_, out, plane);
     fused_relax<Def, BF, i3>(d, EP - XP, cq, a0, ax_, ay_, out, plane);
   }
+}
+
+template <class Def, bool CG = false, int... Is>
+__device__ __forceinline__ void fused_load_inner_all(std::integer_sequence<int, Is...>, float (&d)[Def::Q],
+                                                     const unsigned short* __restrict__ fh,
+                                                     const uint2* __restrict__ ch, const FusedParams& p) {
+  static_assert(Def::Q <= kMaxQ2, "offset tables hold kMaxQ2 populations");
+  (fused_load_inner<Def, Is, CG>(d, fh, ch, p), ...);
 }
 
 template <class Def, bool BF, bool CG = false, int... Is>
@@ -599,8 +666,19 @@ __device__ __forceinline__ void fused_site(const FusedParams& p, const void* __r
     int x, y;
     site_of(site, p.Nx, x, y);
     float d[Q];
-    fused_load_all<Def, BF, CG>(Seq{}, d, fin, static_cast<const uint2*>(p.cin), p.plane, p.pitch, x, y, p.Nx,
-                                p.Ny);
+    const unsigned here = (unsigned)y * (unsigned)p.pitch + (unsigned)x;
+    if constexpr (BF && Def::Q <= 64) {
+      constexpr int H = Def::halo;
+      if ((unsigned)(x - H) < (unsigned)p.inner_nx && (unsigned)(y - H) < (unsigned)p.inner_ny)
+        fused_load_inner_all<Def, CG>(Seq{}, d, static_cast<const unsigned short*>(fin) + here,
+                                      static_cast<const uint2*>(p.cin) + here, p);
+      else
+        fused_load_all<Def, true, CG>(Seq{}, d, fin, static_cast<const uint2*>(p.cin), p.plane, p.pitch, x, y,
+                                      p.Nx, p.Ny);
+    } else {
+      fused_load_all<Def, BF, CG>(Seq{}, d, fin, static_cast<const uint2*>(p.cin), p.plane, p.pitch, x, y, p.Nx,
+                                  p.Ny);
+    }
     using Orb = std::make_integer_sequence<int, Def::O.K>;
     // deviation moments N0 Nx Ny T00 T0x T0y Txx Txy Tyy (reference excluded)
     float M[9];
@@ -628,35 +706,43 @@ __device__ __forceinline__ void fused_site(const FusedParams& p, const void* __r
         for (int k = 0; k < 6; ++k) s[g][k] = 0.0f;
       if constexpr (fused_use_orbits<Def, BF>()) fused_acc_all<Def>(Orb{}, d, s);
       else fused_acc_pop_all<Def>(Seq{}, d, s);
-#pragma unroll
-      for (int k = 0; k < 9; ++k) M[k] = 0.0f;
+      // M = sum_g gm[g] s[g] in hi/lo form; eight of the nine sums as four
+      // packed pairs (each lane the same two fmaf as the scalar form)
+      float2 A = make_float2(0.0f, 0.0f), B = A, C = A, D = A;
+      M[8] = 0.0f;
 #pragma unroll
       for (int g = 0; g < 6; ++g) {
-        M[0] = hl_fma(p.gm[g][0], s[g][0], M[0]);
-        M[3] = hl_fma(p.gm[g][1], s[g][0], M[3]);
-        M[1] = hl_fma(p.gm[g][2], s[g][1], M[1]);
-        M[2] = hl_fma(p.gm[g][2], s[g][2], M[2]);
-        M[4] = hl_fma(p.gm[g][3], s[g][1], M[4]);
-        M[5] = hl_fma(p.gm[g][3], s[g][2], M[5]);
-        M[6] = hl_fma(p.gm[g][4], s[g][3], M[6]);
-        M[7] = hl_fma(p.gm[g][4], s[g][4], M[7]);
-        M[8] = hl_fma(p.gm[g][4], s[g][5], M[8]);
+        const float2 s00 = make_float2(s[g][0], s[g][0]), s12 = make_float2(s[g][1], s[g][2]);
+        const float2 s34 = make_float2(s[g][3], s[g][4]);
+        A = __ffma2_rn(p.gm2[g][0], s00, __ffma2_rn(p.gm2[g][1], s00, A));   // N0, T00
+        B = __ffma2_rn(p.gm2[g][2], s12, __ffma2_rn(p.gm2[g][3], s12, B));   // Nx, Ny
+        C = __ffma2_rn(p.gm2[g][4], s12, __ffma2_rn(p.gm2[g][5], s12, C));   // T0x, T0y
+        D = __ffma2_rn(p.gm2[g][6], s34, __ffma2_rn(p.gm2[g][7], s34, D));   // Txx, Txy
+        M[8] = hl_fma(p.gm[g][4], s[g][5], M[8]);                            // Tyy
       }
+      M[0] = A.x;
+      M[3] = A.y;
+      M[1] = B.x;
+      M[2] = B.y;
+      M[4] = C.x;
+      M[5] = C.y;
+      M[6] = D.x;
+      M[7] = D.y;
       ss = split_solve(p, M, fl);
     }
     const float U0 = ss.U0, Ux = ss.Ux, Uy = ss.Uy;
     float c[6][6];
     fused_coeffs(p, ss, c);
     const float a0 = U0 * p.inv_tau, ax = p.v0 * Ux * p.inv_tau, ay = p.v0 * Uy * p.inv_tau;
-    const long long here = (long long)y * p.pitch + x;
     uint2 cq[6];
     if constexpr (BF) {
       // this site's reference coefficients, rounded once and stored for the readers
+      const size_t pl = (unsigned)p.plane;
 #pragma unroll
       for (int g = 0; g < 6; ++g) {
         cq[g].x = bf_pack(c[g][0], c[g][1]);
         cq[g].y = bf_pack(c[g][2], 0.5f * (c[g][3] + c[g][4]));
-        __stcs(static_cast<uint2*>(p.cout) + (long long)g * p.plane + here, cq[g]);
+        __stcs(static_cast<uint2*>(p.cout) + here + pl * g, cq[g]);
       }
     }
     void* out = BF ? static_cast<void*>(static_cast<unsigned short*>(fout) + here)

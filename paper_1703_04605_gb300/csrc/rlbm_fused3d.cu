@@ -17,11 +17,13 @@
 namespace rlbm {
 namespace {
 
+// element index of the pulled value in its plane (32-bit: a plane holds
+// fewer than 2^32 elements, checked when the lattice is created)
 template <class D, int I>
-__device__ __forceinline__ long long f3_src(const Fused3Params& p, int x, int y, int z) {
+__device__ __forceinline__ unsigned f3_src(const Fused3Params& p, int x, int y, int z) {
   constexpr int DX = D::U.nx[I], DY = D::U.ny[I], DZ = D::U.nz[I];
-  return (long long)wrap_c<DZ>(z, p.Nz) * p.zstride + (long long)wrap_c<DY>(y, p.Ny) * p.pitch +
-         wrap_c<DX>(x, p.Nx);
+  return (unsigned)wrap_c<DZ>(z, p.Nz) * (unsigned)p.zstride + (unsigned)wrap_c<DY>(y, p.Ny) * (unsigned)p.pitch +
+         (unsigned)wrap_c<DX>(x, p.Nx);
 }
 
 // group sums: 1, n_x, n_y, n_z, n_x^2, n_y^2, n_z^2, n_x n_y, n_x n_z, n_y n_z
@@ -29,7 +31,7 @@ template <class D, int I>
 __device__ __forceinline__ void f3_acc(const Fused3Params& p, const float* __restrict__ fin, int x, int y, int z,
                                        float (&s)[6][10], float* __restrict__ keep) {
   constexpr int g = D::U.grp[I], nx = D::U.nx[I], ny = D::U.ny[I], nz = D::U.nz[I];
-  const float v = __ldg(fin + (long long)I * p.plane + f3_src<D, I>(p, x, y, z));
+  const float v = __ldg(fin + f3_src<D, I>(p, x, y, z) + (size_t)(unsigned)p.plane * I);
   keep[I * 128] = v;
   s[g][0] += v;
   if constexpr (nx != 0) s[g][1] = fmaf((float)nx, v, s[g][1]);
@@ -64,7 +66,7 @@ __device__ __forceinline__ void f3_collide(const Fused3Params& p, const float* _
   if constexpr (nx != 0) om = fmaf(-(float)nx, ax, om);
   if constexpr (ny != 0) om = fmaf(-(float)ny, ay, om);
   if constexpr (nz != 0) om = fmaf(-(float)nz, az, om);
-  __stcs(out + (long long)I * p.plane, fmaf(om, e - v, v));
+  __stcs(out + (size_t)(unsigned)p.plane * I, fmaf(om, e - v, v));
 }
 
 template <class D, int... Is>
@@ -86,17 +88,19 @@ __global__ void __launch_bounds__(128, 4) fused3d_kernel(const __grid_constant__
                                                          const float* __restrict__ fin, float* __restrict__ fout) {
   constexpr int Q = D::Q;
   using Seq = std::make_integer_sequence<int, Q>;
-  const long long nsite = (long long)p.Nx * p.Ny * p.Nz;
-  const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  // Nx Ny Nz < 2^31 (checked at creation): 32-bit site arithmetic
+  const int nsite = p.Nx * p.Ny * p.Nz;
+  const int site = (int)(blockIdx.x * blockDim.x + threadIdx.x);
   unsigned fl = 0;
   // each thread keeps its pulled populations here between the two passes
   // (column threadIdx.x of a [Q][128] array: consecutive threads, banks)
   extern __shared__ float keep_all[];
   float* keep = keep_all + threadIdx.x;
   if (site < nsite) {
-    const int x = (int)(site % p.Nx);
-    const long long r = site / p.Nx;
-    const int y = (int)(r % p.Ny), z = (int)(r / p.Ny);
+    const int r = site / p.Nx;
+    const int x = site - r * p.Nx;
+    const int z = r / p.Ny;
+    const int y = r - z * p.Ny;
     float s[6][10];
 #pragma unroll
     for (int g = 0; g < 6; ++g)
@@ -241,7 +245,7 @@ __global__ void __launch_bounds__(128, 4) fused3d_kernel(const __grid_constant__
     }
     const float a0 = U0 * p.inv_tau, ax = p.v0 * Ux * p.inv_tau, ay = p.v0 * Uy * p.inv_tau,
                 az = p.v0 * Uz * p.inv_tau;
-    float* out = fout + (long long)z * p.zstride + (long long)y * p.pitch + x;
+    float* out = fout + ((unsigned)z * (unsigned)p.zstride + (unsigned)y * (unsigned)p.pitch + (unsigned)x);
     f3_collide_all<D>(Seq{}, p, keep, c, a0, ax, ay, az, out);
   }
   report(fl, p.err);

@@ -95,7 +95,8 @@ __device__ __forceinline__ void o3_relax(const float (&d)[Def::Q], float e, floa
   if constexpr (nx != 0) om = fmaf(-(float)nx, ax, om);
   if constexpr (ny != 0) om = fmaf(-(float)ny, ay, om);
   const float v = d[I];
-  __stcs(out + (long long)I * plane, fmaf(om, e - v, v));
+  if constexpr (Def::Q <= 104) __stcs(out + (size_t)(unsigned)plane * I, fmaf(om, e - v, v));
+  else __stcs(out + (long long)I * plane, fmaf(om, e - v, v));   // see o3_load
 }
 
 template <int... L>
@@ -136,11 +137,25 @@ __device__ __forceinline__ void o3_collide_orbit(const float (&d)[Def::Q], const
   }
 }
 
+// Pull of one population.  The stencils above Q = 104 (255 registers, two
+// blocks a SM) keep 64-bit element indices: with the 32-bit form of
+// fused_load their register allocation spills about 1.4 KB a thread.
+template <class Def, int I>
+__device__ __forceinline__ void o3_load(float (&d)[Def::Q], const void* __restrict__ fin, long long plane,
+                                        long long pitch, int x, int y, int Nx, int Ny) {
+  if constexpr (Def::Q <= 104) {
+    fused_load<Def, false, I>(d, fin, nullptr, plane, pitch, x, y, Nx, Ny);
+  } else {
+    const long long idx = (long long)wrap_c<Def::F.ny[I]>(y, Ny) * pitch + wrap_c<Def::F.nx[I]>(x, Nx);
+    d[I] = __ldg(static_cast<const float*>(fin) + (long long)I * plane + idx);
+  }
+}
+
 template <class Def, int... Is>
 __device__ __forceinline__ void o3_load_all(std::integer_sequence<int, Is...>, float (&d)[Def::Q],
                                             const void* __restrict__ fin, long long plane, long long pitch, int x,
                                             int y, int Nx, int Ny) {
-  (fused_load<Def, false, Is>(d, fin, nullptr, plane, pitch, x, y, Nx, Ny), ...);
+  (o3_load<Def, Is>(d, fin, plane, pitch, x, y, Nx, Ny), ...);
 }
 
 template <class Def, int... Ks>

@@ -196,6 +196,27 @@ static void fill_fused(rlbm_ctx* c, double nref) {
     const int e = (int)std::ceil(std::log2(nref * sb.rmax1[g]));
     f.exC[g] = (float)std::ldexp(1.5, 23 + e - 11);
   }
+  for (int g = 0; g < 6; ++g) {
+    const HL* m = f.gm[g];
+    const HL pairs[4][2] = {{m[0], m[1]}, {m[2], m[2]}, {m[3], m[3]}, {m[4], m[4]}};
+    for (int q = 0; q < 4; ++q) {
+      f.gm2[g][2 * q] = make_float2(pairs[q][0].hi, pairs[q][1].hi);
+      f.gm2[g][2 * q + 1] = make_float2(pairs[q][0].lo, pairs[q][1].lo);
+    }
+  }
+  // fixed pull offsets of the sites that need no wrapping (BF16 kernels)
+  const int H = sb.halo;
+  const long long span = (long long)c->Q * c->plane + (long long)H * (c->pitch + 1);
+  if (c->Q <= kMaxQ2 && span < INT_MAX && c->Nx > 2 * H && c->Ny > 2 * H) {
+    f.inner_nx = c->Nx - 2 * H;
+    f.inner_ny = c->Ny - 2 * H;
+    for (int i = 0; i < c->Q; ++i) {
+      const FoldedPop& fp = sb.pops[i];
+      const long long back = (long long)fp.ny * c->pitch + fp.nx;
+      f.doff[i] = (int)((long long)i * c->plane - back);
+      f.dcoff[i] = (int)((long long)fp.group * c->plane - back);
+    }
+  }
   f.k0r = split(nref * sb.kref1);
   f.ykr = split(sb.ykr1);
   f.rt64 = c->d_rt64;
@@ -346,6 +367,8 @@ static rlbm_status create_o3(const rlbm_stencil* st, double m, double tau, int N
   c->pitch = ((long long)Nx + 31) / 32 * 32;
   c->plane = c->pitch * Ny;
   c->sb.halo = sb.halo;
+  if (c->plane >= (1LL << 32))
+    return fail(nullptr, RLBM_ENOTSUP, "a population plane exceeds 2^32 elements (32-bit element indices)");
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess || ndev == 0) return fail(nullptr, RLBM_ECUDA, "no CUDA device available");
@@ -483,6 +506,8 @@ rlbm_status rlbm_create(const rlbm_stencil* st, double m, double tau, int Nx, in
   c->elem = (dtype == RLBM_F64) ? sizeof(double) : (dtype == RLBM_F32) ? sizeof(float) : 2;
   c->pitch = ((long long)Nx + 31) / 32 * 32;
   c->plane = c->pitch * Ny;
+  if (c->plane >= (1LL << 32))
+    return fail(nullptr, RLBM_ENOTSUP, "a population plane exceeds 2^32 elements (32-bit element indices)");
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess || ndev == 0) return fail(nullptr, RLBM_ECUDA, "no CUDA device available");

@@ -212,6 +212,8 @@ rlbm_status rlbm3_create(const rlbm_stencil* st, double m, double tau, int Nx, i
   c->elem = dtype == RLBM_F64 ? sizeof(double) : sizeof(float);
   c->pitch = ((long long)Nx + 31) / 32 * 32;
   c->plane = c->pitch * Ny * Nz;
+  if (c->plane >= (1LL << 32))
+    return fail3(nullptr, RLBM_ENOTSUP, "a population plane exceeds 2^32 elements (32-bit element indices)");
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess || ndev == 0) return fail3(nullptr, RLBM_ECUDA, "no CUDA device available");

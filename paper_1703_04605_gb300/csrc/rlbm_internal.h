@@ -104,6 +104,9 @@ constexpr int DR_NPOS = 192;     // T < 4 T_R
 constexpr int DR_NC = 7;         // degree 6
 constexpr int DR_NSEG = DR_NNEG + DR_NPOS;
 
+// populations of the compiled second-order stencils (at most 73)
+constexpr int kMaxQ2 = 80;
+
 // Parameters of the stencil-specialised FP32 kernels (rlbm_fused.cuh).
 // A constant as the sum of two FP32 numbers (about 48 significant bits).
 struct HL {
@@ -139,6 +142,15 @@ struct FusedParams {
   // six planes (one per group) of uint2 = 4 bf16 (alpha, beta_x, beta_y, q)
   const void* cin;
   void* cout;
+  // gm as the operand pairs of the packed (f32x2) moment sums: per group
+  // (P0, P0^2), (Pv, Pv), (P0 Pv, P0 Pv), (Pv^2, Pv^2), hi pair then lo pair
+  float2 gm2[6][8];
+  // sites x in [halo, halo + inner_nx), y in [halo, halo + inner_ny) pull
+  // without wrapping; there the pulled value of population i and its
+  // coefficient word (BF16) sit doff[i] / dcoff[i] elements from the site's
+  // own element of plane 0 (0 and 0 when the offsets do not fit 32 bits)
+  int inner_nx, inner_ny;
+  int doff[kMaxQ2], dcoff[kMaxQ2];
 };
 
 // One lattice of a persistent batch launch (device memory; rlbm_persist.cuh).
