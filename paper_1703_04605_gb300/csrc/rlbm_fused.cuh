@@ -45,15 +45,6 @@
 // reader rebuilds f_i - r_i = d_i + ref_i(source site) from the same stored
 // numbers, so encoding and decoding agree exactly; the rest of the step is the
 // FP32 path above.
-//
-// Instruction economy (the BF16 kernel is issue-bound, the FP32 kernel
-// close to it): element indices are 32-bit (a plane holds fewer than 2^32
-// elements); a BF16 site whose sources need no wrapping pulls through fixed
-// per-population offsets from its own element; the bfloat16 factors of the
-// reference polynomial enter the sm_100+ mixed-precision FMA straight from
-// their packed words; and the moment sums run as packed FP32 pairs
-// (fma.rn.f32x2), each lane doing the scalar code's operations, so the
-// results are those of the scalar forms bit for bit.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -379,10 +370,38 @@ __device__ __forceinline__ void fused_relax(const float (&d)[Def::Q], float e, c
   }
 }
 
+// Relaxation of two members I, J of an orbit as packed pairs (each lane the
+// scalar fused_relax's operations)
+template <class Def, bool BF, int I, int J>
+__device__ __forceinline__ void fused_relax2(const float (&d)[Def::Q], float eI, float eJ, const uint2 (&cq)[6],
+                                             float a0, float ax, float ay, void* __restrict__ out,
+                                             long long plane) {
+  constexpr int g = Def::F.grp[I], nxI = Def::F.nx[I], nyI = Def::F.ny[I], nxJ = Def::F.nx[J],
+                nyJ = Def::F.ny[J], mult = Def::F.mult[I];
+  float omI = a0, omJ = a0;
+  if constexpr (nxI != 0) omI = fmaf(-(float)nxI, ax, omI);
+  if constexpr (nyI != 0) omI = fmaf(-(float)nyI, ay, omI);
+  if constexpr (nxJ != 0) omJ = fmaf(-(float)nxJ, ax, omJ);
+  if constexpr (nyJ != 0) omJ = fmaf(-(float)nyJ, ay, omJ);
+  const float2 v = make_float2(d[I], d[J]);
+  const float2 t = __ffma2_rn(v, make_float2(-1.0f, -1.0f), make_float2(eI, eJ));   // e - v
+  const float2 vn = __ffma2_rn(make_float2(omI, omJ), t, v);
+  const size_t pl = (unsigned)plane;
+  if constexpr (BF) {
+    const float2 r = make_float2(bf_ref<nxI, nyI, mult>(cq[g]), bf_ref<nxJ, nyJ, mult>(cq[g]));
+    const float2 dv = __ffma2_rn(r, make_float2(-1.0f, -1.0f), vn);
+    __stcs(static_cast<unsigned short*>(out) + pl * I, __bfloat16_as_ushort(__float2bfloat16_rn(dv.x)));
+    __stcs(static_cast<unsigned short*>(out) + pl * J, __bfloat16_as_ushort(__float2bfloat16_rn(dv.y)));
+  } else {
+    __stcs(static_cast<float*>(out) + pl * I, vn.x);
+    __stcs(static_cast<float*>(out) + pl * J, vn.y);
+  }
+}
+
 // Equilibrium of one reflection orbit: the group polynomial
 // mult (c0 + c1 n_x + c2 n_y + c3 n_x^2 + c4 n_y^2 + c5 n_x n_y) split into the
 // part even in both n_x and n_y and the odd terms the members share.
-template <class Def, bool BF, int K>
+template <class Def, bool BF, int K, bool R2 = false>
 __device__ __forceinline__ void fused_collide_orbit(const float (&d)[Def::Q], const float (&c)[6][6],
                                                     const uint2 (&cq)[6], float a0, float ax_, float ay_,
                                                     void* __restrict__ out, long long plane) {
@@ -396,20 +415,33 @@ __device__ __forceinline__ void fused_collide_orbit(const float (&d)[Def::Q], co
     fused_relax<Def, BF, i0>(d, E0, cq, a0, ax_, ay_, out, plane);
   } else if constexpr (kind == 2) {
     const float X = (m * (float)ax) * c[g][1];
-    fused_relax<Def, BF, i0>(d, E0 + X, cq, a0, ax_, ay_, out, plane);
-    fused_relax<Def, BF, i1>(d, E0 - X, cq, a0, ax_, ay_, out, plane);
+    if constexpr (R2) {
+      fused_relax2<Def, BF, i0, i1>(d, E0 + X, E0 - X, cq, a0, ax_, ay_, out, plane);
+    } else {
+      fused_relax<Def, BF, i0>(d, E0 + X, cq, a0, ax_, ay_, out, plane);
+      fused_relax<Def, BF, i1>(d, E0 - X, cq, a0, ax_, ay_, out, plane);
+    }
   } else if constexpr (kind == 3) {
     const float Y = (m * (float)ay) * c[g][2];
-    fused_relax<Def, BF, i0>(d, E0 + Y, cq, a0, ax_, ay_, out, plane);
-    fused_relax<Def, BF, i2>(d, E0 - Y, cq, a0, ax_, ay_, out, plane);
+    if constexpr (R2) {
+      fused_relax2<Def, BF, i0, i2>(d, E0 + Y, E0 - Y, cq, a0, ax_, ay_, out, plane);
+    } else {
+      fused_relax<Def, BF, i0>(d, E0 + Y, cq, a0, ax_, ay_, out, plane);
+      fused_relax<Def, BF, i2>(d, E0 - Y, cq, a0, ax_, ay_, out, plane);
+    }
   } else {
     const float X = (m * (float)ax) * c[g][1], Y = (m * (float)ay) * c[g][2];
     const float Z = (m * (float)(ax * ay)) * c[g][5];
     const float EP = E0 + Z, EM = E0 - Z, XP = X + Y, XM = X - Y;
-    fused_relax<Def, BF, i0>(d, EP + XP, cq, a0, ax_, ay_, out, plane);
-    fused_relax<Def, BF, i1>(d, EM - XM, cq, a0, ax_, ay_, out, plane);
-    fused_relax<Def, BF, i2>(d, EM + XM, cq, a0, ax_, ay_, out, plane);
-    fused_relax<Def, BF, i3>(d, EP - XP, cq, a0, ax_, ay_, out, plane);
+    if constexpr (R2) {
+      fused_relax2<Def, BF, i0, i3>(d, EP + XP, EP - XP, cq, a0, ax_, ay_, out, plane);
+      fused_relax2<Def, BF, i1, i2>(d, EM - XM, EM + XM, cq, a0, ax_, ay_, out, plane);
+    } else {
+      fused_relax<Def, BF, i0>(d, EP + XP, cq, a0, ax_, ay_, out, plane);
+      fused_relax<Def, BF, i1>(d, EM - XM, cq, a0, ax_, ay_, out, plane);
+      fused_relax<Def, BF, i2>(d, EM + XM, cq, a0, ax_, ay_, out, plane);
+      fused_relax<Def, BF, i3>(d, EP - XP, cq, a0, ax_, ay_, out, plane);
+    }
   }
 }
 
@@ -434,11 +466,11 @@ __device__ __forceinline__ void fused_acc_all(std::integer_sequence<int, Ks...>,
   (fused_acc_orbit<Def, Ks>(d, s), ...);
 }
 
-template <class Def, bool BF, int... Ks>
+template <class Def, bool BF, bool R2, int... Ks>
 __device__ __forceinline__ void fused_collide_all(std::integer_sequence<int, Ks...>, const float (&d)[Def::Q],
                                                   const float (&c)[6][6], const uint2 (&cq)[6], float a0,
                                                   float ax, float ay, void* __restrict__ out, long long plane) {
-  (fused_collide_orbit<Def, BF, Ks>(d, c, cq, a0, ax, ay, out, plane), ...);
+  (fused_collide_orbit<Def, BF, Ks, R2>(d, c, cq, a0, ax, ay, out, plane), ...);
 }
 
 // Per-population forms of the two loops (the stencil's reflection orbits are
@@ -470,6 +502,20 @@ __device__ __forceinline__ void fused_collide_pop(const float (&d)[Def::Q], cons
   if constexpr (mult != 1) e *= (float)mult;
   fused_relax<Def, BF, I>(d, e, cq, a0, ax, ay, out, plane);
 }
+
+// Packed (f32x2) forms of the coefficient formulas (groups in pairs) and of
+// the relaxation (orbit members in pairs), and the site division by a
+// multiplier: chosen per compiled stencil and storage from measurements on
+// GB300.  Each is a few per cent faster on some kernels and slower on others,
+// where it changes the register allocation.  Q identifies the stencil: 58
+// M1, 39 G1..G6, 73 E5, 49 S2.
+template <class Def, bool BF, int EXL>
+struct FusedForms {
+  static constexpr int Q = Def::Q;
+  static constexpr bool coeffs2 = BF ? true : EXL ? (Q == 39 || Q == 49) : (Q != 73);
+  static constexpr bool relax2 = BF ? (Q == 39 || Q == 49) : EXL ? false : (Q == 39 || Q == 73);
+  static constexpr bool magic_div = Q == 73 || (EXL && (Q == 39 || Q == 49));
+};
 
 // Orbit form or per-population form, chosen per kernel from measurements on
 // GB300: the orbit form saves about 5 instructions per population (E5 FP32
@@ -534,7 +580,9 @@ __device__ __forceinline__ SplitSite split_solve(const P& p, const float (&M)[9]
 #pragma unroll 1
     for (int it = 0; it < 8; ++it) {
       landau_newton_step_fast(Mf, vx, vy, dvx, dvy);
-      if (fabsf(dvx) + fabsf(dvy) < 1e-7f) break;
+      // quadratic convergence: after a step below 1e-4 the error is of
+      // order its square, below the FP32 rounding of v
+      if (fabsf(dvx) + fabsf(dvy) < 1e-4f) break;
     }
   }
   const float v2 = vx * vx + vy * vy;
@@ -590,7 +638,8 @@ __device__ __forceinline__ SplitSite split_solve(const P& p, const float (&M)[9]
     slope = eos_slope<float>(R32, z);
     const float step = __fdividef(3.0f * Td + p.mb * dR - yd, slope);
     Td -= step;
-    if (fabsf(step) < 3e-8f) break;
+    // the FP64 step below squares the remaining error again
+    if (fabsf(step) < 1e-4f) break;
   }
   // ... and one FP64 Newton step: dR(Td) from the lattice's FP64 table in
   // Td (no reciprocal, no reference subtraction), else from the R(zeta) table
@@ -624,6 +673,7 @@ __device__ __forceinline__ SplitSite split_solve(const P& p, const float (&M)[9]
 // c2 n_y + c3 n_x^2 + c4 n_y^2 + c5 n_x n_y) of each group) from the split
 // site state: the App. B projections in deviation form, without their
 // normalisations (those and the App. A constants are folded into p.gf).
+template <bool C2 = false>
 __device__ __forceinline__ void fused_coeffs(const FusedParams& p, const SplitSite& ss, float (&c)[6][6]) {
   const float dg = ss.dg, Ux = ss.Ux, Uy = ss.Uy, n = ss.n, nd = ss.nd;
   const float Td = ss.Td, dR = ss.dR, R = ss.R, T = ss.T;
@@ -638,20 +688,51 @@ __device__ __forceinline__ void fused_coeffs(const FusedParams& p, const SplitSi
   const float r5 = n * h * Ux, r6 = n * h * Uy;
   const float nm = n * mr32;
   const float r7 = nm * Uy * Uy, r8 = nm * (Uy * Uy - 2.0f * Ux * Ux), r9 = nm * Ux * Uy;
+  if constexpr (C2) {
+    // groups (2j, 2j + 1) as packed pairs; each lane is the scalar form below
+    const float r78 = r7 - r8;
+    const float2 R0 = make_float2(r0, r0), R1 = make_float2(r1, r1), R2 = make_float2(r2, r2);
+    const float2 R3 = make_float2(r3, r3), R4 = make_float2(r4, r4), R5 = make_float2(r5, r5);
+    const float2 R6 = make_float2(r6, r6), R7 = make_float2(r7, r7), R8 = make_float2(r8, r8);
+    const float2 R9 = make_float2(r9, r9), R78 = make_float2(r78, r78);
 #pragma unroll
-  for (int g = 0; g < 6; ++g) {
-    const HL* a = p.gf[g];
-    float al = hl(a[0], r0);
-    al = hl_fma(a[1], r1, al);
-    al = hl_fma(a[2], r4, al);
-    al = hl_fma(a[3], r7, al);
-    al = hl_fma(a[4], r8, al);
-    c[g][0] = al;
-    c[g][1] = hl_fma(a[5], r2, hl(a[6], r5));
-    c[g][2] = hl_fma(a[5], r3, hl(a[6], r6));
-    c[g][3] = hl(a[7], r7 - r8);
-    c[g][4] = hl(a[8], r7);
-    c[g][5] = hl(a[9], r9);
+    for (int j = 0; j < 3; ++j) {
+      const float2(*a)[2] = p.gf2[j];   // a[q][0]: hi pair, a[q][1]: lo pair
+      float2 al = __ffma2_rn(a[0][0], R0, __fmul2_rn(a[0][1], R0));
+      al = __ffma2_rn(a[1][0], R1, __ffma2_rn(a[1][1], R1, al));
+      al = __ffma2_rn(a[2][0], R4, __ffma2_rn(a[2][1], R4, al));
+      al = __ffma2_rn(a[3][0], R7, __ffma2_rn(a[3][1], R7, al));
+      al = __ffma2_rn(a[4][0], R8, __ffma2_rn(a[4][1], R8, al));
+      const float2 h5 = __ffma2_rn(a[6][0], R5, __fmul2_rn(a[6][1], R5));
+      const float2 h6 = __ffma2_rn(a[6][0], R6, __fmul2_rn(a[6][1], R6));
+      const float2 b1 = __ffma2_rn(a[5][0], R2, __ffma2_rn(a[5][1], R2, h5));
+      const float2 b2 = __ffma2_rn(a[5][0], R3, __ffma2_rn(a[5][1], R3, h6));
+      const float2 q3 = __ffma2_rn(a[7][0], R78, __fmul2_rn(a[7][1], R78));
+      const float2 q4 = __ffma2_rn(a[8][0], R7, __fmul2_rn(a[8][1], R7));
+      const float2 q5 = __ffma2_rn(a[9][0], R9, __fmul2_rn(a[9][1], R9));
+      const float2 cc[6] = {al, b1, b2, q3, q4, q5};
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        c[2 * j][k] = cc[k].x;
+        c[2 * j + 1][k] = cc[k].y;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int g = 0; g < 6; ++g) {
+      const HL* a = p.gf[g];
+      float al = hl(a[0], r0);
+      al = hl_fma(a[1], r1, al);
+      al = hl_fma(a[2], r4, al);
+      al = hl_fma(a[3], r7, al);
+      al = hl_fma(a[4], r8, al);
+      c[g][0] = al;
+      c[g][1] = hl_fma(a[5], r2, hl(a[6], r5));
+      c[g][2] = hl_fma(a[5], r3, hl(a[6], r6));
+      c[g][3] = hl(a[7], r7 - r8);
+      c[g][4] = hl(a[8], r7);
+      c[g][5] = hl(a[9], r9);
+    }
   }
 }
 
@@ -664,7 +745,13 @@ __device__ __forceinline__ void fused_site(const FusedParams& p, const void* __r
   using Seq = std::make_integer_sequence<int, Q>;
   {
     int x, y;
-    site_of(site, p.Nx, x, y);
+    if constexpr (FusedForms<Def, BF, EXL>::magic_div) {
+      // y = site / Nx by the multiplier of the lattice (exact for site < 2^31)
+      y = (int)(((unsigned long long)(unsigned)site * p.nx_m) >> p.nx_sh);
+      x = site - y * p.Nx;
+    } else {
+      site_of(site, p.Nx, x, y);
+    }
     float d[Q];
     const unsigned here = (unsigned)y * (unsigned)p.pitch + (unsigned)x;
     if constexpr (BF && Def::Q <= 64) {
@@ -732,7 +819,7 @@ __device__ __forceinline__ void fused_site(const FusedParams& p, const void* __r
     }
     const float U0 = ss.U0, Ux = ss.Ux, Uy = ss.Uy;
     float c[6][6];
-    fused_coeffs(p, ss, c);
+    fused_coeffs<FusedForms<Def, BF, EXL>::coeffs2>(p, ss, c);
     const float a0 = U0 * p.inv_tau, ax = p.v0 * Ux * p.inv_tau, ay = p.v0 * Uy * p.inv_tau;
     uint2 cq[6];
     if constexpr (BF) {
@@ -747,7 +834,8 @@ __device__ __forceinline__ void fused_site(const FusedParams& p, const void* __r
     }
     void* out = BF ? static_cast<void*>(static_cast<unsigned short*>(fout) + here)
                    : static_cast<void*>(static_cast<float*>(fout) + here);
-    if constexpr (fused_use_orbits<Def, BF>()) fused_collide_all<Def, BF>(Orb{}, d, c, cq, a0, ax, ay, out, p.plane);
+    if constexpr (fused_use_orbits<Def, BF>())
+      fused_collide_all<Def, BF, FusedForms<Def, BF, EXL>::relax2>(Orb{}, d, c, cq, a0, ax, ay, out, p.plane);
     else fused_collide_pop_all<Def, BF>(Seq{}, d, c, cq, a0, ax, ay, out, p.plane);
   }
 }

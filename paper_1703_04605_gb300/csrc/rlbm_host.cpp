@@ -204,6 +204,22 @@ static void fill_fused(rlbm_ctx* c, double nref) {
       f.gm2[g][2 * q + 1] = make_float2(pairs[q][0].lo, pairs[q][1].lo);
     }
   }
+  for (int j = 0; j < 3; ++j)
+    for (int q = 0; q < 10; ++q) {
+      f.gf2[j][q][0] = make_float2(f.gf[2 * j][q].hi, f.gf[2 * j + 1][q].hi);
+      f.gf2[j][q][1] = make_float2(f.gf[2 * j][q].lo, f.gf[2 * j + 1][q].lo);
+    }
+  {
+    // multiplier of the exact division by Nx (Granlund-Montgomery): with
+    // 2^(l-1) < Nx <= 2^l, m = ceil(2^(31+l) / Nx) = (2^(31+l) + e) / Nx,
+    // 0 <= e < Nx, is below 2^32, and s m / 2^(31+l) exceeds s / Nx by
+    // s e / (Nx 2^(31+l)) < 2^-l <= 1/Nx for s < 2^31: too little to reach
+    // the next integer, so the floor is s / Nx
+    int l = 0;
+    while ((1LL << l) < c->Nx) ++l;
+    f.nx_m = (unsigned)(((1ULL << (31 + l)) + (unsigned long long)c->Nx - 1) / (unsigned long long)c->Nx);
+    f.nx_sh = 31 + l;
+  }
   // fixed pull offsets of the sites that need no wrapping (BF16 kernels)
   const int H = sb.halo;
   const long long span = (long long)c->Q * c->plane + (long long)H * (c->pitch + 1);

@@ -149,6 +149,10 @@ struct FusedParams {
   // without wrapping; there the pulled value of population i and its
   // coefficient word (BF16) sit doff[i] / dcoff[i] elements from the site's
   // own element of plane 0 (0 and 0 when the offsets do not fit 32 bits)
+  float2 gf2[3][10][2];   // groups (2j, 2j+1): gf hi pair, lo pair
+  // site / Nx = (site nx_m) >> nx_sh for 0 <= site < 2^31
+  unsigned nx_m;
+  int nx_sh;
   int inner_nx, inner_ny;
   int doff[kMaxQ2], dcoff[kMaxQ2];
 };
