@@ -372,6 +372,9 @@ O3_SOURCES = ["paper_1703_04605_gb300/csrc/rlbm_fused_o3.cu", "paper_1703_04605_
               "paper_1703_04605_gb300/csrc/rlbm_fused.cuh",
               "paper_1703_04605_gb300/csrc/rlbm_internal.h", "paper_1703_04605_gb300/csrc/rlbm_stencils.h",
               "paper_1703_04605_gb300/csrc/rlbm_kernels.cuh"]
+F3D_SOURCES = ["paper_1703_04605_gb300/csrc/rlbm_fused3d.cu", "paper_1703_04605_gb300/csrc/rlbm_fused.cuh",
+               "paper_1703_04605_gb300/csrc/rlbm_internal.h", "paper_1703_04605_gb300/csrc/rlbm_stencils.h",
+               "paper_1703_04605_gb300/csrc/rlbm_kernels.cuh"]
 FUSED_SOURCES = ["paper_1703_04605_gb300/csrc/rlbm_fused.cuh", "paper_1703_04605_gb300/csrc/rlbm_internal.h",
                  "paper_1703_04605_gb300/csrc/rlbm_stencils.h", "paper_1703_04605_gb300/csrc/rlbm_kernels.cuh",
                  "paper_1703_04605_gb300/csrc/rlbm_fused_m1.cu"]
@@ -716,7 +719,9 @@ def run_random3d(args):
                                    "G5,G12,G14,G17,G21,G26 (Q=96), v0=0.23342",
                        "sites": int(sites), "Q": info["Q"], "l2": "inputs larger than L2"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": (profiled_traffic("fused3d_kernel_random_flow3d_256.md", F3D_SOURCES)
+                                     if N == 256 and info["kernel"] == 1 else None),
                          "kernel": ("fused3d_kernel<Stencil3Def<5,12,14,17,21,26>>" if info["kernel"] == 1
                                     else "step3d_kernel<float>"),
                          "bytes_per_site": info["bytes_per_site"]},
@@ -965,25 +970,32 @@ def main():
         mask = 0x1F                                   # n, u_x, u_y, T, e
         pout = torch.empty(lat.moments_size(mask), dtype=torch.float64, pin_memory=True).numpy()
         ke = max(10, args.steps)          # the device-timed region's step count
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        lat.init(hostf["n"], hostf["ux"], hostf["uy"], hostf["T"])
-        t1 = time.perf_counter()
-        for _ in range(ke):
-            lat.step(1)
-            lat.sync()
-        t2 = time.perf_counter()
-        out = lat.moments(mask, out=pout)
-        t3 = time.perf_counter()
-        assert np.isfinite(out["n"]).all()
-        e2e = {"value": sites * ke / (t3 - t0) / 1e6, "unit": "MLUPS",
+        runs = []
+        for _ in range(3):                # the host link and cores are shared: median of three
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lat.init(hostf["n"], hostf["ux"], hostf["uy"], hostf["T"])
+            t1 = time.perf_counter()
+            for _ in range(ke):
+                lat.step(1)
+                lat.sync()
+            t2 = time.perf_counter()
+            out = lat.moments(mask, out=pout)
+            t3 = time.perf_counter()
+            assert np.isfinite(out["n"]).all()
+            runs.append((t3 - t0, t1 - t0, t2 - t1, t3 - t2))
+        runs.sort()
+        tt, ti, ts, tr = runs[1]
+        e2e = {"value": sites * ke / tt / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": int(4 * 8 * sites / ke),
                "d2h_bytes_per_step": int(4 + 5 * 8 * sites / ke),
                "steps": ke,
-               "breakdown_ms": {"init": (t1 - t0) * 1e3, "steps": (t2 - t1) * 1e3, "readout": (t3 - t2) * 1e3},
-               "region": "rlbm_init from pinned host fields (upload overlapped with the host validation "
-                         "scan, then the init kernel), %d steps with the status word read back after each, "
-                         "rlbm_moments of n, u_x, u_y, T, e into a pinned host buffer" % ke}
+               "breakdown_ms": {"init": ti * 1e3, "steps": ts * 1e3, "readout": tr * 1e3},
+               "runs_ms": [round(r[0] * 1e3, 3) for r in runs],
+               "region": "median of 3 runs of: rlbm_init from pinned host fields (upload, device check of "
+                         "the copy, init kernel), %d steps with the status word read back after each, "
+                         "rlbm_moments of n, u_x, u_y, T, e written by the read-out kernel into a pinned "
+                         "host buffer" % ke}
     lat.close()
 
     if rank != 0:

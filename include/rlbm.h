@@ -130,8 +130,11 @@ rlbm_status rlbm_create(const rlbm_stencil* st, double m, double tau, int Nx, in
 
 /* Set f_i = f_i^eq(n, U, T) everywhere (Eq. 16) and t = 0.  Host arrays of
  * Nx*Ny doubles: density n > 0, three-velocity (ux, uy) with ux^2+uy^2 < 1,
- * temperature T > 0 (validated on the host; EINVAL names the first bad site).
- * Copies the fields to the device (blocking on the context stream). */
+ * temperature T > 0.  Copies the fields to the device (page-locked arrays
+ * make the copy direct), checks the copy there (EINVAL names the first bad
+ * site; the lattice is then left as it was) and waits for the check on the
+ * context stream; the reference density of the FP32/BF16 storage is the
+ * mean of n.  The arrays may be reused when the call returns. */
 rlbm_status rlbm_init(rlbm_ctx* ctx, const double* n, const double* ux, const double* uy,
                       const double* T);
 
@@ -162,10 +165,12 @@ rlbm_status rlbm_step(rlbm_ctx* ctx, int nsteps);
 rlbm_status rlbm_set_extended_sums(rlbm_ctx* ctx, int level);
 
 /* Macroscopic fields of the current pre-collision state f(., t).
- * mask selects fields (bits below); out receives, in bit order, one
- * Nx*Ny plane per scalar (RLBM_M_NVEC: 3 planes N^0,N^x,N^y; RLBM_M_TMN: 6
- * planes T^00,T^0x,T^0y,T^xx,T^xy,T^yy).  Synchronises the stream, then
- * reports any sticky device error. */
+ * mask selects fields (bits below); out (host memory, rlbm_moments_size
+ * doubles) receives, in bit order, one Nx*Ny plane per scalar (RLBM_M_NVEC:
+ * 3 planes N^0,N^x,N^y; RLBM_M_TMN: 6 planes T^00,T^0x,T^0y,T^xx,T^xy,T^yy).
+ * Page-locked (mapped) memory is written directly by the read-out kernel;
+ * other memory through a device buffer of the context and one copy.
+ * Synchronises the stream, then reports any sticky device error. */
 #define RLBM_M_N    0x01u  /* n = U_a N^a (Eq. 19)             */
 #define RLBM_M_UX   0x02u  /* u_x = U^x / U^0                  */
 #define RLBM_M_UY   0x04u  /* u_y = U^y / U^0                  */
@@ -321,7 +326,8 @@ rlbm_status rlbm3_create(const rlbm_stencil* st, double m, double tau, int Nx, i
                          rlbm_dtype dtype, void* cuda_stream, rlbm_ctx3** out);
 
 /* f = f^eq(n, U, T) (Eq. 16), t = 0.  Host FP64 arrays of Nx*Ny*Nz values;
- * n > 0, T > 0, |u| < 1 checked (EINVAL names the first bad site). */
+ * n > 0, T > 0, |u| < 1 checked on the device copy (EINVAL names the first
+ * bad site), as rlbm_init. */
 rlbm_status rlbm3_init(rlbm_ctx3* ctx, const double* n, const double* ux, const double* uy,
                        const double* uz, const double* T);
 
@@ -331,8 +337,9 @@ rlbm_status rlbm3_step(rlbm_ctx3* ctx, int nsteps);
 /* Macroscopic fields of the pre-collision state at t into host memory, one
  * Nx*Ny*Nz plane per scalar, in the order of the mask bits: RLBM_M_N, _UX,
  * _UY, _T, _E, _NVEC (4 planes N^0..N^z), _TMN (10 planes T^00 T^0x T^0y
- * T^0z T^xx T^xy T^xz T^yy T^yz T^zz), _UZ.  Synchronises the stream and
- * reports sticky device errors (ENONPHYS). */
+ * T^0z T^xx T^xy T^xz T^yy T^yz T^zz), _UZ.  Page-locked memory is written
+ * directly, as rlbm_moments.  Synchronises the stream and reports sticky
+ * device errors (ENONPHYS). */
 rlbm_status rlbm3_moments(rlbm_ctx3* ctx, double* out, unsigned mask);
 size_t rlbm3_moments_size(const rlbm_ctx3* ctx, unsigned mask);
 

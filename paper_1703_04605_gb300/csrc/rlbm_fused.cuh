@@ -107,15 +107,20 @@ __device__ __forceinline__ float add_bf(unsigned short h, float acc) {
   return r;
 }
 
-// reference of a population from its group's packed coefficients:
-// mult (alpha + n_x beta_x + n_y beta_y + |n|^2 q), in this order
+// reference of a population from its group's packed coefficients,
+// mult (alpha + |n|^2 q + n_y beta_y + n_x beta_x) in this order, with the
+// multiplicity (1 or 2) folded into the exact integer factors: the members
+// of a reflection orbit share the first terms, which the encoder evaluates
+// once an orbit, and the decoder's chain is the same operation for operation
 template <int nx, int ny, int mult>
 __device__ __forceinline__ float bf_ref(uint2 c) {
-  float r = bf_lo(c.x);
-  if constexpr (nx != 0) r = fma_kbf<nx, true>(c.x, r);
-  if constexpr (ny != 0) r = fma_kbf<ny, false>(c.y, r);
-  if constexpr (nx * nx + ny * ny != 0) r = fma_kbf<nx * nx + ny * ny, true>(c.y, r);
-  if constexpr (mult != 1) r *= (float)mult;
+  static_assert(mult == 1 || mult == 2, "folded multiplicities are 1 or 2");
+  float r;
+  if constexpr (mult == 1) r = bf_lo(c.x);
+  else r = fma_kbf<mult, false>(c.x, 0.0f);
+  if constexpr (nx * nx + ny * ny != 0) r = fma_kbf<mult * (nx * nx + ny * ny), true>(c.y, r);
+  if constexpr (ny != 0) r = fma_kbf<mult * ny, false>(c.y, r);
+  if constexpr (nx != 0) r = fma_kbf<mult * nx, true>(c.x, r);
   return r;
 }
 

@@ -165,7 +165,9 @@ __global__ void __launch_bounds__(128, 4) fused3d_kernel(const __grid_constant__
       v[0] -= d0;
       v[1] -= d1;
       v[2] -= d2;
-      if (fabsf(d0) + fabsf(d1) + fabsf(d2) < 1e-7f) break;
+      // quadratic convergence: after a step below 1e-4 the error is of
+      // order its square, below the FP32 rounding of v
+      if (fabsf(d0) + fabsf(d1) + fabsf(d2) < 1e-4f) break;
     }
     const float v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
     if (!(v2 < 1.0f)) fl |= ERR_LANDAU;
@@ -195,7 +197,7 @@ __global__ void __launch_bounds__(128, 4) fused3d_kernel(const __grid_constant__
       slope = eos_slope<float>(R32, zz);
       const float step = __fdividef(3.0f * Td + p.mb * ((R32 - p.Rr.hi) - p.Rr.lo) - yd, slope);
       Td -= step;
-      if (fabsf(step) < 3e-8f) break;
+      if (fabsf(step) < 1e-4f) break;   // the FP64 step below squares the remaining error
     }
     // ... and one FP64 Newton step: dR(Td) from the lattice's FP64 table in
     // Td, else from the R(zeta) table

@@ -36,7 +36,7 @@ struct rlbm_ctx {
   double* d_rt64 = nullptr;
   float* d_rt32 = nullptr;
   double* d_dr64 = nullptr;      // the lattice's dR(Td) table (FP32 kernels' EOS step)
-  double* d_fields = nullptr;   // 4 planes for rlbm_init
+  double* d_fields = nullptr;   // 4 planes for rlbm_init, then the field check's scratch
   double* d_out = nullptr;      // read-out planes
   size_t out_cap = 0;
   size_t device_bytes = 0;
@@ -407,7 +407,7 @@ static rlbm_status create_o3(const rlbm_stencil* st, double m, double tau, int N
             c->mem.get(&c->d_rt64, t64.size() * sizeof(double)) == cudaSuccess &&
             c->mem.get(&c->d_rt32, t32.size() * sizeof(float)) == cudaSuccess &&
             c->mem.get(&c->d_dr64, drt.size() * sizeof(double)) == cudaSuccess &&
-            c->mem.get(&c->d_fields, 4 * nsite * sizeof(double)) == cudaSuccess &&
+            c->mem.get(&c->d_fields, (4 * nsite + kScanBlocks + 1) * sizeof(double)) == cudaSuccess &&
             c->mem.get(&c->d_shift, 2 * Q * sizeof(int)) == cudaSuccess &&
             c->mem.get(&c->d_off, Q * sizeof(long long)) == cudaSuccess &&
             c->mem.get(&c->d_tab64, tbytes * sizeof(double)) == cudaSuccess &&
@@ -417,7 +417,7 @@ static rlbm_status create_o3(const rlbm_stencil* st, double m, double tau, int N
     return fail(nullptr, RLBM_ENOMEM, "device allocation failed");
   }
   c->device_bytes = 2 * fbytes + sizeof(unsigned) + t64.size() * 8 + t32.size() * 4 + drt.size() * 8 +
-                    4 * nsite * 8 + 2 * Q * sizeof(int) + Q * sizeof(long long) + tbytes * 12;
+                    (4 * nsite + kScanBlocks + 1) * 8 + 2 * Q * sizeof(int) + Q * sizeof(long long) + tbytes * 12;
   std::vector<int> shift(2 * Q);
   std::vector<long long> off(Q);
   std::vector<double> tab64(tbytes);
@@ -544,13 +544,13 @@ rlbm_status rlbm_create(const rlbm_stencil* st, double m, double tau, int Nx, in
             c->mem.get(&c->d_rt64, t64.size() * sizeof(double)) == cudaSuccess &&
             c->mem.get(&c->d_rt32, t32.size() * sizeof(float)) == cudaSuccess &&
             c->mem.get(&c->d_dr64, drt.size() * sizeof(double)) == cudaSuccess &&
-            c->mem.get(&c->d_fields, 4 * nsite * sizeof(double)) == cudaSuccess;
+            c->mem.get(&c->d_fields, (4 * nsite + kScanBlocks + 1) * sizeof(double)) == cudaSuccess;
   if (!ok) {
     release(c.get());
     return fail(nullptr, RLBM_ENOMEM, "device allocation failed");
   }
   c->device_bytes = 2 * fbytes + sizeof(unsigned) + t64.size() * 8 + t32.size() * 4 + drt.size() * 8 +
-                    4 * nsite * 8;
+                    (4 * nsite + kScanBlocks + 1) * 8;
   e = cudaMemcpy(c->d_rt64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_rt32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_dr64, drt.data(), drt.size() * sizeof(double), cudaMemcpyHostToDevice);
@@ -631,8 +631,8 @@ rlbm_status rlbm_init(rlbm_ctx* c, const double* n, const double* ux, const doub
   if (!c) return RLBM_EINVAL;
   if (!n || !ux || !uy || !T) return fail(c, RLBM_EINVAL, "NULL field pointer");
   const size_t N = (size_t)c->Nx * c->Ny;
-  // the upload (asynchronous from pinned memory) overlaps the host scan; the
-  // populations are written only after the scan has passed
+  // upload, then a device check of the copy (first invalid site, density
+  // sum); the populations are written only after the check has passed
   const double* src[4] = {n, ux, uy, T};
   for (int k = 0; k < 4; ++k) {
     cudaError_t e = cudaMemcpyAsync(c->d_fields + k * N, src[k], N * sizeof(double),
@@ -642,9 +642,10 @@ rlbm_status rlbm_init(rlbm_ctx* c, const double* n, const double* ux, const doub
       return cuda_fail(c, e, "field upload");
     }
   }
-  const FieldScan fs = scan_fields(n, ux, uy, nullptr, T, N);
+  const double* d = c->d_fields;
+  const FieldScan fs = check_fields(d, d + N, d + 2 * N, nullptr, d + 3 * N, N, c->d_fields + 4 * N, c->stream);
+  if (fs.err != cudaSuccess) return cuda_fail(c, fs.err, "field check");
   if (fs.first_bad < N) {
-    cudaStreamSynchronize(c->stream);   // the caller's arrays stay read until here
     const size_t s = fs.first_bad;
     char b[160];
     std::snprintf(b, sizeof b, "invalid field at site %zu (x=%zu, y=%zu): need n>0, T>0, |u|<1",
@@ -717,7 +718,9 @@ rlbm_status rlbm_moments(rlbm_ctx* c, double* out, unsigned mask) {
   if (mask & ~0x7Fu) return fail(c, RLBM_EINVAL, "unknown mask bits");
   const size_t need = rlbm_moments_size(c, mask);
   if (need == 0) return RLBM_OK;
-  if (need > c->out_cap) {
+  // page-locked caller memory: the read-out kernel writes it directly
+  double* direct = mapped_alias(out);
+  if (!direct && need > c->out_cap) {
     c->mem.put(c->d_out);
     c->d_out = nullptr;
     c->out_cap = 0;
@@ -725,7 +728,7 @@ rlbm_status rlbm_moments(rlbm_ctx* c, double* out, unsigned mask) {
     if (e != cudaSuccess) return fail(c, RLBM_ENOMEM, "read-out buffer");
     c->out_cap = need;
   }
-  MomentOut mo{c->d_out, mask};
+  MomentOut mo{direct ? direct : c->d_out, mask};
   cudaError_t e;
   if (c->order == 3) {
     e = launch_moments_o3(c->dtype, *c->o3, c->buf[1 - c->cur], mo, c->stream);
@@ -748,8 +751,10 @@ rlbm_status rlbm_moments(rlbm_ctx* c, double* out, unsigned mask) {
     e = launch_moments(c->dtype, *c->p64, c->buf[1 - c->cur], mo, c->stream);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "moments launch");
-  e = cudaMemcpyAsync(out, c->d_out, need * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "read-out copy");
+  if (!direct) {
+    e = cudaMemcpyAsync(out, c->d_out, need * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read-out copy");
+  }
   return check_device_error(c);
 }
 

@@ -36,7 +36,7 @@ struct rlbm_ctx3 {
   long long* d_off = nullptr;
   double* d_tab64 = nullptr;
   float* d_tab32 = nullptr;
-  double* d_fields = nullptr;  // 5 planes for rlbm3_init
+  double* d_fields = nullptr;  // 5 planes for rlbm3_init, then the field check's scratch
   double* d_out = nullptr;
   size_t out_cap = 0;
   size_t device_bytes = 0;
@@ -250,7 +250,7 @@ rlbm_status rlbm3_create(const rlbm_stencil* st, double m, double tau, int Nx, i
             c->mem.get(&c->d_off, off.size() * sizeof(long long)) == cudaSuccess &&
             c->mem.get(&c->d_tab64, t64.size() * sizeof(double)) == cudaSuccess &&
             c->mem.get(&c->d_tab32, t32.size() * sizeof(float)) == cudaSuccess &&
-            c->mem.get(&c->d_fields, 5 * nsite * sizeof(double)) == cudaSuccess;
+            c->mem.get(&c->d_fields, (5 * nsite + kScanBlocks + 1) * sizeof(double)) == cudaSuccess;
   std::vector<double> w64;
   std::vector<float> w32;
   if (ok && c->order == 3) {
@@ -269,7 +269,7 @@ rlbm_status rlbm3_create(const rlbm_stencil* st, double m, double tau, int Nx, i
     return fail3(nullptr, RLBM_ENOMEM, "device allocation failed");
   }
   c->device_bytes = 2 * fbytes + r64.size() * 8 + r32.size() * 4 + drt.size() * 8 + sh.size() * 4 + off.size() * 8 + t64.size() * 12 +
-                    5 * nsite * 8 + 4;
+                    (5 * nsite + kScanBlocks + 1) * 8 + 4;
   e = cudaMemcpy(c->d_rt64, r64.data(), r64.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_rt32, r32.data(), r32.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_dr64, drt.data(), drt.size() * sizeof(double), cudaMemcpyHostToDevice);
@@ -323,7 +323,7 @@ rlbm_status rlbm3_init(rlbm_ctx3* c, const double* n, const double* ux, const do
   if (!c) return RLBM_EINVAL;
   if (!n || !ux || !uy || !uz || !T) return fail3(c, RLBM_EINVAL, "NULL field pointer");
   const size_t N = (size_t)c->Nx * c->Ny * c->Nz;
-  // the upload overlaps the host scan; populations are written after it passed
+  // upload, then a device check of the copy; populations are written after it passed
   const double* src[5] = {n, ux, uy, uz, T};
   for (int k = 0; k < 5; ++k) {
     cudaError_t e = cudaMemcpyAsync(c->d_fields + k * N, src[k], N * sizeof(double), cudaMemcpyHostToDevice,
@@ -333,9 +333,10 @@ rlbm_status rlbm3_init(rlbm_ctx3* c, const double* n, const double* ux, const do
       return cuda_fail3(c, e, "field upload");
     }
   }
-  const FieldScan fs = scan_fields(n, ux, uy, uz, T, N);
+  const double* d = c->d_fields;
+  const FieldScan fs = check_fields(d, d + N, d + 2 * N, d + 3 * N, d + 4 * N, N, c->d_fields + 5 * N, c->stream);
+  if (fs.err != cudaSuccess) return cuda_fail3(c, fs.err, "field check");
   if (fs.first_bad < N) {
-    cudaStreamSynchronize(c->stream);   // the caller's arrays stay read until here
     const size_t s = fs.first_bad;
     char b[200];
     std::snprintf(b, sizeof b, "invalid field at site %zu (x=%zu, y=%zu, z=%zu): need n>0, T>0, |u|<1", s,
@@ -388,7 +389,9 @@ rlbm_status rlbm3_moments(rlbm_ctx3* c, double* out, unsigned mask) {
   if (mask & ~0xFFu) return fail3(c, RLBM_EINVAL, "unknown mask bits");
   const size_t need = rlbm3_moments_size(c, mask);
   if (need == 0) return RLBM_OK;
-  if (need > c->out_cap) {
+  // page-locked caller memory: the read-out kernel writes it directly
+  double* direct = mapped_alias(out);
+  if (!direct && need > c->out_cap) {
     c->mem.put(c->d_out);
     c->d_out = nullptr;
     c->out_cap = 0;
@@ -396,10 +399,10 @@ rlbm_status rlbm3_moments(rlbm_ctx3* c, double* out, unsigned mask) {
     if (e != cudaSuccess) return fail3(c, RLBM_ENOMEM, "read-out buffer");
     c->out_cap = need;
   }
-  MomentOut mo{c->d_out, mask};
+  MomentOut mo{direct ? direct : c->d_out, mask};
   // the pre-collision state at t is the pull of S_{t-1}, the buffer the last step read
   cudaError_t e = launch_moments3d(c->dtype, c->p, c->buf[1 - c->cur], mo, c->stream);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && !direct)
     e = cudaMemcpyAsync(out, c->d_out, need * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (e != cudaSuccess) return cuda_fail3(c, e, "read-out");
   return check_error3(c);

@@ -198,9 +198,23 @@ struct FieldPtrs {
 };
 
 struct MomentOut {
-  double* out;           // device buffer, planes of Nx*Ny doubles
+  double* out;           // device-accessible buffer (device memory or mapped
+                         // page-locked host memory), planes of Nx*Ny doubles
   unsigned mask;
 };
+
+// Validation of uploaded initial fields (rlbm_init, rlbm3_init), on the
+// device: block b of at most kScanBlocks scans sites [b len, (b+1) len),
+// len = ceil(N / blocks); it lowers *bad (set to all ones before) to the
+// smallest index violating n > 0, T > 0, |u| < 1 (all finite) and writes
+// the FP64 sum of n over its sites, reduced in a fixed order, to part[b]
+// (so the total, summed by the host in block order, depends on N only).
+// uz may be NULL (2D).
+constexpr int kScanBlocks = 1024;
+int field_check_blocks(long long N);
+cudaError_t launch_field_check(const double* n, const double* ux, const double* uy, const double* uz,
+                               const double* T, long long N, double* part, unsigned long long* bad,
+                               cudaStream_t s);
 
 // ------------------------------------------------- third-order 2D lattices
 // Eleven-group stencils folded onto the xy plane (rlbm_kernels_o3.cu); the
