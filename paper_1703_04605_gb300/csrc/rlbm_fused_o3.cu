@@ -171,12 +171,14 @@ __device__ __forceinline__ void o3_collide_all(std::integer_sequence<int, Ks...>
   (o3_collide_orbit<Def, Ks>(d, e, nd, a0, ax, ay, out, plane, p), ...);
 }
 
-// Resident blocks of 128 threads per SM: three (168 registers, no spills)
-// up to Q = 104; the larger halo-4/5 sets take 255 registers at two blocks
-// (36-80 bytes spilled), still about twice the generic kernel.
+// Resident blocks of 128 threads per SM: four (128 registers, 68-92 bytes
+// spilled to L1) up to Q = 104, measured 6-7 % faster on GB300 than three
+// blocks at 168 registers without spills (the kernel is latency-bound); the
+// larger halo-4/5 sets take 255 registers at two blocks (16-48 bytes
+// spilled), still about twice the generic kernel.
 template <class Def>
 constexpr int o3_min_blocks() {
-  return Def::Q <= 104 ? 3 : 2;
+  return Def::Q <= 104 ? 4 : 2;
 }
 
 template <class Def>
