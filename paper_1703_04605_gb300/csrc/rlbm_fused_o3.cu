@@ -85,16 +85,34 @@ __device__ __forceinline__ void o3_acc_orbit(const float (&d)[Def::Q], float (&s
   }
 }
 
+// the pulled values of the collision pass: kept in registers since the
+// moment pass, or pulled again (two-pass form; L1/L2 hits)
+struct O3Repull {
+  const float* fin;
+  long long plane, pitch;
+  int x, y, Nx, Ny;
+};
+template <class Def, int I>
+__device__ __forceinline__ float o3_pop(const float (&d)[Def::Q]) {
+  return d[I];
+}
+template <class Def, int I>
+__device__ __forceinline__ float o3_pop(const O3Repull& r) {
+  constexpr int DX = Def::F.nx[I], DY = Def::F.ny[I];
+  const unsigned idx = (unsigned)wrap_c<DY>(r.y, r.Ny) * (unsigned)r.pitch + (unsigned)wrap_c<DX>(r.x, r.Nx);
+  return __ldg(r.fin + idx + (size_t)(unsigned)r.plane * I);
+}
+
 // d_i + (p_i.U/(p_i^0 tau)) (e - d_i), stored at the site; the weight is
 // (U0 - v0 (n_x U_x + n_y U_y))/tau.
-template <class Def, int I>
-__device__ __forceinline__ void o3_relax(const float (&d)[Def::Q], float e, float a0, float ax, float ay,
+template <class Def, int I, class Pops>
+__device__ __forceinline__ void o3_relax(const Pops& d, float e, float a0, float ax, float ay,
                                          float* __restrict__ out, long long plane) {
   constexpr int nx = Def::F.nx[I], ny = Def::F.ny[I];
   float om = a0;
   if constexpr (nx != 0) om = fmaf(-(float)nx, ax, om);
   if constexpr (ny != 0) om = fmaf(-(float)ny, ay, om);
-  const float v = d[I];
+  const float v = o3_pop<Def, I>(d);
   if constexpr (Def::Q <= 104) __stcs(out + (size_t)(unsigned)plane * I, fmaf(om, e - v, v));
   else __stcs(out + (long long)I * plane, fmaf(om, e - v, v));   // see o3_load
 }
@@ -107,8 +125,8 @@ __device__ __forceinline__ float class_sum(std::integer_sequence<int, L...>, con
 }
 
 // Equilibrium and relaxation of the members of reflection orbit K.
-template <class Def, int K>
-__device__ __forceinline__ void o3_collide_orbit(const float (&d)[Def::Q], const float (&e)[kO3Mono], float nd,
+template <class Def, int K, class Pops>
+__device__ __forceinline__ void o3_collide_orbit(const Pops& d, const float (&e)[kO3Mono], float nd,
                                                  float a0, float ax, float ay, float* __restrict__ out,
                                                  long long plane, const FusedO3Params& p) {
   constexpr int kind = Def::O.kind[K];
@@ -116,24 +134,24 @@ __device__ __forceinline__ void o3_collide_orbit(const float (&d)[Def::Q], const
   const HL* w = p.ow[K];
   const float E = class_sum(kEE{}, w, e, hl(w[0], nd));
   if constexpr (kind == 1) {
-    o3_relax<Def, i0>(d, E, a0, ax, ay, out, plane);
+    o3_relax<Def, i0, Pops>(d, E, a0, ax, ay, out, plane);
   } else if constexpr (kind == 2) {
     const float X = class_sum(kOE{}, w, e, 0.0f);
-    o3_relax<Def, i0>(d, E + X, a0, ax, ay, out, plane);
-    o3_relax<Def, i1>(d, E - X, a0, ax, ay, out, plane);
+    o3_relax<Def, i0, Pops>(d, E + X, a0, ax, ay, out, plane);
+    o3_relax<Def, i1, Pops>(d, E - X, a0, ax, ay, out, plane);
   } else if constexpr (kind == 3) {
     const float Y = class_sum(kEO{}, w, e, 0.0f);
-    o3_relax<Def, i0>(d, E + Y, a0, ax, ay, out, plane);
-    o3_relax<Def, i2>(d, E - Y, a0, ax, ay, out, plane);
+    o3_relax<Def, i0, Pops>(d, E + Y, a0, ax, ay, out, plane);
+    o3_relax<Def, i2, Pops>(d, E - Y, a0, ax, ay, out, plane);
   } else {
     const float X = class_sum(kOE{}, w, e, 0.0f);
     const float Y = class_sum(kEO{}, w, e, 0.0f);
     const float Z = class_sum(kOO{}, w, e, 0.0f);
     const float EP = E + Z, EM = E - Z, XP = X + Y, XM = X - Y;
-    o3_relax<Def, i0>(d, EP + XP, a0, ax, ay, out, plane);   // (+, +)
-    o3_relax<Def, i1>(d, EM - XM, a0, ax, ay, out, plane);   // (-, +)
-    o3_relax<Def, i2>(d, EM + XM, a0, ax, ay, out, plane);   // (+, -)
-    o3_relax<Def, i3>(d, EP - XP, a0, ax, ay, out, plane);   // (-, -)
+    o3_relax<Def, i0, Pops>(d, EP + XP, a0, ax, ay, out, plane);   // (+, +)
+    o3_relax<Def, i1, Pops>(d, EM - XM, a0, ax, ay, out, plane);   // (-, +)
+    o3_relax<Def, i2, Pops>(d, EM + XM, a0, ax, ay, out, plane);   // (+, -)
+    o3_relax<Def, i3, Pops>(d, EP - XP, a0, ax, ay, out, plane);   // (-, -)
   }
 }
 
@@ -164,18 +182,25 @@ __device__ __forceinline__ void o3_acc_all(std::integer_sequence<int, Ks...>, co
   (o3_acc_orbit<Def, Ks>(d, s, M, p), ...);
 }
 
-template <class Def, int... Ks>
-__device__ __forceinline__ void o3_collide_all(std::integer_sequence<int, Ks...>, const float (&d)[Def::Q],
+template <class Def, class Pops, int... Ks>
+__device__ __forceinline__ void o3_collide_all(std::integer_sequence<int, Ks...>, const Pops& d,
                                                const float (&e)[kO3Mono], float nd, float a0, float ax, float ay,
                                                float* __restrict__ out, long long plane, const FusedO3Params& p) {
-  (o3_collide_orbit<Def, Ks>(d, e, nd, a0, ax, ay, out, plane, p), ...);
+  (o3_collide_orbit<Def, Ks, Pops>(d, e, nd, a0, ax, ay, out, plane, p), ...);
 }
 
-// Resident blocks of 128 threads per SM: four (128 registers, 68-92 bytes
-// spilled to L1) up to Q = 104, measured 6-7 % faster on GB300 than three
-// blocks at 168 registers without spills (the kernel is latency-bound); the
-// larger halo-4/5 sets take 255 registers at two blocks (16-48 bytes
-// spilled), still about twice the generic kernel.
+// Resident blocks of 128 threads per SM: four (128 registers) up to
+// Q = 104, in two passes over the populations: the moment pass pulls each
+// value and folds it into the group sums, the collision pass pulls it again
+// (an L1/L2 hit: the block read the same lines moments earlier) instead of
+// keeping 100 values in registers across the site solve, so the four blocks
+// spill at most 8 bytes (bit-identical to the one-pass form; measured on
+// GB300: 4 % faster than one pass at four blocks with 70-90 bytes spilled,
+// 11 % faster than one pass at three blocks of 168 registers; the kernel is
+// latency-bound).  The larger halo-4/5 sets keep one pass at 255 registers
+// and two blocks (16-48 bytes spilled), still about twice the generic kernel.
+constexpr bool O3_TWO_PASS = true;
+
 template <class Def>
 constexpr int o3_min_blocks() {
   return Def::Q <= 104 ? 4 : 2;
@@ -190,14 +215,21 @@ __global__ void __launch_bounds__(128, o3_min_blocks<Def>()) fused_o3_kernel(con
   if (site < p.Nx * p.Ny) {
     int x, y;
     site_of(site, p.Nx, x, y);
-    float d[Def::Q];
-    o3_load_all<Def>(std::make_integer_sequence<int, Def::Q>{}, d, fin, p.plane, p.pitch, x, y, p.Nx, p.Ny);
     float s[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
     float M[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) M[k] = 0.0f;
     using Orb = std::make_integer_sequence<int, Def::O.K>;
-    o3_acc_all<Def>(Orb{}, d, s, M, p);
+    constexpr bool two_pass = O3_TWO_PASS && Def::Q <= 104;
+    float d[two_pass ? 1 : Def::Q];
+    if constexpr (two_pass) {
+      float dd[Def::Q];
+      o3_load_all<Def>(std::make_integer_sequence<int, Def::Q>{}, dd, fin, p.plane, p.pitch, x, y, p.Nx, p.Ny);
+      o3_acc_all<Def>(Orb{}, dd, s, M, p);
+    } else {
+      o3_load_all<Def>(std::make_integer_sequence<int, Def::Q>{}, d, fin, p.plane, p.pitch, x, y, p.Nx, p.Ny);
+      o3_acc_all<Def>(Orb{}, d, s, M, p);
+    }
     const SplitSite ss = split_solve(p, M, fl);
     // e_l = n dmu_l in the small quantities dU, dT, dR, U_x, U_y (no cancellation)
     float e[kO3Mono];
@@ -205,7 +237,10 @@ __global__ void __launch_bounds__(128, o3_min_blocks<Def>()) fused_o3_kernel(con
     const float Ux = ss.Ux, Uy = ss.Uy;
     const float a0 = ss.U0 * p.inv_tau, ax = p.v0 * Ux * p.inv_tau, ay = p.v0 * Uy * p.inv_tau;
     float* out = fout + (long long)y * p.pitch + x;
-    o3_collide_all<Def>(Orb{}, d, e, ss.nd, a0, ax, ay, out, p.plane, p);
+    if constexpr (two_pass)
+      o3_collide_all<Def>(Orb{}, O3Repull{fin, p.plane, p.pitch, x, y, p.Nx, p.Ny}, e, ss.nd, a0, ax, ay, out,
+                          p.plane, p);
+    else o3_collide_all<Def>(Orb{}, d, e, ss.nd, a0, ax, ay, out, p.plane, p);
   }
   report(fl, p.err);
 }
