@@ -258,9 +258,20 @@ class Lattice3D:
     def sync(self):
         self._chk(self._lib.rlbm3_sync(self._ctx))
 
-    def moments(self, mask=A.M_N | A.M_UX | A.M_UY | A.M_UZ | A.M_T | A.M_E):
+    def moments_size(self, mask=A.M_N | A.M_UX | A.M_UY | A.M_UZ | A.M_T | A.M_E):
+        """Doubles that moments(mask) writes (rlbm3_moments_size)."""
+        return int(self._lib.rlbm3_moments_size(self._ctx, mask))
+
+    def moments(self, mask=A.M_N | A.M_UX | A.M_UY | A.M_UZ | A.M_T | A.M_E, out=None):
+        """Fields as [Nz, Ny, Nx] views of one buffer; out as in Lattice.moments."""
         size = self._lib.rlbm3_moments_size(self._ctx, mask)
-        out = np.empty(size, dtype=np.float64)
+        if out is None:
+            out = np.empty(size, dtype=np.float64)
+        else:
+            out = np.asarray(out)
+            if out.dtype != np.float64 or not out.flags.c_contiguous or out.size < size:
+                raise ValueError("out must be a C-contiguous float64 array of at least %d elements" % size)
+            out = out.reshape(-1)
         self._chk(self._lib.rlbm3_moments(self._ctx, out.ctypes.data_as(C.POINTER(C.c_double)), mask))
         res, plane = {}, 0
         N = self.Nx * self.Ny * self.Nz
