@@ -1041,7 +1041,9 @@ template <class Def, int... Is>
 __device__ __forceinline__ void f32_init_pops(std::integer_sequence<int, Is...>, const float (&c)[6][6],
                                               float* __restrict__ cur, float* __restrict__ prev,
                                               long long plane, long long pitch, int x, int y, int Nx, int Ny) {
-  const long long here = (long long)y * pitch + x;
+  // 32-bit element indices (a plane holds fewer than 2^32 elements)
+  const unsigned here = (unsigned)y * (unsigned)pitch + (unsigned)x;
+  const size_t pl = (unsigned)plane;
   (
       [&] {
         constexpr int i = Is;
@@ -1053,10 +1055,10 @@ __device__ __forceinline__ void f32_init_pops(std::integer_sequence<int, Is...>,
         if constexpr (ny != 0) e = fmaf((float)(ny * ny), c[g][4], e);
         if constexpr (nx != 0 && ny != 0) e = fmaf((float)(nx * ny), c[g][5], e);
         if constexpr (mult != 1) e *= (float)mult;
-        cur[(long long)i * plane + here] = e;
+        cur[here + pl * i] = e;
         // population i of S_{-1} sits at x - n_i: the first pull brings it back
-        const int xs = wrap_c<nx>(x, Nx), ys = wrap_c<ny>(y, Ny);
-        prev[(long long)i * plane + (long long)ys * pitch + xs] = e;
+        const unsigned xs = (unsigned)wrap_c<nx>(x, Nx), ys = (unsigned)wrap_c<ny>(y, Ny);
+        prev[ys * (unsigned)pitch + xs + pl * i] = e;
       }(),
       ...);
 }
