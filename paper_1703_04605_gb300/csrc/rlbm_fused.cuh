@@ -1037,7 +1037,7 @@ __global__ void __launch_bounds__(128) bf16_moments(const __grid_constant__ Step
 // equilibrium of the given fields (split site state with the FP64 dR(Td)
 // table, FP32 projections and group coefficients, FP32 group polynomials),
 // written to S_0 at the site and to S_{-1} at x - n_i (see init_kernel).
-template <class Def, int... Is>
+template <class Def, bool PREV, int... Is>
 __device__ __forceinline__ void f32_init_pops(std::integer_sequence<int, Is...>, const float (&c)[6][6],
                                               float* __restrict__ cur, float* __restrict__ prev,
                                               long long plane, long long pitch, int x, int y, int Nx, int Ny) {
@@ -1056,14 +1056,20 @@ __device__ __forceinline__ void f32_init_pops(std::integer_sequence<int, Is...>,
         if constexpr (nx != 0 && ny != 0) e = fmaf((float)(nx * ny), c[g][5], e);
         if constexpr (mult != 1) e *= (float)mult;
         cur[here + pl * i] = e;
-        // population i of S_{-1} sits at x - n_i: the first pull brings it back
-        const unsigned xs = (unsigned)wrap_c<nx>(x, Nx), ys = (unsigned)wrap_c<ny>(y, Ny);
-        prev[ys * (unsigned)pitch + xs + pl * i] = e;
+        if constexpr (PREV) {
+          // population i of S_{-1} sits at x - n_i: the first pull brings it back
+          const unsigned xs = (unsigned)wrap_c<nx>(x, Nx), ys = (unsigned)wrap_c<ny>(y, Ny);
+          prev[ys * (unsigned)pitch + xs + pl * i] = e;
+        }
       }(),
       ...);
 }
 
-template <class Def>
+// PREV: also write S_{-1} (the copy whose pull is the initial state) into
+// prev; without it the read-out of the freshly initialised state reads cur
+// in place (f32_moments_kernel<Def, false>) and the first step overwrites
+// prev anyway.
+template <class Def, bool PREV>
 __global__ void __launch_bounds__(128) f32_init_kernel(const __grid_constant__ FusedParams p, SiteConsts sc,
                                                        FieldPtrs fd, float* __restrict__ cur,
                                                        float* __restrict__ prev) {
@@ -1096,7 +1102,7 @@ __global__ void __launch_bounds__(128) f32_init_kernel(const __grid_constant__ F
     float c[6][6];
     fused_coeffs(p, ss, c);
     (void)sc;
-    f32_init_pops<Def>(std::make_integer_sequence<int, Def::Q>{}, c, cur, prev, p.plane, p.pitch, x, y, p.Nx,
+    f32_init_pops<Def, PREV>(std::make_integer_sequence<int, Def::Q>{}, c, cur, prev, p.plane, p.pitch, x, y, p.Nx,
                        p.Ny);
   }
   report(fl, p.err);
@@ -1108,7 +1114,9 @@ __global__ void __launch_bounds__(128) f32_init_kernel(const __grid_constant__ F
 // reference in FP32, the EOS finished by an FP64 Newton step), so n and T
 // carry FP32 rounding of their deviations from the reference only.  The
 // moment planes are assembled in FP64 from the float-float sums.
-template <class Def>
+// PULL: the state at t is the pull of S_{t-1} in prev; otherwise (right
+// after f32_init_kernel<Def, false>) it is S_0 in prev read in place.
+template <class Def, bool PULL>
 __global__ void __launch_bounds__(128) f32_moments_kernel(const __grid_constant__ FusedParams fp,
                                                           const __grid_constant__ StepParams<double> p,
                                                           const float* __restrict__ prev, MomentOut mo) {
@@ -1119,8 +1127,15 @@ __global__ void __launch_bounds__(128) f32_moments_kernel(const __grid_constant_
     int x, y;
     site_of(site, p.Nx, x, y);
     float d[Def::Q];
-    fused_load_all<Def, false>(std::make_integer_sequence<int, Def::Q>{}, d, prev, nullptr, p.plane, p.pitch, x,
-                               y, p.Nx, p.Ny);
+    if constexpr (PULL) {
+      fused_load_all<Def, false>(std::make_integer_sequence<int, Def::Q>{}, d, prev, nullptr, p.plane, p.pitch, x,
+                                 y, p.Nx, p.Ny);
+    } else {
+      const unsigned here = (unsigned)y * (unsigned)p.pitch + (unsigned)x;
+      const size_t pl = (unsigned)p.plane;
+#pragma unroll
+      for (int i = 0; i < Def::Q; ++i) d[i] = __ldg(prev + here + pl * i);
+    }
     ExMoments em;
     em.N0 = em.Nx = em.Ny = em.K0 = em.Kx = em.Ky = FF{0.0f, 0.0f};
     em.Txx = em.Txy = em.Tyy = 0.0f;
@@ -1173,11 +1188,15 @@ cudaError_t launch_bf16_io_impl(int what, const FusedParams& fp, const StepParam
   const long long nsite = (long long)p.Nx * p.Ny;
   const unsigned grid = (unsigned)((nsite + 127) / 128);
   if (what == 2) {
-    f32_init_kernel<Def><<<grid, 128, 0, s>>>(fp, p.sc, fd, static_cast<float*>(cur), static_cast<float*>(prev));
+    f32_init_kernel<Def, false><<<grid, 128, 0, s>>>(fp, p.sc, fd, static_cast<float*>(cur), static_cast<float*>(prev));
     return cudaGetLastError();
   }
   if (what == 3) {
-    f32_moments_kernel<Def><<<grid, 128, 0, s>>>(fp, p, static_cast<const float*>(prev), mo);
+    f32_moments_kernel<Def, true><<<grid, 128, 0, s>>>(fp, p, static_cast<const float*>(prev), mo);
+    return cudaGetLastError();
+  }
+  if (what == 4) {
+    f32_moments_kernel<Def, false><<<grid, 128, 0, s>>>(fp, p, static_cast<const float*>(prev), mo);
     return cudaGetLastError();
   }
   if (what == 0) {

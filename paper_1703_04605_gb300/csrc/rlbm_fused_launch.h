@@ -50,7 +50,9 @@ const void* persist_kernel_fn<StencilS2>(int);
 const void* fused_o3_kernel_fn(int kind);
 // Init and read-out on a compiled stencil.  BF16 deviation storage: what = 0
 // init (fields -> coefficients, S_0, S_{-1}), what = 1 read-out of the pull of
-// prev; FP32 storage: what = 2 init, what = 3 read-out (ccur, cprev unused).
+// prev; FP32 storage: what = 2 init of S_0 into cur only, what = 3 read-out
+// of the pull of prev, what = 4 read-out of S_0 in prev (pass cur) right after
+// what = 2, before any step (ccur, cprev unused).
 template <class Def>
 cudaError_t launch_bf16_io(int what, const FusedParams& fp, const StepParams<double>& p, FieldPtrs fd,
                            void* cur, void* prev, void* ccur, void* cprev, MomentOut mo, cudaStream_t s);

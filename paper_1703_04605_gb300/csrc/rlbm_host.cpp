@@ -42,6 +42,7 @@ struct rlbm_ctx {
   size_t device_bytes = 0;
   bool initialised = false;
   bool host_init = false;   // rlbm_init in progress (it sets the reference itself)
+  bool fresh = false;       // FP32 compiled path: S_0 written in place by the init, not stepped yet
   std::unique_ptr<StepParams<double>> p64;
   std::unique_ptr<StepParams<float>> p32;
   int fused = 0;                 // 1: M1, 2: G1..G6, 3: E5, 4: S2; 0: generic kernel
@@ -623,6 +624,7 @@ rlbm_status rlbm_init_device(rlbm_ctx* c, const double* n, const double* ux, con
   c->cur = 0;
   c->t = 0;
   c->initialised = true;
+  c->fresh = c->order == 2 && c->dtype == RLBM_F32 && c->fused;
   return RLBM_OK;
 }
 
@@ -697,6 +699,7 @@ rlbm_status rlbm_step(rlbm_ctx* c, int nsteps) {
     if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
     c->cur = 1 - c->cur;
     ++c->t;
+    c->fresh = false;
   }
   return RLBM_OK;
 }
@@ -741,12 +744,14 @@ rlbm_status rlbm_moments(rlbm_ctx* c, double* out, unsigned mask) {
     else if (c->fused == 3) e = launch_bf16_io<StencilE5>(1, *c->fp, *c->p64, none, nullptr, pv, nullptr, cp, mo, c->stream);
     else e = launch_bf16_io<StencilS2>(1, *c->fp, *c->p64, none, nullptr, pv, nullptr, cp, mo, c->stream);
   } else if (c->dtype == RLBM_F32 && c->fused) {
+    // the state at t is the pull of S_{t-1}; right after the init, S_0 read in place
     FieldPtrs none{nullptr, nullptr, nullptr, nullptr};
-    void* pv = c->buf[1 - c->cur];
-    if (c->fused == 1) e = launch_bf16_io<StencilM1>(3, *c->fp, *c->p64, none, nullptr, pv, nullptr, nullptr, mo, c->stream);
-    else if (c->fused == 2) e = launch_bf16_io<StencilG16>(3, *c->fp, *c->p64, none, nullptr, pv, nullptr, nullptr, mo, c->stream);
-    else if (c->fused == 3) e = launch_bf16_io<StencilE5>(3, *c->fp, *c->p64, none, nullptr, pv, nullptr, nullptr, mo, c->stream);
-    else e = launch_bf16_io<StencilS2>(3, *c->fp, *c->p64, none, nullptr, pv, nullptr, nullptr, mo, c->stream);
+    void* pv = c->fresh ? c->buf[c->cur] : c->buf[1 - c->cur];
+    const int what = c->fresh ? 4 : 3;
+    if (c->fused == 1) e = launch_bf16_io<StencilM1>(what, *c->fp, *c->p64, none, nullptr, pv, nullptr, nullptr, mo, c->stream);
+    else if (c->fused == 2) e = launch_bf16_io<StencilG16>(what, *c->fp, *c->p64, none, nullptr, pv, nullptr, nullptr, mo, c->stream);
+    else if (c->fused == 3) e = launch_bf16_io<StencilE5>(what, *c->fp, *c->p64, none, nullptr, pv, nullptr, nullptr, mo, c->stream);
+    else e = launch_bf16_io<StencilS2>(what, *c->fp, *c->p64, none, nullptr, pv, nullptr, nullptr, mo, c->stream);
   } else {
     e = launch_moments(c->dtype, *c->p64, c->buf[1 - c->cur], mo, c->stream);
   }
@@ -980,6 +985,7 @@ void advance_all(const std::vector<rlbm_ctx*>& v, int k) {
   for (rlbm_ctx* c : v) {
     c->cur ^= (k & 1);
     c->t += k;
+    if (k > 0) c->fresh = false;
   }
 }
 

@@ -137,3 +137,32 @@ def test_readout_3d_into_pinned_memory_equals_staged_copy():
         b = lat.moments(mask, out=np.empty(size, dtype=np.float64))
         for k in a:
             assert np.array_equal(a[k], b[k]), k
+
+
+TOL0 = {"f64": 1e-12, "f32": 2e-6, "bf16dev": 2e-3}
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16dev"])
+@pytest.mark.parametrize("name", ["STENCIL_M1", "STENCIL_G16", "STENCIL_E5", "STENCIL_S2"])
+def test_moments_right_after_init_are_the_fields(dtype, name):
+    """The state at t = 0 is f^eq of the input fields: its moments return
+    them (the FP32 path reads the freshly written state in place), and
+    reading them does not change what the first steps compute."""
+    from paper_1703_04605_gb300 import Lattice, batch_step
+    st = getattr(W, name)
+    Nx, Ny = 75, 61
+    f = _fields(Nx, Ny, seed=21)
+    with Lattice(st["groups"], st["m"], 0.8, Nx, Ny, dtype=dtype, v0=st["v0"]) as a, \
+            Lattice(st["groups"], st["m"], 0.8, Nx, Ny, dtype=dtype, v0=st["v0"]) as b:
+        a.init(f["n"], f["ux"], f["uy"], f["T"])
+        m0 = a.moments()
+        for k in ("n", "T"):
+            assert np.max(np.abs(m0[k] / f[k] - 1)) < TOL0[dtype], k
+        for k in ("ux", "uy"):
+            assert np.max(np.abs(m0[k] - f[k])) < TOL0[dtype], k
+        b.init(f["n"], f["ux"], f["uy"], f["T"])
+        a.step(3)
+        batch_step([b], 3)
+        ma, mb = a.moments(), b.moments()
+        for k in ma:
+            assert np.array_equal(ma[k], mb[k]), k
