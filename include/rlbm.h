@@ -124,7 +124,9 @@ typedef struct {
  *  cuda_stream  a cudaStream_t (NULL = legacy default stream), borrowed.
  * Builds the stencil tables on the host (weights of Eq. 52 in binary128),
  * uploads them and allocates two population buffers.  *out is set only on
- * success.  Errors: EINVAL, ENOQUAD, ENOTSUP, ENOMEM, ECUDA. */
+ * success.  Errors: EINVAL, ENOQUAD, ENOTSUP (also: a population plane of
+ * (Nx rounded up to 32) * Ny elements must stay below 2^32, the kernels'
+ * 32-bit element indices), ENOMEM, ECUDA. */
 rlbm_status rlbm_create(const rlbm_stencil* st, double m, double tau, int Nx, int Ny,
                         rlbm_dtype dtype, void* cuda_stream, rlbm_ctx** out);
 
