@@ -117,6 +117,9 @@ def test_create_validates_before_device(lib):
     assert _create(lib, tau=0.5)[0] == A.RLBM_EINVAL
     assert _create(lib, Nx=0)[0] == A.RLBM_EINVAL
     assert _create(lib, Nx=65536, Ny=32768)[0] == A.RLBM_EINVAL      # 2^31 sites: 32-bit site index
+    # fewer than 2^31 sites, but a plane of 32 x (2^31 - 1) padded elements:
+    # beyond the kernels' 32-bit element indices (refused before any device work)
+    assert _create(lib, Nx=1, Ny=2 ** 31 - 1)[0] == A.RLBM_ENOTSUP
     assert _create(lib, groups=(5, 12, 14, 17, 21))[0] == A.RLBM_EINVAL
     assert _create(lib, groups=(5, 12, 14, 17, 21, 21))[0] == A.RLBM_EINVAL
     assert _create(lib, groups=(5, 12, 14, 17, 21, 85))[0] == A.RLBM_EINVAL
