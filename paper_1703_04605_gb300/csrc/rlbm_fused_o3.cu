@@ -113,8 +113,7 @@ __device__ __forceinline__ void o3_relax(const Pops& d, float e, float a0, float
   if constexpr (nx != 0) om = fmaf(-(float)nx, ax, om);
   if constexpr (ny != 0) om = fmaf(-(float)ny, ay, om);
   const float v = o3_pop<Def, I>(d);
-  if constexpr (Def::Q <= 104) __stcs(out + (size_t)(unsigned)plane * I, fmaf(om, e - v, v));
-  else __stcs(out + (long long)I * plane, fmaf(om, e - v, v));   // see o3_load
+  __stcs(out + (size_t)(unsigned)plane * I, fmaf(om, e - v, v));   // plane < 2^32 elements
 }
 
 template <int... L>
@@ -155,18 +154,11 @@ __device__ __forceinline__ void o3_collide_orbit(const Pops& d, const float (&e)
   }
 }
 
-// Pull of one population.  The stencils above Q = 104 (255 registers, two
-// blocks a SM) keep 64-bit element indices: with the 32-bit form of
-// fused_load their register allocation spills about 1.4 KB a thread.
+// Pull of one population (32-bit element indices, as fused_load).
 template <class Def, int I>
 __device__ __forceinline__ void o3_load(float (&d)[Def::Q], const void* __restrict__ fin, long long plane,
                                         long long pitch, int x, int y, int Nx, int Ny) {
-  if constexpr (Def::Q <= 104) {
-    fused_load<Def, false, I>(d, fin, nullptr, plane, pitch, x, y, Nx, Ny);
-  } else {
-    const long long idx = (long long)wrap_c<Def::F.ny[I]>(y, Ny) * pitch + wrap_c<Def::F.nx[I]>(x, Nx);
-    d[I] = __ldg(static_cast<const float*>(fin) + (long long)I * plane + idx);
-  }
+  fused_load<Def, false, I>(d, fin, nullptr, plane, pitch, x, y, Nx, Ny);
 }
 
 template <class Def, int... Is>
@@ -189,21 +181,21 @@ __device__ __forceinline__ void o3_collide_all(std::integer_sequence<int, Ks...>
   (o3_collide_orbit<Def, Ks, Pops>(d, e, nd, a0, ax, ay, out, plane, p), ...);
 }
 
-// Resident blocks of 128 threads per SM: four (128 registers) up to
-// Q = 104, in two passes over the populations: the moment pass pulls each
-// value and folds it into the group sums, the collision pass pulls it again
-// (an L1/L2 hit: the block read the same lines moments earlier) instead of
-// keeping 100 values in registers across the site solve, so the four blocks
-// spill at most 8 bytes (bit-identical to the one-pass form; measured on
-// GB300: 4 % faster than one pass at four blocks with 70-90 bytes spilled,
-// 11 % faster than one pass at three blocks of 168 registers; the kernel is
-// latency-bound).  The larger halo-4/5 sets keep one pass at 255 registers
-// and two blocks (16-48 bytes spilled), still about twice the generic kernel.
+// Two passes over the populations: the moment pass pulls each value and
+// folds it into the group sums, the collision pass pulls it again (an L1/L2
+// hit: the block read the same lines moments earlier, 1 % extra DRAM reads)
+// instead of keeping Q values in registers across the site solve.  Resident
+// blocks of 128 threads per SM: four (128 registers, no spills) up to Q = 104,
+// three (168 registers, at most 16 bytes spilled) for the Q = 133-149 sets.
+// Measured on GB300 against one pass: 4 % faster at Q <= 104 (one pass at
+// four blocks spilled 70-90 bytes; at three blocks of 168 registers it was
+// 11 % slower), 8-21 % faster for the larger sets (one pass at two blocks
+// of 255 registers).  Results are the same bit for bit.
 constexpr bool O3_TWO_PASS = true;
 
 template <class Def>
 constexpr int o3_min_blocks() {
-  return Def::Q <= 104 ? 4 : 2;
+  return Def::Q <= 104 ? 4 : 3;
 }
 
 template <class Def>
@@ -220,7 +212,7 @@ __global__ void __launch_bounds__(128, o3_min_blocks<Def>()) fused_o3_kernel(con
 #pragma unroll
     for (int k = 0; k < 9; ++k) M[k] = 0.0f;
     using Orb = std::make_integer_sequence<int, Def::O.K>;
-    constexpr bool two_pass = O3_TWO_PASS && Def::Q <= 104;
+    constexpr bool two_pass = O3_TWO_PASS;
     float d[two_pass ? 1 : Def::Q];
     if constexpr (two_pass) {
       float dd[Def::Q];
