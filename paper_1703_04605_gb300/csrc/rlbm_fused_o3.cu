@@ -4,10 +4,12 @@
 // third-order equilibrium, Anderson-Witting relaxation) restructured like the
 // second-order fused kernel (rlbm_fused.cuh):
 //
-//  * the folded eleven-group stencil is a compile-time constant: the Q
-//    populations of a site live in registers (one pass), displacements are
-//    immediates, and the moments are accumulated per group with exact integer
-//    weights and folded in with hi/lo group constants;
+//  * the folded eleven-group stencil is a compile-time constant:
+//    displacements are immediates, and the moments are accumulated per group
+//    with exact integer weights and folded in with hi/lo group constants;
+//    the populations are pulled twice, once for the moments and once for the
+//    relaxation (see O3_TWO_PASS), rather than held in registers across the
+//    site solve;
 //  * storage d_i = f_i - nref wr_i and the split site solve (n = n_r + n_d,
 //    T = 1 + T_d, R = R(mbar) + dR, one FP64 EOS step) of split_solve;
 //  * the equilibrium f_i^eq - nref wr_i = n_d wr_i + sum_l e_l W_il, with
