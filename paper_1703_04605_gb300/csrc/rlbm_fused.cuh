@@ -37,7 +37,8 @@
 // kinetic moments K^a are accumulated directly, so the energy above the rest
 // mass, e - m n, is formed without the cancellation of e and m n.
 //
-// BF16 deviation storage (template flag BF): the stored value is
+// BF16 deviation storage (template flag BF; the bfloat16 values of two
+// orbit partners share a 32-bit word, StencilDef::B): the stored value is
 // d_i = (f_i - r_i) - ref_i(x), rounded to bfloat16, where ref_i(x) =
 // mult_i (a + b_x n_x + b_y n_y + q (n_x^2 + n_y^2)) uses the equilibrium
 // coefficients of the writing site x for the population's group, rounded to
@@ -48,6 +49,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cstring>
 #include <utility>
 
 #include "rlbm_kernels.cuh"
@@ -147,8 +149,9 @@ __device__ __forceinline__ void fused_load(float (&d)[Def::Q], const void* __res
   const unsigned idx = (unsigned)ys * (unsigned)pitch + (unsigned)xs;
   const size_t pl = (unsigned)plane;
   if constexpr (BF) {
-    constexpr int g = Def::F.grp[I], mult = Def::F.mult[I];
-    const unsigned short h = fused_ld<CG>(static_cast<const unsigned short*>(fin) + idx + pl * I);
+    constexpr int g = Def::F.grp[I], mult = Def::F.mult[I], w = Def::B.word[I], hf = Def::B.half[I];
+    const unsigned short h =
+        fused_ld<CG>(static_cast<const unsigned short*>(fin) + 2 * (size_t)idx + hf + 2 * pl * w);
     const uint2 c = fused_ld<CG>(cin + idx + pl * g);
     d[I] = add_bf(h, bf_ref<DX, DY, mult>(c));
   } else {
@@ -158,7 +161,8 @@ __device__ __forceinline__ void fused_load(float (&d)[Def::Q], const void* __res
 
 // The same pull for a site whose sources need no wrapping (BF16 storage):
 // the value and its coefficient word sit at fixed offsets from the site's
-// own element (fh, ch), which takes the index arithmetic off the path.
+// own elements (fh: its half-word slot 0 of word plane 0, ch: its
+// coefficient word of group 0), which takes the index arithmetic off the path.
 template <class Def, int I, bool CG = false>
 __device__ __forceinline__ void fused_load_inner(float (&d)[Def::Q], const unsigned short* __restrict__ fh,
                                                  const uint2* __restrict__ ch, const FusedParams& p) {
@@ -368,11 +372,46 @@ __device__ __forceinline__ void fused_relax(const float (&d)[Def::Q], float e, c
   const float vn = fmaf(om, e - v, v);
   const size_t pl = (unsigned)plane;
   if constexpr (BF) {
+    // a population without an orbit partner: its own half of its word
+    constexpr int w = Def::B.word[I], hf = Def::B.half[I];
     const float dv = vn - bf_ref<nx, ny, mult>(cq[g]);
-    __stcs(static_cast<unsigned short*>(out) + pl * I, __bfloat16_as_ushort(__float2bfloat16_rn(dv)));
+    __stcs(static_cast<unsigned short*>(out) + 2 * pl * w + hf, __bfloat16_as_ushort(__float2bfloat16_rn(dv)));
   } else {
     __stcs(static_cast<float*>(out) + pl * I, vn);
   }
+}
+
+// BF16 storage: relaxation of the orbit partners I, J (one word, I in its low
+// half) and one conversion and store of the pair; R2: the arithmetic as
+// packed pairs (each lane the scalar operations)
+template <class Def, int I, int J, bool R2>
+__device__ __forceinline__ void bf_relax_pair(const float (&d)[Def::Q], float eI, float eJ, const uint2 (&cq)[6],
+                                              float a0, float ax, float ay, void* __restrict__ out,
+                                              long long plane) {
+  constexpr int g = Def::F.grp[I], nxI = Def::F.nx[I], nyI = Def::F.ny[I], nxJ = Def::F.nx[J],
+                nyJ = Def::F.ny[J], mult = Def::F.mult[I];
+  static_assert(Def::B.word[I] == Def::B.word[J] && Def::B.half[I] == 0 && Def::B.half[J] == 1,
+                "orbit partners share a word, the first in its low half");
+  float omI = a0, omJ = a0;
+  if constexpr (nxI != 0) omI = fmaf(-(float)nxI, ax, omI);
+  if constexpr (nyI != 0) omI = fmaf(-(float)nyI, ay, omI);
+  if constexpr (nxJ != 0) omJ = fmaf(-(float)nxJ, ax, omJ);
+  if constexpr (nyJ != 0) omJ = fmaf(-(float)nyJ, ay, omJ);
+  const float rI = bf_ref<nxI, nyI, mult>(cq[g]), rJ = bf_ref<nxJ, nyJ, mult>(cq[g]);
+  float2 dv;
+  if constexpr (R2) {
+    const float2 v = make_float2(d[I], d[J]);
+    const float2 t = __ffma2_rn(v, make_float2(-1.0f, -1.0f), make_float2(eI, eJ));   // e - v
+    const float2 vn = __ffma2_rn(make_float2(omI, omJ), t, v);
+    dv = __ffma2_rn(make_float2(rI, rJ), make_float2(-1.0f, -1.0f), vn);
+  } else {
+    const float vI = d[I], vJ = d[J];
+    dv = make_float2(fmaf(omI, eI - vI, vI) - rI, fmaf(omJ, eJ - vJ, vJ) - rJ);
+  }
+  const __nv_bfloat162 b = __floats2bfloat162_rn(dv.x, dv.y);   // .x: low half
+  unsigned word;
+  memcpy(&word, &b, sizeof word);
+  __stcs(static_cast<unsigned*>(out) + (size_t)(unsigned)plane * Def::B.word[I], word);
 }
 
 // Relaxation of two members I, J of an orbit as packed pairs (each lane the
@@ -391,16 +430,13 @@ __device__ __forceinline__ void fused_relax2(const float (&d)[Def::Q], float eI,
   const float2 v = make_float2(d[I], d[J]);
   const float2 t = __ffma2_rn(v, make_float2(-1.0f, -1.0f), make_float2(eI, eJ));   // e - v
   const float2 vn = __ffma2_rn(make_float2(omI, omJ), t, v);
+  static_assert(!BF, "BF16 pairs go through bf_relax_pair");
+  (void)cq;
+  (void)mult;
+  (void)g;
   const size_t pl = (unsigned)plane;
-  if constexpr (BF) {
-    const float2 r = make_float2(bf_ref<nxI, nyI, mult>(cq[g]), bf_ref<nxJ, nyJ, mult>(cq[g]));
-    const float2 dv = __ffma2_rn(r, make_float2(-1.0f, -1.0f), vn);
-    __stcs(static_cast<unsigned short*>(out) + pl * I, __bfloat16_as_ushort(__float2bfloat16_rn(dv.x)));
-    __stcs(static_cast<unsigned short*>(out) + pl * J, __bfloat16_as_ushort(__float2bfloat16_rn(dv.y)));
-  } else {
-    __stcs(static_cast<float*>(out) + pl * I, vn.x);
-    __stcs(static_cast<float*>(out) + pl * J, vn.y);
-  }
+  __stcs(static_cast<float*>(out) + pl * I, vn.x);
+  __stcs(static_cast<float*>(out) + pl * J, vn.y);
 }
 
 // Equilibrium of one reflection orbit: the group polynomial
@@ -418,6 +454,18 @@ __device__ __forceinline__ void fused_collide_orbit(const float (&d)[Def::Q], co
   if constexpr (ay != 0) E0 = fmaf(m * (float)(ay * ay), c[g][4], E0);
   if constexpr (kind == 1) {
     fused_relax<Def, BF, i0>(d, E0, cq, a0, ax_, ay_, out, plane);
+  } else if constexpr (BF && kind == 2) {
+    const float X = (m * (float)ax) * c[g][1];
+    bf_relax_pair<Def, i0, i1, R2>(d, E0 + X, E0 - X, cq, a0, ax_, ay_, out, plane);
+  } else if constexpr (BF && kind == 3) {
+    const float Y = (m * (float)ay) * c[g][2];
+    bf_relax_pair<Def, i0, i2, R2>(d, E0 + Y, E0 - Y, cq, a0, ax_, ay_, out, plane);
+  } else if constexpr (BF) {
+    const float X = (m * (float)ax) * c[g][1], Y = (m * (float)ay) * c[g][2];
+    const float Z = (m * (float)(ax * ay)) * c[g][5];
+    const float EP = E0 + Z, EM = E0 - Z, XP = X + Y, XM = X - Y;
+    bf_relax_pair<Def, i0, i3, R2>(d, EP + XP, EP - XP, cq, a0, ax_, ay_, out, plane);
+    bf_relax_pair<Def, i1, i2, R2>(d, EM - XM, EM + XM, cq, a0, ax_, ay_, out, plane);
   } else if constexpr (kind == 2) {
     const float X = (m * (float)ax) * c[g][1];
     if constexpr (R2) {
@@ -762,7 +810,7 @@ __device__ __forceinline__ void fused_site(const FusedParams& p, const void* __r
     if constexpr (BF && Def::Q <= 64) {
       constexpr int H = Def::halo;
       if ((unsigned)(x - H) < (unsigned)p.inner_nx && (unsigned)(y - H) < (unsigned)p.inner_ny)
-        fused_load_inner_all<Def, CG>(Seq{}, d, static_cast<const unsigned short*>(fin) + here,
+        fused_load_inner_all<Def, CG>(Seq{}, d, static_cast<const unsigned short*>(fin) + 2 * (size_t)here,
                                       static_cast<const uint2*>(p.cin) + here, p);
       else
         fused_load_all<Def, true, CG>(Seq{}, d, fin, static_cast<const uint2*>(p.cin), p.plane, p.pitch, x, y,
@@ -837,7 +885,8 @@ __device__ __forceinline__ void fused_site(const FusedParams& p, const void* __r
         __stcs(static_cast<uint2*>(p.cout) + here + pl * g, cq[g]);
       }
     }
-    void* out = BF ? static_cast<void*>(static_cast<unsigned short*>(fout) + here)
+    // BF16: the site's word of word plane 0 (two bfloat16 halves)
+    void* out = BF ? static_cast<void*>(static_cast<unsigned*>(fout) + here)
                    : static_cast<void*>(static_cast<float*>(fout) + here);
     if constexpr (fused_use_orbits<Def, BF>())
       fused_collide_all<Def, BF, FusedForms<Def, BF, EXL>::relax2>(Orb{}, d, c, cq, a0, ax, ay, out, p.plane);
@@ -973,19 +1022,21 @@ __global__ void __launch_bounds__(128) bf16_init_pops(const __grid_constant__ Fu
     double c[6][6];
     fp64_group_coeffs(p, sc, fd.n[s], fd.ux[s], fd.uy[s], fd.T[s], c, fl);
     const long long here = (long long)y * p.pitch + x;
-    constexpr Folded F = Def::F;   // local copy: indexed at run time below
+    constexpr Folded F = Def::F;   // local copies: indexed at run time below
+    constexpr BfWords B = Def::B;
     for (int i = 0; i < Def::Q; ++i) {
       const int g = F.grp[i], nx = F.nx[i], ny = F.ny[i], mult = F.mult[i];
       const double fr = mult * (c[g][0] + nx * c[g][1] + ny * c[g][2] + nx * nx * c[g][3] + ny * ny * c[g][4] +
                                 nx * ny * c[g][5]);
       const uint2 own = coef[(long long)g * p.plane + here];
-      cur[(long long)i * p.plane + here] = __bfloat16_as_ushort(__double2bfloat16(fr - bf_ref_rt(own, nx, ny, mult)));
+      cur[2 * ((long long)B.word[i] * p.plane + here) + B.half[i]] =
+          __bfloat16_as_ushort(__double2bfloat16(fr - bf_ref_rt(own, nx, ny, mult)));
       int xs = x - nx, ys = y - ny;
       xs = ((xs % p.Nx) + p.Nx) % p.Nx;
       ys = ((ys % p.Ny) + p.Ny) % p.Ny;
       const long long there = (long long)ys * p.pitch + xs;
       const uint2 rem = coef[(long long)g * p.plane + there];
-      prev[(long long)i * p.plane + there] =
+      prev[2 * ((long long)B.word[i] * p.plane + there) + B.half[i]] =
           __bfloat16_as_ushort(__double2bfloat16(fr - bf_ref_rt(rem, nx, ny, mult)));
     }
   }
@@ -1005,13 +1056,15 @@ __global__ void __launch_bounds__(128) bf16_moments(const __grid_constant__ Step
     site_of(s, p.Nx, x, y);
     double m[9];
     for (int k = 0; k < 9; ++k) m[k] = 0.0;
-    constexpr Folded F = Def::F;   // local copy: indexed at run time below
+    constexpr Folded F = Def::F;   // local copies: indexed at run time below
+    constexpr BfWords B = Def::B;
     for (int i = 0; i < Def::Q; ++i) {
       const int g = F.grp[i], nx = F.nx[i], ny = F.ny[i], mult = F.mult[i];
       const int xs = wrap_sub(x, p.pt.dxm[i], p.Nx);
       const int ys = wrap_sub(y, p.pt.dym[i], p.Ny);
       const long long there = (long long)ys * p.pitch + xs;
-      const double f = (double)__uint_as_float((unsigned)prev[(long long)i * p.plane + there] << 16) +
+      const unsigned short h = prev[2 * ((long long)B.word[i] * p.plane + there) + B.half[i]];
+      const double f = (double)__uint_as_float((unsigned)h << 16) +
                        bf_ref_rt(cprev[(long long)g * p.plane + there], nx, ny, mult);
       for (int k = 0; k < 9; ++k) m[k] = fma(f, p.pt.mom[k][i], m[k]);
     }

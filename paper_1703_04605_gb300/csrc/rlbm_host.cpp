@@ -221,16 +221,21 @@ static void fill_fused(rlbm_ctx* c, double nref) {
     f.nx_m = (unsigned)(((1ULL << (31 + l)) + (unsigned long long)c->Nx - 1) / (unsigned long long)c->Nx);
     f.nx_sh = 31 + l;
   }
-  // fixed pull offsets of the sites that need no wrapping (BF16 kernels)
+  // fixed pull offsets of the sites that need no wrapping (BF16 kernels):
+  // bfloat16 slots (two per word, population i in half half[i] of word plane
+  // word[i]) from the site's slot 0 of word plane 0, coefficient words from
+  // its word of group 0
+  const BfWords* bw = c->fused == 1 ? &StencilM1::B : c->fused == 2 ? &StencilG16::B
+                    : c->fused == 3 ? &StencilE5::B : &StencilS2::B;
   const int H = sb.halo;
-  const long long span = (long long)c->Q * c->plane + (long long)H * (c->pitch + 1);
+  const long long span = 2LL * (c->Q + 1) * c->plane + 2LL * H * (c->pitch + 1);
   if (c->Q <= kMaxQ2 && span < INT_MAX && c->Nx > 2 * H && c->Ny > 2 * H) {
     f.inner_nx = c->Nx - 2 * H;
     f.inner_ny = c->Ny - 2 * H;
     for (int i = 0; i < c->Q; ++i) {
       const FoldedPop& fp = sb.pops[i];
       const long long back = (long long)fp.ny * c->pitch + fp.nx;
-      f.doff[i] = (int)((long long)i * c->plane - back);
+      f.doff[i] = (int)(2 * ((long long)bw->word[i] * c->plane - back) + bw->half[i]);
       f.dcoff[i] = (int)((long long)fp.group * c->plane - back);
     }
   }
@@ -529,7 +534,9 @@ rlbm_status rlbm_create(const rlbm_stencil* st, double m, double tau, int Nx, in
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess || ndev == 0) return fail(nullptr, RLBM_ECUDA, "no CUDA device available");
   c->mem = current_devmem(c->stream);
-  const size_t fbytes = (size_t)c->Q * (size_t)c->plane * c->elem;
+  // BF16: two bfloat16 values a 32-bit word, so Q rounded up to even slots
+  const size_t slots = dtype == RLBM_BF16_DEV ? (size_t)((c->Q + 1) / 2 * 2) : (size_t)c->Q;
+  const size_t fbytes = slots * (size_t)c->plane * c->elem;
   for (int b = 0; b < 2; ++b) {
     e = c->mem.get(&c->buf[b], fbytes);
     if (e != cudaSuccess) {

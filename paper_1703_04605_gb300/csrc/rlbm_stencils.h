@@ -242,6 +242,61 @@ constexpr bool orbits_cover(const Folded& F, const Orbits& O) {
   return true;
 }
 
+// Word layout of the BF16-deviation storage: the bfloat16 values of two
+// populations share one 32-bit word, so that the writer converts and stores
+// them together.  Partners are the members of a reflection orbit that the
+// collision relaxes side by side ((+,+) with (-,-), (-,+) with (+,-); the two
+// members of a pair orbit); single populations (n = 0) share words among
+// themselves, an odd last one a word of its own.  Population i sits in word
+// plane word[i], half half[i] (0: low, 1: high).
+struct BfWords {
+  int words;
+  int word[kMaxFolded], half[kMaxFolded];
+};
+
+constexpr BfWords make_bf_words(const Folded& F, const Orbits& O) {
+  BfWords W{};
+  W.words = 0;
+  int single = -1;
+  for (int k = 0; k < O.K; ++k) {
+    const int i0 = O.idx[k][0], i1 = O.idx[k][1], i2 = O.idx[k][2], i3 = O.idx[k][3];
+    if (O.kind[k] == 4) {
+      W.word[i0] = W.word[i3] = W.words++;
+      W.half[i0] = 0, W.half[i3] = 1;
+      W.word[i1] = W.word[i2] = W.words++;
+      W.half[i1] = 0, W.half[i2] = 1;
+    } else if (O.kind[k] == 2) {
+      W.word[i0] = W.word[i1] = W.words++;
+      W.half[i0] = 0, W.half[i1] = 1;
+    } else if (O.kind[k] == 3) {
+      W.word[i0] = W.word[i2] = W.words++;
+      W.half[i0] = 0, W.half[i2] = 1;
+    } else if (single < 0) {
+      single = i0;
+      W.word[i0] = W.words++;
+      W.half[i0] = 0;
+    } else {
+      W.word[i0] = W.word[single];
+      W.half[i0] = 1;
+      single = -1;
+    }
+  }
+  (void)F;
+  return W;
+}
+
+// Every (word, half) slot used by exactly one population.
+constexpr bool bf_words_ok(const Folded& F, const BfWords& W) {
+  int used[kMaxFolded][2] = {};
+  for (int i = 0; i < F.Q; ++i) {
+    if (W.word[i] < 0 || W.word[i] >= W.words || W.half[i] < 0 || W.half[i] > 1) return false;
+    used[W.word[i]][W.half[i]] += 1;
+  }
+  for (int w = 0; w < W.words; ++w)
+    if (used[w][0] != 1 || used[w][1] > 1) return false;
+  return true;
+}
+
 // Stencils with compiled fused kernels (group ids ascending).
 template <int G0, int G1, int G2, int G3, int G4, int G5>
 struct StencilDef {
@@ -251,6 +306,9 @@ struct StencilDef {
   static constexpr int halo = F.halo;
   static constexpr Orbits O = make_orbits(F);
   static_assert(orbits_cover(F, O), "reflection orbits must partition the folded stencil");
+  static constexpr BfWords B = make_bf_words(F, O);
+  static_assert(bf_words_ok(F, B), "every population needs its own half of a BF16 word");
+  static_assert(B.words == (F.Q + 1) / 2, "BF16 buffers hold Q rounded up to even slots");
 };
 
 using StencilM1 = StencilDef<5, 12, 14, 17, 21, 26>;    // m/T_R ~ 1
@@ -268,6 +326,9 @@ struct StencilO3Def {
   static constexpr int halo = F.halo;
   static constexpr Orbits O = make_orbits(F);
   static_assert(orbits_cover(F, O), "reflection orbits must partition the folded stencil");
+  static constexpr BfWords B = make_bf_words(F, O);
+  static_assert(bf_words_ok(F, B), "every population needs its own half of a BF16 word");
+  static_assert(B.words == (F.Q + 1) / 2, "BF16 buffers hold Q rounded up to even slots");
 };
 
 using StencilO3M5 = StencilO3Def<1, 2, 5, 6, 7, 9, 10, 11, 12, 13, 15>;   // m/T_R in [4.75, 5.19]
