@@ -807,7 +807,7 @@ __device__ __forceinline__ void fused_site(const FusedParams& p, const void* __r
     }
     float d[Q];
     const unsigned here = (unsigned)y * (unsigned)p.pitch + (unsigned)x;
-    if constexpr (BF && Def::Q <= 64) {
+    if constexpr (BF) {
       constexpr int H = Def::halo;
       if ((unsigned)(x - H) < (unsigned)p.inner_nx && (unsigned)(y - H) < (unsigned)p.inner_ny)
         fused_load_inner_all<Def, CG>(Seq{}, d, static_cast<const unsigned short*>(fin) + 2 * (size_t)here,
