@@ -379,6 +379,8 @@ FUSED_SOURCES = ["paper_1703_04605_gb300/csrc/rlbm_fused.cuh", "paper_1703_04605
                  "paper_1703_04605_gb300/csrc/rlbm_stencils.h", "paper_1703_04605_gb300/csrc/rlbm_kernels.cuh",
                  "paper_1703_04605_gb300/csrc/rlbm_fused_m1.cu"]
 
+FUSED_E5_SOURCES = FUSED_SOURCES[:4] + ["paper_1703_04605_gb300/csrc/rlbm_fused_e5.cu"]
+
 
 def profiled_traffic(profile, sources):
     """DRAM bytes per launch recorded in a committed ncu summary, or None when
@@ -590,7 +592,9 @@ def run_blast(args):
     torch.cuda.set_device(local)
     build.build()
     st = W.STENCIL_E5
-    N, R, tau = 8192, 512, 0.7
+    # --side: a smaller copy with the disc radius scaled with the side (profiling)
+    N = 8192 if args.side == N_SIDE else args.side
+    R, tau = max(1, 512 * N // 8192), 0.7
     f = W.blast(N, R)
     stream = torch.cuda.Stream()
     sites = float(N) * N
@@ -635,14 +639,16 @@ def run_blast(args):
     line = {"metric": METRIC, "value": sites / (ms / 1e3) / 1e6, "unit": "MLUPS", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": "blast_8192: 8192x8192 periodic, disc r=512 at T=2 in T=1 (T_R = their mean), "
+            "config": {"workload": "blast_%d: %dx%d periodic, disc r=%d at T=2 in T=1 (T_R = their mean), " % (N, N, N, R) +
                                    "n=1, u=0, tau=0.7, "
                                    "m/T=0.01 requested, run at m/T_R=0.36 (smallest covered), stencil "
                                    "G1,G14,G49,G51,G60,G70 (Q=73 folded), v0=0.1488232",
                        "sites": int(sites), "Q": info["Q"], "m_over_T_used": st["m"],
                        "l2": "inputs larger than L2"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": (profiled_traffic("fused_bf16_kernel_blast_8192.md", FUSED_E5_SOURCES)
+                                     if N == 8192 and info["kernel"] == 3 else None),
                          "kernel": kernel_name("bf16dev", info["kernel"]),
                          "bytes_per_site": info["bytes_per_site"],
                          "frac_incl_coefficients": (info["bytes_per_site"] + info["extra_bytes_per_site"]) * sites
@@ -841,7 +847,8 @@ def main():
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64", "bf16dev"])
     ap.add_argument("--side", type=int, default=N_SIDE,
                     help="random_flow: time a side x side crop of the 4096^2 field; random3d: a side^3 lattice "
-                         "instead of 256^3 (profiling of small cases)")
+                         "instead of 256^3; blast: a side^2 copy with the disc radius scaled "
+                         "(profiling of small cases)")
     ap.add_argument("--mass", type=float, default=None,
                     help="third_order only: m/T_R of the stencil library's set to time (default: the m/T_R = 5 set)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
