@@ -104,7 +104,7 @@ constexpr int DR_NPOS = 192;     // T < 4 T_R
 constexpr int DR_NC = 7;         // degree 6
 constexpr int DR_NSEG = DR_NNEG + DR_NPOS;
 
-// populations of the compiled second-order stencils (at most 73)
+// bound on the populations of the compiled second-order stencils (at most 73)
 constexpr int kMaxQ2 = 80;
 
 // Parameters of the stencil-specialised FP32 kernels (rlbm_fused.cuh).
@@ -145,14 +145,15 @@ struct FusedParams {
   // gm as the operand pairs of the packed (f32x2) moment sums: per group
   // (P0, P0^2), (Pv, Pv), (P0 Pv, P0 Pv), (Pv^2, Pv^2), hi pair then lo pair
   float2 gm2[6][8];
-  // sites x in [halo, halo + inner_nx), y in [halo, halo + inner_ny) pull
-  // without wrapping; there the pulled value of population i and its
-  // coefficient word (BF16) sit doff[i] / dcoff[i] elements from the site's
-  // own element of plane 0 (0 and 0 when the offsets do not fit 32 bits)
   float2 gf2[3][10][2];   // groups (2j, 2j+1): gf hi pair, lo pair
   // site / Nx = (site nx_m) >> nx_sh for 0 <= site < 2^31
   unsigned nx_m;
   int nx_sh;
+  // BF16 kernels: sites x in [halo, halo + inner_nx), y in [halo, halo +
+  // inner_ny) pull without wrapping; there the bfloat16 value of population
+  // i and its coefficient word sit doff[i] / dcoff[i] elements from the
+  // site's own slot and word of plane 0.  inner_nx = inner_ny = 0 (every
+  // site takes the wrapped pull) when the offsets do not fit 32 bits.
   int inner_nx, inner_ny;
   int doff[kMaxQ2], dcoff[kMaxQ2];
 };
