@@ -270,7 +270,8 @@ def cpu_baseline_o3(seconds=10.0, side=24, procs=None):
 
 # FP64 paths are bound by the FP64 pipe.  FLOPs per site of the FP64 step
 # kernels on the benchmarked stencils, from ncu's FP64 instruction counts
-# (profiles/fp64_kernels_alu_1024.md); the peak is GB300's nominal FP64 rate.
+# (profiles/fp64_kernels_alu_1024.md).  The peak is measured (fp64_peak); GB300's
+# nominal FP64 rate is reported beside it and used only if the probe fails.
 FP64_PEAK_TFLOPS = 1.25
 FP64_FLOP_PER_SITE = {"step_f64_kernel/5,12,14,17,21,26": 3271.0,
                       "step_o3_kernel/1,2,5,6,7,9,10,11,12,13,15": 7352.0}
