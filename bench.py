@@ -289,7 +289,7 @@ def fp64_peak():
         from paper_1703_04605_gb300 import _abi as A
         v = C.c_double()
         ok = A.load().rlbm_fp64_fma_rate(None, C.byref(v)) == A.RLBM_OK and v.value > 0
-        _FP64_PEAK.append((v.value, "measured (rlbm_fp64_fma_rate: FMA chains, best of 5, CUDA events)")
+        _FP64_PEAK.append((v.value, "measured (rlbm_fp64_fma_rate: FMA chains on register operands, best of 5, CUDA events)")
                           if ok else (FP64_PEAK_TFLOPS, "nominal"))
     return _FP64_PEAK[0]
 
