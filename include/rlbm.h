@@ -171,7 +171,10 @@ rlbm_status rlbm_set_extended_sums(rlbm_ctx* ctx, int level);
  * doubles) receives, in bit order, one Nx*Ny plane per scalar (RLBM_M_NVEC:
  * 3 planes N^0,N^x,N^y; RLBM_M_TMN: 6 planes T^00,T^0x,T^0y,T^xx,T^xy,T^yy).
  * Page-locked (mapped) memory is written directly by the read-out kernel;
- * other memory through a device buffer of the context and one copy.
+ * other memory through a device buffer of the context and one copy.  The
+ * library cannot see the buffer's length: a page-locked buffer shorter than
+ * rlbm_moments_size would be overrun by the device (the Python binding
+ * checks the length before the call).
  * Synchronises the stream, then reports any sticky device error. */
 #define RLBM_M_N    0x01u  /* n = U_a N^a (Eq. 19)             */
 #define RLBM_M_UX   0x02u  /* u_x = U^x / U^0                  */
@@ -339,9 +342,10 @@ rlbm_status rlbm3_step(rlbm_ctx3* ctx, int nsteps);
 /* Macroscopic fields of the pre-collision state at t into host memory, one
  * Nx*Ny*Nz plane per scalar, in the order of the mask bits: RLBM_M_N, _UX,
  * _UY, _T, _E, _NVEC (4 planes N^0..N^z), _TMN (10 planes T^00 T^0x T^0y
- * T^0z T^xx T^xy T^xz T^yy T^yz T^zz), _UZ.  Page-locked memory is written
- * directly, as rlbm_moments.  Synchronises the stream and reports sticky
- * device errors (ENONPHYS). */
+ * T^0z T^xx T^xy T^xz T^yy T^yz T^zz), _UZ; rlbm3_moments_size doubles.
+ * Page-locked memory is written directly, as rlbm_moments (same length
+ * caveat).  Synchronises the stream and reports sticky device errors
+ * (ENONPHYS). */
 rlbm_status rlbm3_moments(rlbm_ctx3* ctx, double* out, unsigned mask);
 size_t rlbm3_moments_size(const rlbm_ctx3* ctx, unsigned mask);
 
